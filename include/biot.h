@@ -1,0 +1,209 @@
+/*
+ * biot.h - C ABI of the GB300 space-time Biot poroelasticity library.
+ *
+ * The library applies and solves the monolithic space-time slab system of the
+ * fully coupled Biot equations (Köcher, "Space-Time-Parallel Poroelasticity
+ * Simulation"):
+ *
+ *   strong form (paper §Poroelasticity): quasi-static momentum with the
+ *   effective stress C:eps(u) - b p I, Darcy's law eta K^{-1} q + grad p = 0 and
+ *   the storage equation b d_t div u + (1/M) d_t p + div q = f (the volumetric
+ *   mean stress substituted, so K_dr cancels from the operator);
+ *   space (paper §Discretisation in Space): continuous Q2 displacement,
+ *   Raviart-Thomas RT1 flux, discontinuous Q1 (DGQ1) pressure on a Cartesian
+ *   quad/hex mesh;
+ *   time (paper §Discretisation in Time): discontinuous Galerkin dG(r),
+ *   r = 0, 1, 2, on slabs I_n = (t_{n-1}, t_n), Lagrange basis on the r+1
+ *   right-Radau points (the last one is t_n, so the last temporal DoF is the
+ *   end state U(t_n^-));
+ *   slab system (paper §Monolithic Approach):
+ *     calA X = (D (x) S + tau M_t (x) A_s) X = F + (phi(0) e_r^T (x) S) X_prev
+ *   with A_s = [[A, 0, -bE], [0, Mq, -B^T], [0, B, 0]],
+ *        S   = [[0, 0, 0], [0, 0, 0], [b E^T, 0, (1/M) Mp]];
+ *   solver (paper §Monolithic Approach, §Preconditioning technology):
+ *   restarted flexible GMRES, right-preconditioned by the time-spectral
+ *   decomposition of M_t^{-1} D with the complex-pair couplings dropped
+ *   ("diagonal blockwise L_j") and a block-triangular fixed-stress
+ *   preconditioner per block: flux-pressure block first with the
+ *   displacement coupling replaced by (b^2/K_dr) Mp, then the displacement
+ *   block by a geometric-multigrid V-cycle with Chebyshev-Jacobi smoothing.
+ *
+ * Vector layout.  A spatial vector ("one temporal level", length n_space) is
+ *   [u_0 | .. | u_{d-1} | q_0 | .. | q_{d-1} | p]
+ *   u_c : Q2 nodes, (2n_x+1) x (2n_y+1) [x (2n_z+1)], x fastest;
+ *   q_c : 2n_c+1 Lagrange points {0,1/2,1} per cell along direction c, times
+ *         the two Gauss points (1/2 -+ sqrt(3)/6) per cell across every
+ *         other direction (2n_t), x fastest;
+ *   p   : the 2 x 2 [x 2] Gauss points of every cell as one (2n_x) x (2n_y)
+ *         [x (2n_z)] grid, x fastest.
+ * A slab vector is r+1 spatial vectors back to back (time-major).
+ * Essential (constrained) DoFs are identity rows of every operator; right-hand
+ * sides must carry the prescribed value there (only homogeneous data is
+ * supported: 0).
+ *
+ * Memory.  Unless stated otherwise, vector arguments are DEVICE pointers
+ * owned by the caller, 8-byte aligned (FP64) or 4-byte aligned (FP32).  The
+ * library allocates its own workspace in biot_setup (and, lazily, Krylov
+ * bases on the first solve) and frees it in biot_destroy.  All GPU work is
+ * enqueued on the given stream (a cudaStream_t passed as void*, NULL = the
+ * legacy default stream); calls that report results on the host synchronise
+ * that stream.
+ *
+ * Errors.  Every entry point returns BIOT_OK or a BIOT_E* code; no C++
+ * exception crosses the ABI.  biot_last_error(ctx) gives a message for the
+ * last failing call on that context.  On BIOT_ECUDA the context is left in an
+ * unspecified but destroyable state.
+ */
+#ifndef BIOT_H
+#define BIOT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  BIOT_OK = 0,
+  BIOT_EINVAL = 1,      /* invalid argument (sizes, coefficients out of range, NULL) */
+  BIOT_ENOMEM = 2,      /* device allocation failed */
+  BIOT_ECUDA = 3,       /* a CUDA call failed */
+  BIOT_ENOCONV = 4,     /* iteration limit reached before the tolerance */
+  BIOT_EBREAKDOWN = 5,  /* non-finite value met in the Krylov iteration */
+  BIOT_ETIMEOUT = 6     /* a bounded device-side wait ran out */
+};
+
+/* boundary condition codes per face, faces numbered 2*dir + side (side 0 = lower) */
+enum { BIOT_U_NATURAL = 0, BIOT_U_DIRICHLET = 1, BIOT_U_ROLLER = 2 }; /* traction | all comps | normal comp */
+enum { BIOT_F_NATURAL = 0, BIOT_F_NOFLOW = 1 };                      /* pressure | q.n = 0 essential      */
+
+/* arithmetic of a call */
+enum { BIOT_FP64 = 0, BIOT_FP32 = 1, BIOT_MIXED = 2 };
+
+typedef struct biot_ctx* biot_t;
+
+typedef struct {
+  int dim;       /* 2 or 3 */
+  int n[3];      /* cells per direction */
+  double lo[3];  /* box corner */
+  double hi[3];  /* box corner */
+  int u_bc[6];   /* BIOT_U_* per face */
+  int f_bc[6];   /* BIOT_F_* per face */
+} biot_mesh;
+
+/* Coefficients (paper §Poroelasticity): Biot coefficient 0 < b < 1, 1/M >= 0,
+ * drained bulk modulus K_dr > 0 (enters only the fixed-stress preconditioner,
+ * beta = b^2 / K_dr), Lame coefficients lambda >= 0, mu > 0 (isotropic C),
+ * fluid viscosity eta > 0, and the isotropic permeability of every cell
+ * (HOST array, length n_x n_y [n_z], lexicographic, x fastest, all > 0). */
+typedef struct {
+  double b, invM, K_dr, lambda, mu, eta;
+  const double* K_cell;
+} biot_coeffs;
+
+typedef struct {
+  int gmres_restart;    /* m (default 30) */
+  int cheb_degree;      /* Chebyshev degree of the elasticity smoother (default 4) */
+  int schur_degree;     /* Chebyshev degree of the flux-pressure Schur solve (default 8) */
+  int mg_min_cells;     /* stop coarsening at this many cells per direction (default 2) */
+  double beta_fs;       /* fixed-stress parameter; <= 0 selects b^2 / K_dr */
+} biot_opts;
+
+typedef struct {
+  double tol;           /* relative true residual ||b - calA x|| / ||b|| (default 1e-10) */
+  int max_iters;        /* total Krylov iterations (inner ones for MIXED), default 2000 */
+  int mode;             /* BIOT_FP64 or BIOT_MIXED */
+  double inner_tol;     /* MIXED: relative tolerance of each FP32 inner solve (default 1e-5) */
+  int transpose;        /* 1: solve calA^T x = rhs (adjoint) */
+} biot_solve_opts;
+
+typedef struct {
+  int iterations;       /* Krylov iterations (all inner iterations for MIXED) */
+  int refinements;      /* MIXED: outer refinement steps */
+  int restarts;
+  double rel_residual;  /* final true relative residual (FP64) */
+  double seconds;       /* wall time of the call (host clock, synchronised) */
+} biot_stats;
+
+/* Create a context for one mesh, coefficient set and time order r (0..2).
+ * Builds the 1-D reference tables, the multigrid hierarchy (dense coarse
+ * inverse in FP64) and the time-spectral transform on the current CUDA
+ * device.  opts may be NULL (defaults).  Errors: EINVAL for dim not in {2,3},
+ * n < 1, r not in 0..2, b not in (0,1), invM < 0, K_dr <= 0, mu <= 0,
+ * lambda < 0, eta <= 0, any K_cell <= 0 or non-finite; ENOMEM; ECUDA. */
+int biot_setup(const biot_mesh* mesh, const biot_coeffs* coeffs, int r, const biot_opts* opts, biot_t* out);
+
+/* Sizes: DoFs per temporal level and per slab, number of cells. */
+int biot_sizes(biot_t ctx, int64_t* n_space, int64_t* n_slab, int64_t* n_cells);
+
+/* Replace the cellwise permeability (HOST array, n_cells, > 0). */
+int biot_set_permeability(biot_t ctx, const double* K_cell);
+
+/* y = calA x (transpose = 0) or calA^T x (transpose = 1) for one slab of
+ * length tau > 0 (paper §Monolithic Approach block system, applied matrix-free
+ * in Kronecker form).  prec = BIOT_FP64: x, y are double*; BIOT_FP32: float*.
+ * x and y must not overlap. */
+int biot_apply_slab(biot_t ctx, double tau, const void* x, void* y, int prec, int transpose, void* stream);
+
+/* Apply the slab preconditioner P ~ calA^{-1} (or P^T ~ calA^{-T}) once:
+ * z = P r.  prec as in biot_apply_slab. */
+int biot_precondition(biot_t ctx, double tau, const void* r, void* z, int prec, int transpose, void* stream);
+
+/* Solve calA x = rhs (or calA^T x = rhs) for one slab.  rhs, x: double*,
+ * n_slab; x holds the initial guess on entry and the solution on exit.
+ * opts/stats may be NULL.  Returns ENOCONV (x = best iterate) if max_iters
+ * is reached first, EBREAKDOWN on non-finite values. */
+int biot_solve_slab(biot_t ctx, double tau, const double* rhs, double* x, const biot_solve_opts* opts, biot_stats* stats,
+                    void* stream);
+
+/* Time marching over `slabs` slabs of (0, T] (paper §Discretisation in Time:
+ * the discontinuous test space gives a slab-by-slab march).  The load is
+ * F(x, t) = sum_m g_m(t) f_m(x) with nterms spatial load vectors f_terms[m]
+ * (each n_space, assembled right-hand sides of one temporal level; constrained
+ * entries are ignored) and polynomial time profiles
+ * g_m(t) = tcoef[4m] + tcoef[4m+1] t + tcoef[4m+2] t^2 + tcoef[4m+3] t^3
+ * (HOST array).  U0 (n_space) is the state at t = 0 (only u and p matter);
+ * U_end (n_space) receives U(T^-).  f_terms, U0 and U_end may each be HOST or
+ * DEVICE pointers (detected); host data is copied inside the call.  X_all,
+ * if not NULL, is a DEVICE array of slabs * n_slab doubles receiving every
+ * slab solution.  iters_per_slab (HOST, may be NULL) receives the Krylov
+ * iterations of each slab. */
+int biot_march(biot_t ctx, double T, int slabs, int nterms, const double* const* f_terms, const double* tcoef,
+               const double* U0, double* U_end, double* X_all, const biot_solve_opts* opts, int* iters_per_slab,
+               biot_stats* stats, void* stream);
+
+/* Adjoint gradient of J = j^T U(T^-) with respect to the cellwise
+ * log-permeability g_c (K_c = K0 exp(g_c)): the dual problem marched backwards
+ * over slabs with the transposed slab operator, the forward slab solutions
+ * recomputed from end-state checkpoints (recompute = 1) or kept from the
+ * forward pass (recompute = 0).  j_goal (DEVICE, n_space) is the goal
+ * weight vector (see biot_goal_mean_pressure); the load is as in biot_march.
+ * J_out (HOST) receives J; dJ_dlogK (DEVICE, n_cells) receives the gradient. */
+int biot_adjoint_grad(biot_t ctx, double T, int slabs, int nterms, const double* const* f_terms, const double* tcoef,
+                      const double* U0, const double* j_goal, const biot_solve_opts* opts, int recompute, double* J_out,
+                      double* dJ_dlogK, void* stream);
+
+/* Goal weight vector of J = mean pressure over the box [lo, hi] (exact
+ * integration of the DGQ1 pressure over the clipped cells), written to the
+ * DEVICE array j (n_space; zero outside the pressure block). */
+int biot_goal_mean_pressure(biot_t ctx, const double* lo, const double* hi, double* j, void* stream);
+
+/* Built-in spatial load vectors (one temporal level, DEVICE output, n_space):
+ *  BIOT_LOAD_TRACTION_TOP  : traction -value * n on the upper face of the last
+ *                            direction (compressive load of magnitude value);
+ *  BIOT_LOAD_MMS2D_CONST   : time-constant part of the 2-D manufactured load
+ *                            (source b pi sin(pi(x+y)) + (1/M) cos(pi x)cos(pi y));
+ *  BIOT_LOAD_MMS2D_LINEAR  : part linear in t (body force, source and the
+ *                            natural-pressure boundary term) of the manufactured
+ *                            solution u = (S t, S t), p = cos(pi x)cos(pi y) t. */
+enum { BIOT_LOAD_TRACTION_TOP = 0, BIOT_LOAD_MMS2D_CONST = 1, BIOT_LOAD_MMS2D_LINEAR = 2 };
+int biot_load_preset(biot_t ctx, int kind, double value, double* f, void* stream);
+
+const char* biot_last_error(biot_t ctx);
+void biot_destroy(biot_t ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BIOT_H */

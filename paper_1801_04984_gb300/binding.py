@@ -1,0 +1,270 @@
+"""Thin ctypes binding of the C ABI in include/biot.h.
+
+Only argument marshalling happens here: every step of the computation runs in
+the CUDA library (libbiot_gb300.so, built in-tree by `build.py`).  PyTorch
+provides device memory and the current stream.  There is no CPU fallback: if
+the library is missing, loading fails with an error.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libbiot_gb300.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "biot.h")
+
+OK, EINVAL, ENOMEM, ECUDA, ENOCONV, EBREAKDOWN, ETIMEOUT = range(7)
+U_NATURAL, U_DIRICHLET, U_ROLLER = 0, 1, 2
+F_NATURAL, F_NOFLOW = 0, 1
+FP64, FP32, MIXED = 0, 1, 2
+LOAD_TRACTION_TOP, LOAD_MMS2D_CONST, LOAD_MMS2D_LINEAR = 0, 1, 2
+ERR_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOCONV", 5: "EBREAKDOWN", 6: "ETIMEOUT"}
+
+
+class Mesh(C.Structure):
+    _fields_ = [("dim", C.c_int), ("n", C.c_int * 3), ("lo", C.c_double * 3), ("hi", C.c_double * 3),
+                ("u_bc", C.c_int * 6), ("f_bc", C.c_int * 6)]
+
+
+class Coeffs(C.Structure):
+    _fields_ = [("b", C.c_double), ("invM", C.c_double), ("K_dr", C.c_double), ("lam", C.c_double),
+                ("mu", C.c_double), ("eta", C.c_double), ("K_cell", C.POINTER(C.c_double))]
+
+
+class Opts(C.Structure):
+    _fields_ = [("gmres_restart", C.c_int), ("cheb_degree", C.c_int), ("schur_degree", C.c_int),
+                ("mg_min_cells", C.c_int), ("beta_fs", C.c_double)]
+
+
+class SolveOpts(C.Structure):
+    _fields_ = [("tol", C.c_double), ("max_iters", C.c_int), ("mode", C.c_int), ("inner_tol", C.c_double),
+                ("transpose", C.c_int)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("refinements", C.c_int), ("restarts", C.c_int),
+                ("rel_residual", C.c_double), ("seconds", C.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lib = None
+
+
+def header_functions():
+    """Names of the functions declared in include/biot.h."""
+    txt = open(HEADER).read()
+    return sorted(set(re.findall(r"\b(biot_[a-z_]+)\s*\(", txt)))
+
+
+def load(path: str = LIB_PATH):
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("CUDA library %s not built (run paper_1801_04984_gb300.build.build())" % path)
+    lib = C.CDLL(path)
+    vp, dp, ip, i64p = C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int), C.POINTER(C.c_int64)
+    sig = {
+        "biot_setup": (C.c_int, [C.POINTER(Mesh), C.POINTER(Coeffs), C.c_int, C.POINTER(Opts), C.POINTER(vp)]),
+        "biot_sizes": (C.c_int, [vp, i64p, i64p, i64p]),
+        "biot_set_permeability": (C.c_int, [vp, dp]),
+        "biot_apply_slab": (C.c_int, [vp, C.c_double, vp, vp, C.c_int, C.c_int, vp]),
+        "biot_precondition": (C.c_int, [vp, C.c_double, vp, vp, C.c_int, C.c_int, vp]),
+        "biot_solve_slab": (C.c_int, [vp, C.c_double, vp, vp, C.POINTER(SolveOpts), C.POINTER(Stats), vp]),
+        "biot_march": (C.c_int, [vp, C.c_double, C.c_int, C.c_int, C.POINTER(vp), dp, vp, vp, vp,
+                                 C.POINTER(SolveOpts), ip, C.POINTER(Stats), vp]),
+        "biot_adjoint_grad": (C.c_int, [vp, C.c_double, C.c_int, C.c_int, C.POINTER(vp), dp, vp, vp,
+                                        C.POINTER(SolveOpts), C.c_int, dp, vp, vp]),
+        "biot_goal_mean_pressure": (C.c_int, [vp, dp, dp, vp, vp]),
+        "biot_load_preset": (C.c_int, [vp, C.c_int, C.c_double, vp, vp]),
+        "biot_last_error": (C.c_char_p, [vp]),
+        "biot_destroy": (None, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+class BiotError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s: %s" % (ERR_NAMES.get(code, code), msg))
+        self.code = code
+
+
+def _stream():
+    import torch
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t, dtype=None, numel=None, name="tensor"):
+    import torch
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("%s must be a torch tensor" % name)
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError("%s must be %s, got %s" % (name, dtype, t.dtype))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    if numel is not None and t.numel() != numel:
+        raise ValueError("%s must have %d elements, got %d" % (name, numel, t.numel()))
+    return C.c_void_p(t.data_ptr())
+
+
+def _solve_opts(tol=1e-10, max_iters=2000, mode=FP64, inner_tol=1e-5, transpose=0):
+    return SolveOpts(tol, max_iters, mode, inner_tol, transpose)
+
+
+class Context:
+    """One mesh + coefficient set + time order r on the current CUDA device."""
+
+    def __init__(self, dim, n, coeffs: dict, r: int, u_bc, f_bc, lo=None, hi=None, opts: dict | None = None):
+        lib = load()
+        m = Mesh()
+        m.dim = dim
+        for d in range(3):
+            m.n[d] = int(n[d]) if d < dim else 1
+            m.lo[d] = float(lo[d]) if (lo is not None and d < dim) else 0.0
+            m.hi[d] = float(hi[d]) if (hi is not None and d < dim) else 1.0
+        for f in range(6):
+            m.u_bc[f] = int(u_bc[f]) if f < 2 * dim else 0
+            m.f_bc[f] = int(f_bc[f]) if f < 2 * dim else 0
+        self.K = np.ascontiguousarray(np.asarray(coeffs["K"], dtype=np.float64))
+        co = Coeffs(coeffs["b"], coeffs["invM"], coeffs["K_dr"], coeffs["lam"], coeffs["mu"], coeffs["eta"],
+                    self.K.ctypes.data_as(C.POINTER(C.c_double)))
+        o = Opts(0, 0, 0, 0, -1.0)
+        if opts:
+            for k, v in opts.items():
+                setattr(o, k, v)
+        h = C.c_void_p()
+        rc = lib.biot_setup(C.byref(m), C.byref(co), int(r), C.byref(o), C.byref(h))
+        if rc != OK:
+            raise BiotError(rc, lib.biot_last_error(None).decode())
+        self.h = h
+        self.lib = lib
+        self.dim, self.r, self.nt = dim, r, r + 1
+        ns, nsl, nc = C.c_int64(), C.c_int64(), C.c_int64()
+        lib.biot_sizes(h, C.byref(ns), C.byref(nsl), C.byref(nc))
+        self.n_space, self.n_slab, self.n_cells = ns.value, nsl.value, nc.value
+
+    def _check(self, rc, allow=()):
+        if rc != OK and rc not in allow:
+            raise BiotError(rc, self.lib.biot_last_error(self.h).decode())
+        return rc
+
+    def destroy(self):
+        if getattr(self, "h", None):
+            self.lib.biot_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+    # --- entry points (names follow include/biot.h) ---
+    def set_permeability(self, K):
+        self.K = np.ascontiguousarray(np.asarray(K, dtype=np.float64))
+        assert self.K.size == self.n_cells
+        return self._check(self.lib.biot_set_permeability(self.h, self.K.ctypes.data_as(C.POINTER(C.c_double))))
+
+    def apply_slab(self, tau, x, y, transpose=False):
+        import torch
+        prec = FP64 if x.dtype == torch.float64 else FP32
+        dt = torch.float64 if prec == FP64 else torch.float32
+        return self._check(self.lib.biot_apply_slab(self.h, float(tau), _ptr(x, dt, self.n_slab, "x"),
+                                                    _ptr(y, dt, self.n_slab, "y"), prec, int(transpose), _stream()))
+
+    def precondition(self, tau, r, z, transpose=False):
+        import torch
+        prec = FP64 if r.dtype == torch.float64 else FP32
+        dt = torch.float64 if prec == FP64 else torch.float32
+        return self._check(self.lib.biot_precondition(self.h, float(tau), _ptr(r, dt, self.n_slab, "r"),
+                                                      _ptr(z, dt, self.n_slab, "z"), prec, int(transpose), _stream()))
+
+    def solve_slab(self, tau, rhs, x, tol=1e-10, max_iters=2000, mode=FP64, inner_tol=1e-5, transpose=False,
+                   allow_noconv=False):
+        import torch
+        st = Stats()
+        o = _solve_opts(tol, max_iters, mode, inner_tol, int(transpose))
+        rc = self.lib.biot_solve_slab(self.h, float(tau), _ptr(rhs, torch.float64, self.n_slab, "rhs"),
+                                      _ptr(x, torch.float64, self.n_slab, "x"), C.byref(o), C.byref(st), _stream())
+        self._check(rc, allow=(ENOCONV,) if allow_noconv else ())
+        return st.as_dict()
+
+    def _loads(self, f_terms, tcoef):
+        nterms = len(f_terms)
+        arr = (C.c_void_p * max(1, nterms))()
+        keep = []
+        for i, f in enumerate(f_terms):
+            if isinstance(f, np.ndarray):
+                f = np.ascontiguousarray(f, dtype=np.float64)
+                assert f.size == self.n_space
+                keep.append(f)
+                arr[i] = f.ctypes.data
+            else:
+                arr[i] = _ptr(f, None, self.n_space, "f_term").value
+                keep.append(f)
+        tc = np.ascontiguousarray(np.asarray(tcoef, dtype=np.float64).reshape(-1)) if nterms else np.zeros(4)
+        assert tc.size == 4 * max(1, nterms) or nterms == 0
+        return nterms, arr, tc, keep
+
+    def march(self, T, slabs, f_terms, tcoef, U0, U_end, X_all=None, tol=1e-10, max_iters=2000, mode=FP64,
+              inner_tol=1e-5, allow_noconv=False):
+        """U0 / U_end may be torch CUDA tensors or (pinned) CPU tensors / numpy arrays."""
+        nterms, arr, tc, keep = self._loads(f_terms, tcoef)
+        o = _solve_opts(tol, max_iters, mode, inner_tol, 0)
+        st = Stats()
+        its = (C.c_int * slabs)()
+
+        def anyptr(t, name):
+            if t is None:
+                return None
+            if isinstance(t, np.ndarray):
+                assert t.dtype == np.float64 and t.flags.c_contiguous and t.size == self.n_space, name
+                return C.c_void_p(t.ctypes.data)
+            return _ptr(t, None, self.n_space, name)
+        rc = self.lib.biot_march(self.h, float(T), int(slabs), nterms, arr, tc.ctypes.data_as(C.POINTER(C.c_double)),
+                                 anyptr(U0, "U0"), anyptr(U_end, "U_end"),
+                                 _ptr(X_all, None, None, "X_all"), C.byref(o), its, C.byref(st), _stream())
+        self._check(rc, allow=(ENOCONV,) if allow_noconv else ())
+        d = st.as_dict()
+        d["iters_per_slab"] = list(its)
+        return d
+
+    def adjoint_grad(self, T, slabs, f_terms, tcoef, U0, j_goal, dJ, tol=1e-10, max_iters=2000, mode=FP64,
+                     inner_tol=1e-5, recompute=True):
+        import torch
+        nterms, arr, tc, keep = self._loads(f_terms, tcoef)
+        o = _solve_opts(tol, max_iters, mode, inner_tol, 0)
+        J = C.c_double()
+        rc = self.lib.biot_adjoint_grad(self.h, float(T), int(slabs), nterms, arr,
+                                        tc.ctypes.data_as(C.POINTER(C.c_double)),
+                                        _ptr(U0, torch.float64, self.n_space, "U0"),
+                                        _ptr(j_goal, torch.float64, self.n_space, "j_goal"), C.byref(o),
+                                        int(bool(recompute)), C.byref(J), _ptr(dJ, torch.float64, self.n_cells, "dJ"),
+                                        _stream())
+        self._check(rc)
+        return J.value
+
+    def goal_mean_pressure(self, lo, hi, j):
+        import torch
+        lo = (C.c_double * 3)(*[float(v) for v in lo] + [0.0] * (3 - len(lo)))
+        hi = (C.c_double * 3)(*[float(v) for v in hi] + [0.0] * (3 - len(hi)))
+        return self._check(self.lib.biot_goal_mean_pressure(self.h, lo, hi, _ptr(j, torch.float64, self.n_space, "j"),
+                                                            _stream()))
+
+    def load_preset(self, kind, value, f):
+        import torch
+        return self._check(self.lib.biot_load_preset(self.h, int(kind), float(value),
+                                                     _ptr(f, torch.float64, self.n_space, "f"), _stream()))

@@ -1,0 +1,1508 @@
+// C ABI of the space-time Biot library: context set-up, slab apply, the
+// time-spectral block preconditioner, flexible GMRES, mixed-precision
+// refinement, slab marching and the adjoint gradient.
+//
+// Paper references: §Poroelasticity (the coupled system), §Discretisation in
+// Time (dG(r) slabs, marching), §Discretisation in Space (Q2 / RT1 / DGQ1),
+// §Monolithic Approach (slab block system, spectral decomposition of the time
+// matrix, diagonal blocks L_j of dG(0) type), §Preconditioning technology
+// (GMRES with truncated fixed-stress preconditioning).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/biot.h"
+#include "internal.h"
+
+using namespace biot;
+
+// ---------------------------------------------------------------------------
+// helpers
+namespace {
+
+struct Err {
+  int code;
+};
+
+#define CK(call)                                                                                 \
+  do {                                                                                           \
+    cudaError_t e_ = (call);                                                                     \
+    if (e_ != cudaSuccess) {                                                                     \
+      throw_cuda(e_, #call, __LINE__);                                                           \
+    }                                                                                            \
+  } while (0)
+
+thread_local std::string g_err_msg;
+
+[[noreturn]] void throw_cuda(cudaError_t e, const char* what, int line) {
+  char buf[512];
+  snprintf(buf, sizeof(buf), "CUDA error %s (%d) at api.cu:%d in %s", cudaGetErrorString(e), (int)e, line, what);
+  g_err_msg = buf;
+  throw Err{e == cudaErrorMemoryAllocation ? BIOT_ENOMEM : BIOT_ECUDA};
+}
+
+[[noreturn]] void fail(int code, const std::string& msg) {
+  g_err_msg = msg;
+  throw Err{code};
+}
+
+void check_launch(int line) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) throw_cuda(e, "kernel launch", line);
+}
+#define CKL() check_launch(__LINE__)
+
+template <typename T>
+T* dalloc(size_t n) {
+  void* p = nullptr;
+  if (n == 0) n = 1;
+  CK(cudaMalloc(&p, n * sizeof(T)));
+  return reinterpret_cast<T*>(p);
+}
+
+double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// ---- time basis (right-Radau Lagrange) --------------------------------------
+struct TimeBasis {
+  int nt;
+  double nodes[MAXR], w[MAXR], D[MAXR][MAXR], phi0[MAXR];
+  double V[MAXR][MAXR], W[MAXR][MAXR];  // M_t^{-1} D = V Lambda_R V^{-1};  W = V^{-1} M_t^{-1}
+  double lam[MAXR];                      // real part of the eigenvalue owning each transformed component
+};
+
+long double lagr(const long double* x, int n, int i, long double s) {
+  long double v = 1;
+  for (int j = 0; j < n; ++j)
+    if (j != i) v *= (s - x[j]) / (x[i] - x[j]);
+  return v;
+}
+long double lagr_d(const long double* x, int n, int i, long double s) {
+  long double tot = 0;
+  for (int k = 0; k < n; ++k) {
+    if (k == i) continue;
+    long double v = 1 / (x[i] - x[k]);
+    for (int j = 0; j < n; ++j)
+      if (j != i && j != k) v *= (s - x[j]) / (x[i] - x[j]);
+    tot += v;
+  }
+  return tot;
+}
+
+void invert_small(int n, const long double A[MAXR][MAXR], long double Ai[MAXR][MAXR]) {
+  long double M[MAXR][2 * MAXR];
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < 2 * n; ++j) M[i][j] = (j < n) ? A[i][j] : (j - n == i ? 1 : 0);
+  for (int c = 0; c < n; ++c) {
+    int p = c;
+    for (int i = c + 1; i < n; ++i)
+      if (std::fabs((double)M[i][c]) > std::fabs((double)M[p][c])) p = i;
+    for (int j = 0; j < 2 * n; ++j) std::swap(M[c][j], M[p][j]);
+    long double d = M[c][c];
+    for (int j = 0; j < 2 * n; ++j) M[c][j] /= d;
+    for (int i = 0; i < n; ++i)
+      if (i != c) {
+        long double f = M[i][c];
+        for (int j = 0; j < 2 * n; ++j) M[i][j] -= f * M[c][j];
+      }
+  }
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) Ai[i][j] = M[i][j + n];
+}
+
+TimeBasis make_time_basis(int r) {
+  TimeBasis tb;
+  std::memset(&tb, 0, sizeof(tb));
+  int nt = r + 1;
+  tb.nt = nt;
+  long double x[MAXR];
+  if (r == 0) x[0] = 1;
+  if (r == 1) { x[0] = 1.0L / 3; x[1] = 1; }
+  if (r == 2) { x[0] = (4 - std::sqrt(6.0L)) / 10; x[1] = (4 + std::sqrt(6.0L)) / 10; x[2] = 1; }
+  // 5-point Gauss on [0,1] (exact to degree 9)
+  const long double gx[5] = {-0.9061798459386639927976L, -0.5384693101056830910363L, 0.0L, 0.5384693101056830910363L,
+                             0.9061798459386639927976L};
+  const long double gw[5] = {0.2369268850561890875143L, 0.4786286704993664680413L, 0.5688888888888888888889L,
+                             0.4786286704993664680413L, 0.2369268850561890875143L};
+  long double M[MAXR][MAXR] = {}, D[MAXR][MAXR] = {};
+  for (int k = 0; k < nt; ++k)
+    for (int l = 0; l < nt; ++l) {
+      long double m = 0, d = 0;
+      for (int q = 0; q < 5; ++q) {
+        long double s = (gx[q] + 1) / 2, w = gw[q] / 2;
+        m += w * lagr(x, nt, l, s) * lagr(x, nt, k, s);
+        d += w * lagr_d(x, nt, l, s) * lagr(x, nt, k, s);
+      }
+      M[k][l] = m;
+      D[k][l] = d + lagr(x, nt, l, 0) * lagr(x, nt, k, 0);
+    }
+  for (int k = 0; k < nt; ++k) {
+    tb.nodes[k] = (double)x[k];
+    tb.w[k] = (double)M[k][k];
+    tb.phi0[k] = (double)lagr(x, nt, k, 0);
+    for (int l = 0; l < nt; ++l) tb.D[k][l] = (double)D[k][l];
+  }
+  // T = M^{-1} D (M diagonal)
+  typedef std::complex<long double> cx;
+  long double T[MAXR][MAXR];
+  for (int k = 0; k < nt; ++k)
+    for (int l = 0; l < nt; ++l) T[k][l] = D[k][l] / M[k][k];
+  // eigenvalues: characteristic polynomial z^n + c1 z^{n-1} + ... via Faddeev-LeVerrier
+  std::vector<cx> ev;
+  if (nt == 1) ev.push_back(T[0][0]);
+  else if (nt == 2) {
+    long double tr = T[0][0] + T[1][1], det = T[0][0] * T[1][1] - T[0][1] * T[1][0];
+    cx disc = std::sqrt(cx(tr * tr - 4 * det));
+    ev.push_back((tr + disc) / 2.0L);
+    ev.push_back((tr - disc) / 2.0L);
+  } else {
+    long double tr = T[0][0] + T[1][1] + T[2][2];
+    long double m2 = T[0][0] * T[1][1] - T[0][1] * T[1][0] + T[0][0] * T[2][2] - T[0][2] * T[2][0] + T[1][1] * T[2][2] -
+                     T[1][2] * T[2][1];
+    long double det = T[0][0] * (T[1][1] * T[2][2] - T[1][2] * T[2][1]) - T[0][1] * (T[1][0] * T[2][2] - T[1][2] * T[2][0]) +
+                      T[0][2] * (T[1][0] * T[2][1] - T[1][1] * T[2][0]);
+    // p(z) = z^3 - tr z^2 + m2 z - det ; one real root by Newton from an upper bound
+    long double z = tr + 1;
+    for (int it = 0; it < 200; ++it) {
+      long double p = ((z - tr) * z + m2) * z - det, dp = (3 * z - 2 * tr) * z + m2;
+      long double nz = z - p / dp;
+      if (std::fabs((double)(nz - z)) < 1e-30) break;
+      z = nz;
+    }
+    // deflate: z^2 + (z0 - tr) z + det/z0
+    long double bq = z - tr, cq = det / z;
+    cx disc = std::sqrt(cx(bq * bq - 4 * cq));
+    ev.push_back(z);
+    ev.push_back((-bq + disc) / 2.0L);
+    ev.push_back((-bq - disc) / 2.0L);
+  }
+  // real block form: columns of V
+  long double V[MAXR][MAXR] = {};
+  int col = 0;
+  for (size_t i = 0; i < ev.size(); ++i) {
+    cx lam = ev[i];
+    if (std::fabs((double)lam.imag()) > 1e-12 && lam.imag() < 0) continue;  // conjugate handled with its partner
+    // null vector of (T - lam I)
+    cx A[MAXR][MAXR];
+    for (int a = 0; a < nt; ++a)
+      for (int b = 0; b < nt; ++b) A[a][b] = cx(T[a][b]) - (a == b ? lam : cx(0));
+    cx v[MAXR];
+    if (nt == 1) v[0] = 1;
+    else if (nt == 2) { v[0] = A[0][1]; v[1] = -A[0][0]; if (std::abs(v[0]) + std::abs(v[1]) < 1e-20L) { v[0] = -A[1][1]; v[1] = A[1][0]; } }
+    else {  // cross product of two rows
+      v[0] = A[0][1] * A[1][2] - A[0][2] * A[1][1];
+      v[1] = A[0][2] * A[1][0] - A[0][0] * A[1][2];
+      v[2] = A[0][0] * A[1][1] - A[0][1] * A[1][0];
+    }
+    if (std::fabs((double)lam.imag()) <= 1e-12) {
+      long double nr = 0;
+      for (int a = 0; a < nt; ++a) nr += std::norm(v[a]);
+      nr = std::sqrt(nr);
+      // make real: divide by the phase of the largest entry
+      int am = 0;
+      for (int a = 1; a < nt; ++a) if (std::abs(v[a]) > std::abs(v[am])) am = a;
+      cx ph = v[am] / std::abs(v[am]);
+      for (int a = 0; a < nt; ++a) V[a][col] = (v[a] / ph).real() / nr;
+      tb.lam[col] = (double)lam.real();
+      ++col;
+    } else {
+      // T (a + ib) = (alpha + i beta)(a + ib): V = [a, b] gives block [[alpha, beta], [-beta, alpha]]
+      for (int a = 0; a < nt; ++a) { V[a][col] = v[a].real(); V[a][col + 1] = v[a].imag(); }
+      tb.lam[col] = tb.lam[col + 1] = (double)lam.real();
+      col += 2;
+    }
+  }
+  long double Vi[MAXR][MAXR];
+  invert_small(nt, V, Vi);
+  for (int a = 0; a < nt; ++a)
+    for (int b = 0; b < nt; ++b) {
+      tb.V[a][b] = (double)V[a][b];
+      tb.W[a][b] = (double)(Vi[a][b] / M[b][b]);
+    }
+  return tb;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// context
+template <typename T>
+struct LevelWork {
+  T *x = nullptr, *xo = nullptr, *d = nullptr, *Ax = nullptr, *b = nullptr;
+};
+
+struct Level {
+  Grid g;
+  TabT<double> t64;
+  TabT<float> t32;
+  double* dinv64 = nullptr;
+  float* dinv32 = nullptr;
+  double lmax = 2.0;
+  LevelWork<double> w64;
+  LevelWork<float> w32;
+};
+
+template <typename T>
+struct Krylov {
+  int m = 0;
+  std::vector<T*> V, Z;
+  const T** dV = nullptr;  // device array of basis pointers
+  T* tmp = nullptr;        // slab temporary
+};
+
+template <typename T>
+struct PrecWork {
+  T *tA = nullptr, *tB = nullptr;  // slab
+  T *fq = nullptr, *tq = nullptr;  // nt * Nq
+  T *gp = nullptr, *pp = nullptr, *pd = nullptr, *pAx = nullptr, *pxo = nullptr, *pdinv = nullptr;  // nt * Np
+  double schur_tau = -1.0;
+};
+
+struct biot_ctx {
+  Grid g;
+  int r = 0, nt = 1;
+  double b, invM, Kdr, lam, mu, eta, beta;
+  std::vector<double> Kcell;
+  TabT<double> t64;
+  TabT<float> t32;
+  double* kscale64 = nullptr;
+  float* kscale32 = nullptr;
+  double *dmq64 = nullptr, *sb2_64 = nullptr;
+  float *dmq32 = nullptr, *sb2_32 = nullptr;
+  std::vector<Level> lv;
+  double* Ainv = nullptr;
+  int ncoarse = 0;
+  TimeBasis tb;
+  biot_opts opts;
+  double schur_lmax = 0, schur_lmax_tau = -1;
+  Krylov<double> k64;
+  Krylov<float> k32;
+  PrecWork<double> p64;
+  PrecWork<float> p32;
+  void** ptrbuf = nullptr;     // device array of vector pointers for small reductions
+  void** hptr = nullptr;       // pinned staging for ptrbuf
+  double* hdev = nullptr;      // device scalars for the Krylov reductions
+  double* hhost = nullptr;     // pinned mirror
+  double* partial = nullptr;   // reduction partials
+  double* r64 = nullptr;       // FP64 slab temporaries (refinement / march)
+  double* a64 = nullptr;
+  float* d32 = nullptr;
+  float* r32 = nullptr;
+  double* lvl64 = nullptr;     // one-level temporaries
+  double* lvl64b = nullptr;
+  std::vector<void*> extra;    // other allocations
+  std::string err;
+
+  template <typename T> Krylov<T>& kry();
+  template <typename T> PrecWork<T>& pw();
+  template <typename T> const TabT<T>& tab() const;
+  template <typename T> const T* kscale() const;
+  template <typename T> const T* dmq() const;
+  template <typename T> const T* sb2() const;
+};
+template <> Krylov<double>& biot_ctx::kry<double>() { return k64; }
+template <> Krylov<float>& biot_ctx::kry<float>() { return k32; }
+template <> PrecWork<double>& biot_ctx::pw<double>() { return p64; }
+template <> PrecWork<float>& biot_ctx::pw<float>() { return p32; }
+template <> const TabT<double>& biot_ctx::tab<double>() const { return t64; }
+template <> const TabT<float>& biot_ctx::tab<float>() const { return t32; }
+template <> const double* biot_ctx::kscale<double>() const { return kscale64; }
+template <> const float* biot_ctx::kscale<float>() const { return kscale32; }
+template <> const double* biot_ctx::dmq<double>() const { return dmq64; }
+template <> const float* biot_ctx::dmq<float>() const { return dmq32; }
+template <> const double* biot_ctx::sb2<double>() const { return sb2_64; }
+template <> const float* biot_ctx::sb2<float>() const { return sb2_32; }
+
+template <typename T> LevelWork<T>& lwork(Level& L);
+template <> LevelWork<double>& lwork<double>(Level& L) { return L.w64; }
+template <> LevelWork<float>& lwork<float>(Level& L) { return L.w32; }
+template <typename T> const T* ldinv(const Level& L);
+template <> const double* ldinv<double>(const Level& L) { return L.dinv64; }
+template <> const float* ldinv<float>(const Level& L) { return L.dinv32; }
+template <typename T> const TabT<T>& ltab(const Level& L);
+template <> const TabT<double>& ltab<double>(const Level& L) { return L.t64; }
+template <> const TabT<float>& ltab<float>(const Level& L) { return L.t32; }
+
+namespace {
+
+// ---- slab coefficients ------------------------------------------------------
+SlabCoef slab_coef(const biot_ctx& c, double tau, int transpose) {
+  SlabCoef s;
+  std::memset(&s, 0, sizeof(s));
+  s.nt = c.nt;
+  s.lam = c.lam;
+  s.mu = c.mu;
+  for (int k = 0; k < c.nt; ++k) {
+    double tw = tau * c.tb.w[k];
+    s.au[k] = tw;
+    s.aq[k] = tw;
+    if (!transpose) {
+      s.ep[k][k] = -c.b * tw;
+      s.qp[k][k] = -tw;
+      s.pq[k] = tw;
+      for (int l = 0; l < c.nt; ++l) {
+        s.pu[k][l] = c.b * c.tb.D[k][l];
+        s.pp[k][l] = c.invM * c.tb.D[k][l];
+      }
+    } else {
+      s.qp[k][k] = tw;
+      s.pq[k] = -tw;
+      s.pu[k][k] = -c.b * tw;
+      for (int l = 0; l < c.nt; ++l) {
+        s.ep[k][l] = c.b * c.tb.D[l][k];
+        s.pp[k][l] = c.invM * c.tb.D[l][k];
+      }
+    }
+  }
+  return s;
+}
+
+template <typename T>
+void apply_slab_T(biot_ctx& c, double tau, const T* x, T* y, int transpose, cudaStream_t st) {
+  SlabCoef sc = slab_coef(c, tau, transpose);
+  const Grid& g = c.g;
+  launch_apply_u<T>(g, c.tab<T>(), sc, x, g.N, x + g.offp, g.N, y, g.N, st);
+  CKL();
+  launch_apply_q<T>(g, c.tab<T>(), sc, c.kscale<T>(), x, g.N, y, g.N, st);
+  CKL();
+  launch_apply_p<T>(g, c.tab<T>(), sc, x, g.N, y, g.N, st);
+  CKL();
+}
+
+// tau A x on one MG level, nrhs vectors of stride Nu
+template <typename T>
+void apply_A(const Level& L, double lam, double mu, double tau, const T* x, T* y, int nrhs, cudaStream_t st) {
+  SlabCoef sc;
+  std::memset(&sc, 0, sizeof(sc));
+  sc.nt = nrhs;
+  sc.lam = lam;
+  sc.mu = mu;
+  for (int k = 0; k < nrhs; ++k) sc.au[k] = tau;
+  launch_apply_u<T>(L.g, ltab<T>(L), sc, x, L.g.Nu, nullptr, 0, y, L.g.Nu, st);
+  CKL();
+}
+
+// ---- workspace -------------------------------------------------------------------
+template <typename T>
+void ensure_prec(biot_ctx& c) {
+  PrecWork<T>& w = c.pw<T>();
+  if (w.tA) return;
+  const Grid& g = c.g;
+  const int nt = c.nt;
+  int64_t nqt = g.nq[0] + g.nq[1] + g.nq[2];
+  w.tA = dalloc<T>(nt * g.N);
+  w.tB = dalloc<T>(nt * g.N);
+  w.fq = dalloc<T>(nt * nqt);
+  w.tq = dalloc<T>(nt * nqt);
+  w.gp = dalloc<T>(nt * g.Np);
+  w.pp = dalloc<T>(nt * g.Np);
+  w.pd = dalloc<T>(nt * g.Np);
+  w.pAx = dalloc<T>(nt * g.Np);
+  w.pxo = dalloc<T>(nt * g.Np);
+  w.pdinv = dalloc<T>(nt * g.Np);
+  for (Level& L : c.lv) {
+    LevelWork<T>& lw = lwork<T>(L);
+    int64_t n = (int64_t)nt * L.g.Nu;
+    lw.x = dalloc<T>(n);
+    lw.xo = dalloc<T>(n);
+    lw.d = dalloc<T>(n);
+    lw.Ax = dalloc<T>(n);
+    lw.b = dalloc<T>(n);
+  }
+}
+
+template <typename T>
+void ensure_krylov(biot_ctx& c, int m) {
+  Krylov<T>& K = c.kry<T>();
+  if (K.m >= m) return;
+  for (T* p : K.V) cudaFree(p);
+  for (T* p : K.Z) cudaFree(p);
+  if (K.dV) cudaFree((void*)K.dV);
+  if (K.tmp) cudaFree(K.tmp);
+  K.V.clear();
+  K.Z.clear();
+  const int64_t n = c.g.N * c.nt;
+  for (int i = 0; i <= m; ++i) K.V.push_back(dalloc<T>(n));
+  for (int i = 0; i < m; ++i) K.Z.push_back(dalloc<T>(n));
+  K.tmp = dalloc<T>(n);
+  K.dV = (const T**)dalloc<T*>(2 * m + 1);
+  std::vector<T*> ptrs(K.V.begin(), K.V.end());
+  ptrs.insert(ptrs.end(), K.Z.begin(), K.Z.end());
+  CK(cudaMemcpy((void*)K.dV, ptrs.data(), ptrs.size() * sizeof(T*), cudaMemcpyHostToDevice));
+  K.m = m;
+}
+
+double dev_dot(biot_ctx& c, const double* a, const double* b, int64_t n, cudaStream_t st) {
+  // the pointer goes through pinned host memory so the copy is stream ordered
+  c.hptr[0] = (void*)a;
+  CK(cudaMemcpyAsync(c.ptrbuf, c.hptr, sizeof(void*), cudaMemcpyHostToDevice, st));
+  launch_multidot<double>(reinterpret_cast<const double* const*>(c.ptrbuf), 1, b, n, c.partial, c.hdev + 100, st);
+  CKL();
+  CK(cudaMemcpyAsync(c.hhost + 100, c.hdev + 100, sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return c.hhost[100];
+}
+
+// ---- Chebyshev smoothing -----------------------------------------------------
+struct ChebCoef {
+  int n;
+  double c1[32], c2[32];
+};
+ChebCoef cheb_coefs(int degree, double lmin, double lmax) {
+  ChebCoef cc;
+  cc.n = degree;
+  double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin), sigma = theta / delta;
+  double rho_old = 1.0 / sigma;
+  cc.c1[0] = 0.0;
+  cc.c2[0] = 1.0 / theta;
+  for (int k = 1; k < degree && k < 32; ++k) {
+    double rho = 1.0 / (2.0 * sigma - rho_old);
+    cc.c1[k] = rho * rho_old;
+    cc.c2[k] = 2.0 * rho / delta;
+    rho_old = rho;
+  }
+  return cc;
+}
+
+// smooth tau A x = b on level l; x_in_zero: start from 0.  Result pointer in w.x.
+template <typename T>
+void smooth(biot_ctx& c, Level& L, double tau, int nrhs, bool zero_start, cudaStream_t st) {
+  LevelWork<T>& w = lwork<T>(L);
+  ChebCoef cc = cheb_coefs(c.opts.cheb_degree, L.lmax / 20.0, 1.1 * L.lmax);
+  const int64_t n = L.g.Nu;
+  for (int k = 0; k < cc.n; ++k) {
+    bool first = (k == 0 && zero_start);
+    if (!first) apply_A<T>(L, c.lam, c.mu, tau, w.x, w.Ax, nrhs, st);
+    launch_cheb_update<T>(w.b, w.Ax, ldinv<T>(L), w.d, w.x, w.xo, cc.c1[k], cc.c2[k] / tau, first ? 1 : 0, n, nrhs, n, st);
+    CKL();
+    std::swap(w.x, w.xo);
+  }
+}
+
+// V-cycle on levels[0..]: b in lv[0].w.b, result in lv[0].w.x
+template <typename T>
+void vcycle(biot_ctx& c, double tau, int nrhs, cudaStream_t st) {
+  const int nl = (int)c.lv.size();
+  for (int l = 0; l < nl - 1; ++l) {
+    Level& L = c.lv[l];
+    LevelWork<T>& w = lwork<T>(L);
+    smooth<T>(c, L, tau, nrhs, true, st);
+    apply_A<T>(L, c.lam, c.mu, tau, w.x, w.Ax, nrhs, st);
+    launch_axpby<T>(w.Ax, w.b, 1.0, -1.0, L.g.Nu * nrhs, st);  // residual in Ax
+    CKL();
+    Level& C = c.lv[l + 1];
+    launch_restrict<T>(L.g, C.g, w.Ax, L.g.Nu, lwork<T>(C).b, C.g.Nu, nrhs, st);
+    CKL();
+  }
+  Level& Lc = c.lv[nl - 1];
+  if (c.Ainv) {
+    launch_dense_gemv<T>(c.Ainv, c.ncoarse, lwork<T>(Lc).b, Lc.g.Nu, lwork<T>(Lc).x, Lc.g.Nu, nrhs, 1.0 / tau, st);
+    CKL();
+  } else {
+    smooth<T>(c, Lc, tau, nrhs, true, st);
+  }
+  for (int l = nl - 2; l >= 0; --l) {
+    Level& L = c.lv[l];
+    Level& C = c.lv[l + 1];
+    launch_prolong_add<T>(L.g, C.g, lwork<T>(C).x, C.g.Nu, lwork<T>(L).x, L.g.Nu, nrhs, st);
+    CKL();
+    smooth<T>(c, L, tau, nrhs, false, st);
+  }
+}
+
+// ---- flux-pressure Schur complement ---------------------------------------------
+template <typename T>
+void schur_apply(biot_ctx& c, double tau, const double* cm, const T* p, T* out, int nrhs, cudaStream_t st) {
+  PrecWork<T>& w = c.pw<T>();
+  const Grid& g = c.g;
+  int64_t nqt = g.nq[0] + g.nq[1] + g.nq[2];
+  launch_schur_apply<T>(g, c.tab<T>(), p, g.Np, c.dmq<T>(), w.tq, nqt, tau, cm, out, g.Np, nrhs, st);
+  CKL();
+}
+
+void schur_cm(const biot_ctx& c, double* cm) {
+  for (int k = 0; k < c.nt; ++k) cm[k] = c.tb.lam[k] * (c.invM + c.beta);
+}
+
+// largest eigenvalue of Dinv Shat (power iteration in FP64 on every rhs, max over rhs),
+// cached per tau
+double schur_lmax(biot_ctx& c, double tau, cudaStream_t st) {
+  if (c.schur_lmax_tau == tau) return c.schur_lmax;
+  ensure_prec<double>(c);
+  PrecWork<double>& w = c.p64;
+  const Grid& g = c.g;
+  double cm[MAXR];
+  schur_cm(c, cm);
+  launch_schur_dinv<double>(g, c.t64, c.sb2_64, cm, tau, w.pdinv, c.nt, st);
+  CKL();
+  std::vector<double> h(g.Np * c.nt);
+  for (int64_t i = 0; i < (int64_t)h.size(); ++i) h[i] = 1.0 + 0.37 * std::sin(0.7 * (double)i);
+  CK(cudaMemcpyAsync(w.gp, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+  CK(cudaStreamSynchronize(st));
+  double lm = 1.0;
+  for (int it = 0; it < 25; ++it) {
+    schur_apply<double>(c, tau, cm, w.gp, w.pAx, c.nt, st);
+    launch_cheb_update_r<double>(w.pAx, w.pAx, w.pdinv, w.pd, w.pAx, w.pp, 0.0, 1.0, 1, g.Np, c.nt, st);  // pp = Dinv S gp
+    CKL();
+    lm = 0;
+    for (int r = 0; r < c.nt; ++r) {
+      double ny = std::sqrt(dev_dot(c, w.pp + r * g.Np, w.pp + r * g.Np, g.Np, st));
+      double nx = std::sqrt(dev_dot(c, w.gp + r * g.Np, w.gp + r * g.Np, g.Np, st));
+      lm = std::max(lm, ny / nx);
+      launch_axpby<double>(w.gp + r * g.Np, w.pp + r * g.Np, 1.0 / ny, 0.0, g.Np, st);
+      CKL();
+    }
+  }
+  c.schur_lmax = lm;
+  c.schur_lmax_tau = tau;
+  return lm;
+}
+
+// p = Shat^{-1} g by Chebyshev-Jacobi (w.gp -> w.pp)
+template <typename T>
+void schur_solve(biot_ctx& c, double tau, cudaStream_t st) {
+  PrecWork<T>& w = c.pw<T>();
+  const Grid& g = c.g;
+  double cm[MAXR];
+  schur_cm(c, cm);
+  double lmax = schur_lmax(c, tau, st);
+  if (w.schur_tau != tau) {
+    launch_schur_dinv<T>(g, c.tab<T>(), c.sb2<T>(), cm, tau, w.pdinv, c.nt, st);
+    CKL();
+    w.schur_tau = tau;
+  }
+  ChebCoef cc = cheb_coefs(c.opts.schur_degree, lmax / 30.0, 1.05 * lmax);
+  for (int k = 0; k < cc.n; ++k) {
+    bool first = (k == 0);
+    if (!first) schur_apply<T>(c, tau, cm, w.pp, w.pAx, c.nt, st);
+    launch_cheb_update_r<T>(w.gp, w.pAx, w.pdinv, w.pd, w.pp, w.pxo, cc.c1[k], cc.c2[k], first ? 1 : 0, g.Np, c.nt, st);
+    CKL();
+    std::swap(w.pp, w.pxo);
+  }
+}
+
+template <typename T>
+void copy2d(T* dst, int64_t dpitch, const T* src, int64_t spitch, int64_t width, int rows, cudaStream_t st) {
+  CK(cudaMemcpy2DAsync(dst, dpitch * sizeof(T), src, spitch * sizeof(T), width * sizeof(T), rows, cudaMemcpyDeviceToDevice, st));
+}
+
+// z = P r  (or P^T r)
+template <typename T>
+void precondition_T(biot_ctx& c, double tau, const T* R, T* Z, int transpose, cudaStream_t st) {
+  PrecWork<T>& w = c.pw<T>();
+  const Grid& g = c.g;
+  const int nt = c.nt;
+  const int64_t N = g.N, Nu = g.Nu, Np = g.Np;
+  const int64_t nqt = g.nq[0] + g.nq[1] + g.nq[2];
+  Level& L0 = c.lv[0];
+  LevelWork<T>& lw = lwork<T>(L0);
+  double Wm[MAXR * MAXR], Vm[MAXR * MAXR];
+  for (int a = 0; a < nt; ++a)
+    for (int b = 0; b < nt; ++b) {
+      Wm[a * nt + b] = transpose ? c.tb.V[b][a] : c.tb.W[a][b];
+      Vm[a * nt + b] = transpose ? c.tb.W[b][a] : c.tb.V[a][b];
+    }
+  launch_time_mix<T, T>(R, N, w.tA, N, nt, Wm, N, st);
+  CKL();
+  if (!transpose) {
+    launch_q_jacobi<T>(g, c.tab<T>(), w.tA + Nu, N, c.dmq<T>(), tau, w.fq, nqt, nt, st);
+    CKL();
+    launch_p_minus_Bq<T>(g, c.tab<T>(), w.tA + g.offp, N, w.fq, nqt, tau, w.gp, Np, nt, st);
+    CKL();
+    schur_solve<T>(c, tau, st);
+    launch_q_final<T>(g, c.tab<T>(), w.tA + Nu, N, w.pp, Np, c.dmq<T>(), tau, tau, w.tB + Nu, N, nt, st);
+    CKL();
+    copy2d<T>(w.tB + g.offp, N, w.pp, Np, Np, nt, st);
+    launch_u_rhs<T>(g, c.tab<T>(), w.tA, N, w.pp, Np, c.b * tau, lw.b, Nu, nt, st);
+    CKL();
+    vcycle<T>(c, tau, nt, st);
+    copy2d<T>(w.tB, N, lw.x, Nu, Nu, nt, st);
+  } else {
+    copy2d<T>(lw.b, Nu, w.tA, N, Nu, nt, st);
+    vcycle<T>(c, tau, nt, st);
+    copy2d<T>(w.tB, N, lw.x, Nu, Nu, nt, st);
+    launch_p_plus_ETu<T>(g, c.tab<T>(), w.tA + g.offp, N, lw.x, Nu, c.b * tau, w.gp, Np, nt, st);
+    CKL();
+    launch_q_jacobi<T>(g, c.tab<T>(), w.tA + Nu, N, c.dmq<T>(), tau, w.fq, nqt, nt, st);
+    CKL();
+    launch_p_minus_Bq<T>(g, c.tab<T>(), w.gp, Np, w.fq, nqt, -tau, w.gp, Np, nt, st);
+    CKL();
+    schur_solve<T>(c, tau, st);
+    launch_q_final<T>(g, c.tab<T>(), w.tA + Nu, N, w.pp, Np, c.dmq<T>(), tau, -tau, w.tB + Nu, N, nt, st);
+    CKL();
+    copy2d<T>(w.tB + g.offp, N, w.pp, Np, Np, nt, st);
+  }
+  launch_time_mix<T, T>(w.tB, N, Z, N, nt, Vm, N, st);
+  CKL();
+}
+
+// ---- flexible GMRES(m), right preconditioned -------------------------------------
+// Solves calA x = b (precision T) to ||b - calA x|| <= tol_abs.  Returns BIOT_OK,
+// BIOT_ENOCONV or BIOT_EBREAKDOWN.
+template <typename T>
+int gmres(biot_ctx& c, double tau, int transpose, const T* b, T* x, double tol_abs, int maxit, int& iters, int& restarts,
+          double& resnorm, cudaStream_t st) {
+  const int m = c.opts.gmres_restart;
+  ensure_krylov<T>(c, m);
+  ensure_prec<T>(c);
+  Krylov<T>& K = c.kry<T>();
+  const int64_t n = c.g.N * c.nt;
+  std::vector<double> H((m + 1) * m), cs(m), sn(m), gv(m + 1), y(m);
+  double* hd = c.hdev;  // [0..m]: h1, [64..64+m]: h2, [128]: norm^2
+  auto norm2 = [&](T* v) -> double {
+    // ||V_0||^2 (K.dV[0] == V_0 == v)
+    launch_multidot<T>(K.dV, 1, v, n, c.partial, hd + 128, st);
+    CKL();
+    CK(cudaMemcpyAsync(c.hhost + 128, hd + 128, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return c.hhost[128];
+  };
+  // r0 = b - A x
+  apply_slab_T<T>(c, tau, x, K.V[0], transpose, st);
+  launch_axpby<T>(K.V[0], b, 1.0, -1.0, n, st);
+  CKL();
+  double beta = std::sqrt(norm2(K.V[0]));
+  resnorm = beta;
+  while (true) {
+    if (!std::isfinite(beta)) return BIOT_EBREAKDOWN;
+    if (beta <= tol_abs) return BIOT_OK;
+    if (iters >= maxit) return BIOT_ENOCONV;
+    launch_axpby<T>(K.V[0], K.V[0], 0.0, 1.0 / beta, n, st);
+    CKL();
+    std::fill(gv.begin(), gv.end(), 0.0);
+    gv[0] = beta;
+    int jl = -1;
+    bool done = false;
+    for (int j = 0; j < m; ++j) {
+      precondition_T<T>(c, tau, K.V[j], K.Z[j], transpose, st);
+      apply_slab_T<T>(c, tau, K.Z[j], K.V[j + 1], transpose, st);
+      T* w = K.V[j + 1];
+      launch_multidot<T>(K.dV, j + 1, w, n, c.partial, hd, st);
+      CKL();
+      launch_multiaxpy_dot<T>(K.dV, j + 1, hd, w, n, 1, c.partial, hd + 64, st);
+      CKL();
+      launch_multiaxpy_dot<T>(K.dV, j + 1, hd + 64, w, n, 2, c.partial, hd + 128, st);
+      CKL();
+      CK(cudaMemcpyAsync(c.hhost, hd, 130 * sizeof(double), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      for (int i = 0; i <= j; ++i) H[i * m + j] = c.hhost[i] + c.hhost[64 + i];
+      double hn = std::sqrt(std::max(c.hhost[128], 0.0));
+      if (!std::isfinite(hn)) return BIOT_EBREAKDOWN;
+      H[(j + 1) * m + j] = hn;
+      if (hn > 0) {
+        launch_axpby<T>(w, w, 0.0, 1.0 / hn, n, st);
+        CKL();
+      }
+      for (int i = 0; i < j; ++i) {
+        double a = H[i * m + j], bb = H[(i + 1) * m + j];
+        H[i * m + j] = cs[i] * a + sn[i] * bb;
+        H[(i + 1) * m + j] = -sn[i] * a + cs[i] * bb;
+      }
+      double a = H[j * m + j], bb = H[(j + 1) * m + j];
+      double rr = std::hypot(a, bb);
+      cs[j] = (rr > 0) ? a / rr : 1.0;
+      sn[j] = (rr > 0) ? bb / rr : 0.0;
+      H[j * m + j] = rr;
+      H[(j + 1) * m + j] = 0.0;
+      gv[j + 1] = -sn[j] * gv[j];
+      gv[j] = cs[j] * gv[j];
+      ++iters;
+      jl = j;
+      if (std::fabs(gv[j + 1]) <= tol_abs || iters >= maxit || hn == 0.0) { done = true; break; }
+    }
+    // y = H^{-1} g
+    for (int i = jl; i >= 0; --i) {
+      double s = gv[i];
+      for (int k = i + 1; k <= jl; ++k) s -= H[i * m + k] * y[k];
+      y[i] = s / H[i * m + i];
+    }
+    CK(cudaMemcpyAsync(hd + 160, y.data(), (jl + 1) * sizeof(double), cudaMemcpyHostToDevice, st));
+    launch_lincomb_add<T, T>(x, K.dV + (m + 1), jl + 1, hd + 160, n, st);
+    CKL();
+    // true residual
+    apply_slab_T<T>(c, tau, x, K.V[0], transpose, st);
+    launch_axpby<T>(K.V[0], b, 1.0, -1.0, n, st);
+    CKL();
+    beta = std::sqrt(norm2(K.V[0]));
+    resnorm = beta;
+    ++restarts;
+    (void)done;
+  }
+}
+
+// ---- slab solve ---------------------------------------------------------------------
+int solve_slab_impl(biot_ctx& c, double tau, const double* rhs, double* x, const biot_solve_opts& o, biot_stats& s,
+                    cudaStream_t st) {
+  double t0 = now_s();
+  const int64_t n = c.g.N * c.nt;
+  int iters = 0, restarts = 0, refs = 0;
+  double res = 0;
+  int rc = BIOT_OK;
+  // ||b||
+  double bn = std::sqrt(dev_dot(c, rhs, rhs, n, st));
+  if (!std::isfinite(bn)) fail(BIOT_EINVAL, "non-finite right-hand side");
+  if (bn == 0.0) {
+    CK(cudaMemsetAsync(x, 0, n * sizeof(double), st));
+    s = biot_stats{0, 0, 0, 0.0, now_s() - t0};
+    return BIOT_OK;
+  }
+  if (o.mode == BIOT_FP64) {
+    rc = gmres<double>(c, tau, o.transpose, rhs, x, o.tol * bn, o.max_iters, iters, restarts, res, st);
+  } else {
+    if (!c.r64) c.r64 = dalloc<double>(n);
+    if (!c.d32) c.d32 = dalloc<float>(n);
+    if (!c.r32) c.r32 = dalloc<float>(n);
+    while (true) {
+      apply_slab_T<double>(c, tau, x, c.r64, o.transpose, st);
+      launch_axpby<double>(c.r64, rhs, 1.0, -1.0, n, st);
+      CKL();
+      double rn = std::sqrt(dev_dot(c, c.r64, c.r64, n, st));
+      res = rn;
+      if (!std::isfinite(rn)) { rc = BIOT_EBREAKDOWN; break; }
+      if (rn <= o.tol * bn) { rc = BIOT_OK; break; }
+      if (iters >= o.max_iters || refs >= 50) { rc = BIOT_ENOCONV; break; }
+      launch_axpby<double>(c.r64, c.r64, 0.0, 1.0 / rn, n, st);
+      launch_convert<double, float>(c.r64, c.r32, n, st);
+      CK(cudaMemsetAsync(c.d32, 0, n * sizeof(float), st));
+      CKL();
+      int it_in = 0, rs_in = 0;
+      double res_in = 0;
+      int budget = std::min(o.max_iters - iters, 3 * c.opts.gmres_restart);
+      int rci = gmres<float>(c, tau, o.transpose, c.r32, c.d32, o.inner_tol, budget, it_in, rs_in, res_in, st);
+      iters += it_in;
+      restarts += rs_in;
+      if (rci == BIOT_EBREAKDOWN) { rc = rci; break; }
+      launch_add_scaled<double, float>(x, c.d32, rn, n, st);
+      CKL();
+      ++refs;
+    }
+  }
+  s.iterations = iters;
+  s.restarts = restarts;
+  s.refinements = refs;
+  s.rel_residual = res / bn;
+  CK(cudaStreamSynchronize(st));
+  s.seconds = now_s() - t0;
+  return rc;
+}
+
+// ---- multigrid set-up ----------------------------------------------------------------
+double power_lmax_A(biot_ctx& c, Level& L, cudaStream_t st) {
+  // power iteration on Dinv A (FP64, one vector); uses the level's FP64 work arrays
+  LevelWork<double>& w = L.w64;
+  int64_t n = L.g.Nu;
+  std::vector<double> h(n);
+  for (int64_t i = 0; i < n; ++i) h[i] = 1.0 + 0.5 * std::sin(0.37 * (double)i + 0.1);
+  CK(cudaMemcpy(w.x, h.data(), n * sizeof(double), cudaMemcpyHostToDevice));
+  launch_mask_u<double>(L.g, w.x, 0, 1, st);
+  double lm = 1.0;
+  for (int it = 0; it < 30; ++it) {
+    apply_A<double>(L, c.lam, c.mu, 1.0, w.x, w.Ax, 1, st);
+    // xo = Dinv Ax (zero on constrained rows via first-step form with b = Ax)
+    launch_cheb_update<double>(w.Ax, w.Ax, L.dinv64, w.d, w.x, w.xo, 0.0, 1.0, 1, n, 1, n, st);
+    CKL();
+    // constrained rows copied b = Ax = x there: zero them for the estimate
+    launch_mask_u<double>(L.g, w.xo, 0, 1, st);
+    double nn = std::sqrt(dev_dot(c, w.xo, w.xo, n, st));
+    double nx = std::sqrt(dev_dot(c, w.x, w.x, n, st));
+    lm = nn / nx;
+    launch_axpby<double>(w.x, w.xo, 1.0 / nn, 0.0, n, st);
+    CKL();
+  }
+  return lm;
+}
+
+void build_levels(biot_ctx& c, cudaStream_t st) {
+  Grid g = c.g;
+  int minc = std::max(1, c.opts.mg_min_cells);
+  c.lv.clear();
+  while (true) {
+    Level L;
+    L.g = g;
+    build_tables(g, L.t64);
+    L.t32 = cast_tables<float>(L.t64);
+    c.lv.push_back(L);
+    bool can = true;
+    for (int d = 0; d < g.dim; ++d)
+      if (g.n[d] % 2 != 0 || g.n[d] / 2 < minc) can = false;
+    if (!can) break;
+    g = coarsen(g);
+  }
+  for (Level& L : c.lv) {
+    int64_t n = L.g.Nu;
+    L.dinv64 = dalloc<double>(n);
+    L.dinv32 = dalloc<float>(n);
+    launch_diag_A<double>(L.g, L.t64, c.lam, c.mu, L.dinv64, st);
+    CKL();
+    // invert (constrained -> 0)
+    std::vector<double> h(n);
+    CK(cudaMemcpy(h.data(), L.dinv64, n * sizeof(double), cudaMemcpyDeviceToHost));
+    std::vector<double> hm(n, 1.0);
+    {
+      // constraint flags from a masked vector of ones
+      double* ones = dalloc<double>(L.g.N);
+      std::vector<double> o(L.g.N, 1.0);
+      CK(cudaMemcpy(ones, o.data(), L.g.N * sizeof(double), cudaMemcpyHostToDevice));
+      launch_mask<double>(L.g, ones, L.g.N, 1, st);
+      CKL();
+      CK(cudaMemcpy(hm.data(), ones, n * sizeof(double), cudaMemcpyDeviceToHost));
+      cudaFree(ones);
+    }
+    std::vector<float> hf(n);
+    for (int64_t i = 0; i < n; ++i) {
+      h[i] = hm[i] != 0.0 ? 1.0 / h[i] : 0.0;
+      hf[i] = (float)h[i];
+    }
+    CK(cudaMemcpy(L.dinv64, h.data(), n * sizeof(double), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(L.dinv32, hf.data(), n * sizeof(float), cudaMemcpyHostToDevice));
+  }
+  ensure_prec<double>(c);
+  for (Level& L : c.lv) L.lmax = power_lmax_A(c, L, st);
+  // dense coarse inverse when the coarsest level is small
+  Level& Lc = c.lv.back();
+  int64_t nc = Lc.g.Nu;
+  c.Ainv = nullptr;
+  c.ncoarse = 0;
+  if (nc <= 4000) {
+    std::vector<double> A(nc * nc);
+    double* e = dalloc<double>(3 * nc);
+    double* ae = dalloc<double>(3 * nc);
+    std::vector<double> eh(3 * nc), aeh(3 * nc);
+    for (int64_t j0 = 0; j0 < nc; j0 += 3) {
+      int cnt = (int)std::min<int64_t>(3, nc - j0);
+      std::fill(eh.begin(), eh.end(), 0.0);
+      for (int k = 0; k < cnt; ++k) eh[k * nc + j0 + k] = 1.0;
+      CK(cudaMemcpy(e, eh.data(), 3 * nc * sizeof(double), cudaMemcpyHostToDevice));
+      apply_A<double>(Lc, c.lam, c.mu, 1.0, e, ae, cnt, st);
+      CK(cudaMemcpy(aeh.data(), ae, 3 * nc * sizeof(double), cudaMemcpyDeviceToHost));
+      for (int k = 0; k < cnt; ++k)
+        for (int64_t i = 0; i < nc; ++i) A[i * nc + j0 + k] = aeh[k * nc + i];
+    }
+    cudaFree(e);
+    cudaFree(ae);
+    // Cholesky-based inverse in long double
+    std::vector<long double> Lm(nc * nc, 0.0L);
+    for (int64_t i = 0; i < nc; ++i)
+      for (int64_t j = 0; j <= i; ++j) {
+        long double s = 0.5L * ((long double)A[i * nc + j] + (long double)A[j * nc + i]);
+        for (int64_t k = 0; k < j; ++k) s -= Lm[i * nc + k] * Lm[j * nc + k];
+        if (i == j) {
+          if (s <= 0) fail(BIOT_EINVAL, "coarse elasticity matrix is not positive definite (check boundary conditions)");
+          Lm[i * nc + i] = std::sqrt(s);
+        } else
+          Lm[i * nc + j] = s / Lm[j * nc + j];
+      }
+    // inverse of L (lower), then A^{-1} = L^{-T} L^{-1}
+    std::vector<long double> Li(nc * nc, 0.0L);
+    for (int64_t j = 0; j < nc; ++j) {
+      Li[j * nc + j] = 1.0L / Lm[j * nc + j];
+      for (int64_t i = j + 1; i < nc; ++i) {
+        long double s = 0;
+        for (int64_t k = j; k < i; ++k) s -= Lm[i * nc + k] * Li[k * nc + j];
+        Li[i * nc + j] = s / Lm[i * nc + i];
+      }
+    }
+    std::vector<double> Ai(nc * nc);
+    for (int64_t i = 0; i < nc; ++i)
+      for (int64_t j = 0; j <= i; ++j) {
+        long double s = 0;
+        for (int64_t k = i; k < nc; ++k) s += Li[k * nc + i] * Li[k * nc + j];
+        Ai[i * nc + j] = Ai[j * nc + i] = (double)s;
+      }
+    c.Ainv = dalloc<double>(nc * nc);
+    CK(cudaMemcpy(c.Ainv, Ai.data(), nc * nc * sizeof(double), cudaMemcpyHostToDevice));
+    c.ncoarse = (int)nc;
+  }
+}
+
+void set_permeability(biot_ctx& c, const double* K, cudaStream_t st) {
+  const int64_t nc = c.g.ncells;
+  std::vector<double> ks(nc);
+  std::vector<float> kf(nc);
+  for (int64_t i = 0; i < nc; ++i) {
+    if (!(K[i] > 0.0) || !std::isfinite(K[i])) fail(BIOT_EINVAL, "permeability must be positive and finite");
+    ks[i] = c.eta / K[i];
+    kf[i] = (float)ks[i];
+  }
+  c.Kcell.assign(K, K + nc);
+  CK(cudaMemcpy(c.kscale64, ks.data(), nc * sizeof(double), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(c.kscale32, kf.data(), nc * sizeof(float), cudaMemcpyHostToDevice));
+  launch_diag_Mq<double>(c.g, c.t64, c.kscale64, c.dmq64, st);
+  launch_diag_Mq<float>(c.g, c.t32, c.kscale32, c.dmq32, st);
+  launch_diag_BDBt<double>(c.g, c.t64, c.dmq64, c.sb2_64, st);
+  launch_diag_BDBt<float>(c.g, c.t32, c.dmq32, c.sb2_32, st);
+  CKL();
+  CK(cudaStreamSynchronize(st));
+  c.schur_lmax_tau = -1;
+  c.p64.schur_tau = -1;
+  c.p32.schur_tau = -1;
+}
+
+// ---- loads ---------------------------------------------------------------------------
+// time integrals c[k][m] = tau int_0^1 g_m(t0 + tau s) l_k(s) ds (6-point Gauss, exact for the cubic profiles)
+void time_load_coefs(const biot_ctx& c, double t0, double tau, int nterms, const double* tcoef, double* out) {
+  static const double gx[6] = {-0.9324695142031521, -0.6612093864662645, -0.2386191860831969,
+                               0.2386191860831969, 0.6612093864662645, 0.9324695142031521};
+  static const double gw[6] = {0.1713244923791704, 0.3607615730481386, 0.4679139345726910,
+                               0.4679139345726910, 0.3607615730481386, 0.1713244923791704};
+  long double x[MAXR];
+  for (int k = 0; k < c.nt; ++k) x[k] = c.tb.nodes[k];
+  for (int k = 0; k < c.nt; ++k)
+    for (int m = 0; m < nterms; ++m) {
+      double s = 0;
+      for (int q = 0; q < 6; ++q) {
+        double sq = 0.5 * (gx[q] + 1.0), w = 0.5 * gw[q];
+        double t = t0 + tau * sq;
+        const double* a = tcoef + 4 * m;
+        double gm = a[0] + t * (a[1] + t * (a[2] + t * a[3]));
+        s += w * gm * (double)lagr(x, c.nt, k, sq);
+      }
+      out[k * nterms + m] = tau * s;
+    }
+}
+
+struct MarchBufs {
+  std::vector<double*> f;
+  const double** fdev = nullptr;
+  double* U = nullptr;
+  double* SU = nullptr;  // one level
+  double* rhs = nullptr;
+  double* X = nullptr;
+};
+
+void march_prepare(biot_ctx& c, int nterms, const double* const* f_terms, const double* U0, MarchBufs& mb, cudaStream_t st) {
+  const Grid& g = c.g;
+  if (nterms < 0 || nterms > 8) fail(BIOT_EINVAL, "nterms must be in 0..8");
+  for (int m = 0; m < nterms; ++m) {
+    double* d = dalloc<double>(g.N);
+    if (!f_terms[m]) fail(BIOT_EINVAL, "NULL load term");
+    CK(cudaMemcpyAsync(d, f_terms[m], g.N * sizeof(double), is_device_ptr(f_terms[m]) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    launch_mask<double>(g, d, g.N, 1, st);
+    CKL();
+    mb.f.push_back(d);
+  }
+  mb.fdev = (const double**)dalloc<double*>(std::max(1, nterms));
+  if (nterms) CK(cudaMemcpyAsync((void*)mb.fdev, mb.f.data(), nterms * sizeof(double*), cudaMemcpyHostToDevice, st));
+  mb.U = dalloc<double>(g.N);
+  if (U0) CK(cudaMemcpyAsync(mb.U, U0, g.N * sizeof(double), is_device_ptr(U0) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+  else CK(cudaMemsetAsync(mb.U, 0, g.N * sizeof(double), st));
+  mb.SU = dalloc<double>(g.N);
+  mb.rhs = dalloc<double>(g.N * c.nt);
+  mb.X = dalloc<double>(g.N * c.nt);
+  CK(cudaStreamSynchronize(st));
+}
+
+void march_free(MarchBufs& mb) {
+  for (double* p : mb.f) cudaFree(p);
+  cudaFree((void*)mb.fdev);
+  cudaFree(mb.U);
+  cudaFree(mb.SU);
+  cudaFree(mb.rhs);
+  cudaFree(mb.X);
+}
+
+// rhs of slab n from the loads and the jump term of the state mb.U
+void build_slab_rhs(biot_ctx& c, double t0, double tau, int nterms, const double* tcoef, MarchBufs& mb, cudaStream_t st) {
+  const Grid& g = c.g;
+  SlabCoef s;
+  std::memset(&s, 0, sizeof(s));
+  s.nt = 1;
+  s.pu[0][0] = c.b;
+  s.pp[0][0] = c.invM;
+  launch_apply_p<double>(g, c.t64, s, mb.U, g.N, mb.SU, g.N, st);
+  CKL();
+  std::vector<double> coef(c.nt * std::max(1, nterms), 0.0);
+  if (nterms) time_load_coefs(c, t0, tau, nterms, tcoef, coef.data());
+  launch_slab_rhs(g, mb.fdev, nterms, coef.data(), c.tb.phi0, c.nt, mb.SU + g.offp, mb.rhs, st);
+  CKL();
+}
+
+void march_impl(biot_ctx& c, double T, int slabs, int nterms, const double* const* f_terms, const double* tcoef,
+                const double* U0, double* U_end, double* X_all, double* ckpt, const biot_solve_opts& o, int* iters,
+                biot_stats& st_out, cudaStream_t st, int& rc_out) {
+  double t_start = now_s();
+  const Grid& g = c.g;
+  MarchBufs mb;
+  march_prepare(c, nterms, f_terms, U0, mb, st);
+  const double tau = T / slabs;
+  biot_stats tot{0, 0, 0, 0.0, 0.0};
+  rc_out = BIOT_OK;
+  for (int nsl = 0; nsl < slabs; ++nsl) {
+    if (ckpt) CK(cudaMemcpyAsync(ckpt + (int64_t)nsl * g.N, mb.U, g.N * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    build_slab_rhs(c, nsl * tau, tau, nterms, tcoef, mb, st);
+    for (int k = 0; k < c.nt; ++k) CK(cudaMemcpyAsync(mb.X + k * g.N, mb.U, g.N * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    biot_stats s;
+    int rc = solve_slab_impl(c, tau, mb.rhs, mb.X, o, s, st);
+    if (rc != BIOT_OK && rc_out == BIOT_OK) rc_out = rc;
+    tot.iterations += s.iterations;
+    tot.refinements += s.refinements;
+    tot.restarts += s.restarts;
+    tot.rel_residual = std::max(tot.rel_residual, s.rel_residual);
+    if (iters) iters[nsl] = s.iterations;
+    if (X_all) CK(cudaMemcpyAsync(X_all + (int64_t)nsl * g.N * c.nt, mb.X, g.N * c.nt * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(mb.U, mb.X + (int64_t)(c.nt - 1) * g.N, g.N * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  }
+  if (ckpt) CK(cudaMemcpyAsync(ckpt + (int64_t)slabs * g.N, mb.U, g.N * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  if (U_end) CK(cudaMemcpyAsync(U_end, mb.U, g.N * sizeof(double), is_device_ptr(U_end) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  march_free(mb);
+  tot.seconds = now_s() - t_start;
+  st_out = tot;
+}
+
+biot_solve_opts solve_defaults(const biot_solve_opts* o) {
+  biot_solve_opts d;
+  d.tol = 1e-10;
+  d.max_iters = 2000;
+  d.mode = BIOT_FP64;
+  d.inner_tol = 1e-5;
+  d.transpose = 0;
+  if (o) {
+    d = *o;
+    if (d.tol <= 0) d.tol = 1e-10;
+    if (d.max_iters <= 0) d.max_iters = 2000;
+    if (d.inner_tol <= 0) d.inner_tol = 1e-5;
+  }
+  if (d.mode != BIOT_FP64 && d.mode != BIOT_MIXED) fail(BIOT_EINVAL, "solve mode must be BIOT_FP64 or BIOT_MIXED");
+  return d;
+}
+
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// exported entry points
+#define API_BEGIN(ctx)         \
+  try {                        \
+    if (!(ctx)) { g_err_msg = "NULL context"; return BIOT_EINVAL; }
+#define API_END(ctx)                                  \
+  }                                                   \
+  catch (const Err& e) {                              \
+    (ctx)->err = g_err_msg;                           \
+    return e.code;                                    \
+  }                                                   \
+  catch (const std::exception& e) {                   \
+    (ctx)->err = e.what();                            \
+    return BIOT_ENOMEM;                               \
+  }
+
+extern "C" int biot_setup(const biot_mesh* mesh, const biot_coeffs* co, int r, const biot_opts* opts, biot_t* out) {
+  if (!out || !mesh || !co) return BIOT_EINVAL;
+  *out = nullptr;
+  biot_ctx* c = new biot_ctx();
+  try {
+    if (mesh->dim != 2 && mesh->dim != 3) fail(BIOT_EINVAL, "dim must be 2 or 3");
+    for (int d = 0; d < mesh->dim; ++d) {
+      if (mesh->n[d] < 1) fail(BIOT_EINVAL, "n must be >= 1");
+      if (!(mesh->hi[d] > mesh->lo[d])) fail(BIOT_EINVAL, "hi must exceed lo");
+    }
+    for (int f = 0; f < 2 * mesh->dim; ++f) {
+      if (mesh->u_bc[f] < 0 || mesh->u_bc[f] > 2) fail(BIOT_EINVAL, "bad u_bc code");
+      if (mesh->f_bc[f] < 0 || mesh->f_bc[f] > 1) fail(BIOT_EINVAL, "bad f_bc code");
+    }
+    if (r < 0 || r > 2) fail(BIOT_EINVAL, "r must be 0, 1 or 2");
+    if (!(co->b > 0 && co->b < 1)) fail(BIOT_EINVAL, "b must lie in (0, 1)");
+    if (!(co->invM >= 0) || !(co->K_dr > 0) || !(co->mu > 0) || !(co->lambda >= 0) || !(co->eta > 0))
+      fail(BIOT_EINVAL, "coefficients out of range");
+    if (!co->K_cell) fail(BIOT_EINVAL, "K_cell is NULL");
+    c->g = make_grid(mesh->dim, mesh->n, mesh->lo, mesh->hi, mesh->u_bc, mesh->f_bc);
+    c->r = r;
+    c->nt = r + 1;
+    c->b = co->b;
+    c->invM = co->invM;
+    c->Kdr = co->K_dr;
+    c->lam = co->lambda;
+    c->mu = co->mu;
+    c->eta = co->eta;
+    biot_opts d;
+    d.gmres_restart = 30;
+    d.cheb_degree = 4;
+    d.schur_degree = 8;
+    d.mg_min_cells = 2;
+    d.beta_fs = -1;
+    if (opts) {
+      if (opts->gmres_restart > 0) d.gmres_restart = std::min(opts->gmres_restart, 60);
+      if (opts->cheb_degree > 0) d.cheb_degree = std::min(opts->cheb_degree, 30);
+      if (opts->schur_degree > 0) d.schur_degree = std::min(opts->schur_degree, 30);
+      if (opts->mg_min_cells > 0) d.mg_min_cells = opts->mg_min_cells;
+      d.beta_fs = opts->beta_fs;
+    }
+    c->opts = d;
+    c->beta = (d.beta_fs > 0) ? d.beta_fs : c->b * c->b / c->Kdr;
+    build_tables(c->g, c->t64);
+    c->t32 = cast_tables<float>(c->t64);
+    c->tb = make_time_basis(r);
+    const Grid& g = c->g;
+    int64_t nqt = g.nq[0] + g.nq[1] + g.nq[2];
+    c->kscale64 = dalloc<double>(g.ncells);
+    c->kscale32 = dalloc<float>(g.ncells);
+    c->dmq64 = dalloc<double>(nqt);
+    c->dmq32 = dalloc<float>(nqt);
+    c->sb2_64 = dalloc<double>(g.Np);
+    c->sb2_32 = dalloc<float>(g.Np);
+    c->hdev = dalloc<double>(512);
+    c->ptrbuf = dalloc<void*>(64);
+    CK(cudaMallocHost((void**)&c->hptr, 64 * sizeof(void*)));
+    CK(cudaMallocHost((void**)&c->hhost, 512 * sizeof(double)));
+    c->partial = dalloc<double>(RED_BLOCKS * 16);
+    c->lvl64 = dalloc<double>(g.N);
+    c->lvl64b = dalloc<double>(g.N);
+    cudaStream_t st = 0;
+    set_permeability(*c, co->K_cell, st);
+    build_levels(*c, st);
+    CK(cudaDeviceSynchronize());
+  } catch (const Err& e) {
+    biot_destroy(c);
+    return e.code;
+  } catch (const std::exception& e) {
+    g_err_msg = e.what();
+    biot_destroy(c);
+    return BIOT_ENOMEM;
+  }
+  *out = c;
+  return BIOT_OK;
+}
+
+extern "C" int biot_sizes(biot_t c, int64_t* n_space, int64_t* n_slab, int64_t* n_cells) {
+  if (!c) return BIOT_EINVAL;
+  if (n_space) *n_space = c->g.N;
+  if (n_slab) *n_slab = c->g.N * c->nt;
+  if (n_cells) *n_cells = c->g.ncells;
+  return BIOT_OK;
+}
+
+extern "C" int biot_set_permeability(biot_t c, const double* K) {
+  API_BEGIN(c)
+  if (!K) fail(BIOT_EINVAL, "K is NULL");
+  set_permeability(*c, K, 0);
+  return BIOT_OK;
+  API_END(c)
+}
+
+extern "C" int biot_apply_slab(biot_t c, double tau, const void* x, void* y, int prec, int transpose, void* stream) {
+  API_BEGIN(c)
+  if (!x || !y || !(tau > 0)) fail(BIOT_EINVAL, "apply_slab: NULL vector or tau <= 0");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (prec == BIOT_FP64) apply_slab_T<double>(*c, tau, (const double*)x, (double*)y, transpose, st);
+  else if (prec == BIOT_FP32) apply_slab_T<float>(*c, tau, (const float*)x, (float*)y, transpose, st);
+  else fail(BIOT_EINVAL, "prec must be BIOT_FP64 or BIOT_FP32");
+  return BIOT_OK;
+  API_END(c)
+}
+
+extern "C" int biot_precondition(biot_t c, double tau, const void* r, void* z, int prec, int transpose, void* stream) {
+  API_BEGIN(c)
+  if (!r || !z || !(tau > 0)) fail(BIOT_EINVAL, "precondition: NULL vector or tau <= 0");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (prec == BIOT_FP64) {
+    ensure_prec<double>(*c);
+    precondition_T<double>(*c, tau, (const double*)r, (double*)z, transpose, st);
+  } else if (prec == BIOT_FP32) {
+    ensure_prec<float>(*c);
+    precondition_T<float>(*c, tau, (const float*)r, (float*)z, transpose, st);
+  } else
+    fail(BIOT_EINVAL, "prec must be BIOT_FP64 or BIOT_FP32");
+  return BIOT_OK;
+  API_END(c)
+}
+
+extern "C" int biot_solve_slab(biot_t c, double tau, const double* rhs, double* x, const biot_solve_opts* opts, biot_stats* stats,
+                               void* stream) {
+  API_BEGIN(c)
+  if (!rhs || !x || !(tau > 0)) fail(BIOT_EINVAL, "solve_slab: NULL vector or tau <= 0");
+  biot_solve_opts o = solve_defaults(opts);
+  biot_stats s{0, 0, 0, 0.0, 0.0};
+  int rc = solve_slab_impl(*c, tau, rhs, x, o, s, (cudaStream_t)stream);
+  if (stats) *stats = s;
+  if (rc != BIOT_OK) c->err = (rc == BIOT_ENOCONV) ? "iteration limit reached" : "breakdown (non-finite values)";
+  return rc;
+  API_END(c)
+}
+
+extern "C" int biot_march(biot_t c, double T, int slabs, int nterms, const double* const* f_terms, const double* tcoef,
+                          const double* U0, double* U_end, double* X_all, const biot_solve_opts* opts, int* iters_per_slab,
+                          biot_stats* stats, void* stream) {
+  API_BEGIN(c)
+  if (!(T > 0) || slabs < 1) fail(BIOT_EINVAL, "march: T must be > 0 and slabs >= 1");
+  if (nterms > 0 && (!f_terms || !tcoef)) fail(BIOT_EINVAL, "march: load terms missing");
+  biot_solve_opts o = solve_defaults(opts);
+  biot_stats s{0, 0, 0, 0.0, 0.0};
+  int rc = BIOT_OK;
+  march_impl(*c, T, slabs, nterms, f_terms, tcoef, U0, U_end, X_all, nullptr, o, iters_per_slab, s, (cudaStream_t)stream, rc);
+  if (stats) *stats = s;
+  return rc;
+  API_END(c)
+}
+
+extern "C" int biot_adjoint_grad(biot_t c, double T, int slabs, int nterms, const double* const* f_terms, const double* tcoef,
+                                 const double* U0, const double* j_goal, const biot_solve_opts* opts, int recompute,
+                                 double* J_out, double* dJ, void* stream) {
+  API_BEGIN(c)
+  if (!(T > 0) || slabs < 1 || !j_goal || !dJ) fail(BIOT_EINVAL, "adjoint_grad: bad arguments");
+  cudaStream_t st = (cudaStream_t)stream;
+  biot_solve_opts o = solve_defaults(opts);
+  const Grid& g = c->g;
+  const int nt = c->nt;
+  const int64_t ns = g.N * nt;
+  const double tau = T / slabs;
+  // forward march with end-state checkpoints (and all slabs when not recomputing)
+  double* ck = dalloc<double>((int64_t)(slabs + 1) * g.N);
+  double* Xall = recompute ? nullptr : dalloc<double>((int64_t)slabs * ns);
+  biot_stats s;
+  int rc = BIOT_OK;
+  march_impl(*c, T, slabs, nterms, f_terms, tcoef, U0, nullptr, Xall, ck, o, nullptr, s, st, rc);
+  double J = dev_dot(*c, j_goal, ck + (int64_t)slabs * g.N, g.N, st);
+  if (J_out) *J_out = J;
+  CK(cudaMemsetAsync(dJ, 0, g.ncells * sizeof(double), st));
+  MarchBufs mb;
+  march_prepare(*c, nterms, f_terms, nullptr, mb, st);
+  double* Z = dalloc<double>(ns);
+  double* zr = dalloc<double>(ns);
+  double* tmp = dalloc<double>(g.N);
+  double* zero = dalloc<double>(g.N);
+  CK(cudaMemsetAsync(zero, 0, g.N * sizeof(double), st));
+  // terminal adjoint rhs: level r gets j
+  CK(cudaMemsetAsync(zr, 0, ns * sizeof(double), st));
+  CK(cudaMemcpyAsync(zr + (int64_t)(nt - 1) * g.N, j_goal, g.N * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  launch_mask<double>(g, zr, g.N, nt, st);
+  biot_solve_opts oa = o;
+  oa.transpose = 1;
+  double mp = 1.0;
+  for (int d = 0; d < g.dim; ++d) mp *= c->t64.wg[d];
+  for (int nsl = slabs - 1; nsl >= 0; --nsl) {
+    const double* X;
+    if (recompute) {
+      CK(cudaMemcpyAsync(mb.U, ck + (int64_t)nsl * g.N, g.N * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      build_slab_rhs(*c, nsl * tau, tau, nterms, tcoef, mb, st);
+      for (int k = 0; k < nt; ++k) CK(cudaMemcpyAsync(mb.X + k * g.N, mb.U, g.N * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      biot_stats s2;
+      int rc2 = solve_slab_impl(*c, tau, mb.rhs, mb.X, o, s2, st);
+      if (rc2 != BIOT_OK && rc == BIOT_OK) rc = rc2;
+      X = mb.X;
+    } else {
+      X = Xall + (int64_t)nsl * ns;
+    }
+    CK(cudaMemsetAsync(Z, 0, ns * sizeof(double), st));
+    biot_stats s3;
+    int rc3 = solve_slab_impl(*c, tau, zr, Z, oa, s3, st);
+    if (rc3 != BIOT_OK && rc == BIOT_OK) rc = rc3;
+    for (int k = 0; k < nt; ++k) {
+      launch_grad_pair(g, c->t64, c->kscale64, Z + k * g.N, X + k * g.N, tau * c->tb.w[k], dJ, st);
+      CKL();
+    }
+    if (nsl > 0) {
+      // next rhs: level r = M S^T (sum_k phi_k(0) Z_k), others 0
+      CK(cudaMemsetAsync(tmp, 0, g.N * sizeof(double), st));
+      for (int k = 0; k < nt; ++k) launch_axpby<double>(tmp, Z + k * g.N, c->tb.phi0[k], 1.0, g.N, st);
+      CKL();
+      CK(cudaMemsetAsync(zr, 0, ns * sizeof(double), st));
+      double* zl = zr + (int64_t)(nt - 1) * g.N;
+      launch_u_rhs<double>(g, c->t64, zero, g.N, tmp + g.offp, g.N, c->b, zl, g.N, 1, st);
+      launch_axpby<double>(zl + g.offp, tmp + g.offp, c->invM * mp, 0.0, g.Np, st);
+      CKL();
+    }
+  }
+  CK(cudaStreamSynchronize(st));
+  march_free(mb);
+  cudaFree(Z);
+  cudaFree(zr);
+  cudaFree(tmp);
+  cudaFree(zero);
+  cudaFree(ck);
+  if (Xall) cudaFree(Xall);
+  return rc;
+  API_END(c)
+}
+
+extern "C" int biot_goal_mean_pressure(biot_t c, const double* lo, const double* hi, double* j, void* stream) {
+  API_BEGIN(c)
+  if (!lo || !hi || !j) fail(BIOT_EINVAL, "goal: NULL argument");
+  const Grid& g = c->g;
+  std::vector<double> h(g.N, 0.0);
+  double vol = 1.0;
+  for (int d = 0; d < g.dim; ++d) {
+    if (!(hi[d] > lo[d])) fail(BIOT_EINVAL, "goal box is empty");
+    vol *= hi[d] - lo[d];
+  }
+  const double gs[2] = {0.5 - std::sqrt(3.0) / 6.0, 0.5 + std::sqrt(3.0) / 6.0};
+  // int over [sa, sb] (reference) of the Gauss-point Lagrange function psi_q
+  auto psi_int = [&](int q, double sa, double sb) {
+    double mid = 0.5 * (sa + sb);
+    double v = (q == 0) ? (mid - gs[1]) / (gs[0] - gs[1]) : (mid - gs[0]) / (gs[1] - gs[0]);
+    return v * (sb - sa);
+  };
+  for (int64_t cid = 0; cid < g.ncells; ++cid) {
+    int cell[3] = {(int)(cid % g.n[0]), (int)((cid / g.n[0]) % g.n[1]), (int)(cid / ((int64_t)g.n[0] * g.n[1]))};
+    double I[3][2];
+    bool inside = true;
+    for (int d = 0; d < 3; ++d) {
+      if (d >= g.dim) { I[d][0] = 1; I[d][1] = 0; continue; }
+      double a = std::max(lo[d], cell[d] * g.h[d]), b = std::min(hi[d], (cell[d] + 1) * g.h[d]);
+      if (!(b > a)) { inside = false; break; }
+      double sa = a / g.h[d] - cell[d], sb = b / g.h[d] - cell[d];
+      for (int q = 0; q < 2; ++q) I[d][q] = psi_int(q, sa, sb) * g.h[d];
+    }
+    if (!inside) continue;
+    for (int qz = 0; qz < (g.dim == 3 ? 2 : 1); ++qz)
+      for (int qy = 0; qy < 2; ++qy)
+        for (int qx = 0; qx < 2; ++qx) {
+          int64_t idx = g.offp + ((int64_t)(2 * cell[2] + qz) * g.ng[1] + (2 * cell[1] + qy)) * g.ng[0] + 2 * cell[0] + qx;
+          double v = I[0][qx] * I[1][qy] * (g.dim == 3 ? I[2][qz] : 1.0);
+          h[idx] += v / vol;
+        }
+  }
+  CK(cudaMemcpyAsync(j, h.data(), g.N * sizeof(double), cudaMemcpyHostToDevice, (cudaStream_t)stream));
+  CK(cudaStreamSynchronize((cudaStream_t)stream));
+  return BIOT_OK;
+  API_END(c)
+}
+
+extern "C" int biot_load_preset(biot_t c, int kind, double value, double* f, void* stream) {
+  API_BEGIN(c)
+  if (!f) fail(BIOT_EINVAL, "load: NULL output");
+  const Grid& g = c->g;
+  std::vector<double> h(g.N, 0.0);
+  const double PI = 3.14159265358979323846;
+  auto q2 = [](int a, double s) {
+    return a == 0 ? 2 * (s - 0.5) * (s - 1) : (a == 1 ? 4 * s * (1 - s) : 2 * s * (s - 0.5));
+  };
+  const double gs[2] = {0.5 - std::sqrt(3.0) / 6.0, 0.5 + std::sqrt(3.0) / 6.0};
+  auto gl = [&](int q, double s) { return q == 0 ? (s - gs[1]) / (gs[0] - gs[1]) : (s - gs[0]) / (gs[1] - gs[0]); };
+  static const double g4x[4] = {0.0694318442029737, 0.3300094782075719, 0.6699905217924281, 0.9305681557970263};
+  static const double g4w[4] = {0.1739274225687269, 0.3260725774312731, 0.3260725774312731, 0.1739274225687269};
+  if (kind == BIOT_LOAD_TRACTION_TOP) {
+    int d = g.dim - 1;
+    int top = 2 * d + 1;
+    if (g.ubc[top] != U_NATURAL) fail(BIOT_EINVAL, "top face is not a traction face");
+    // -value * int_top phi_node ds on component d
+    int iz = g.nu[d] - 1;
+    for (int64_t node = 0; node < g.nnode; ++node) {
+      int ix = (int)(node % g.nu[0]);
+      int iy = (int)((node / g.nu[0]) % g.nu[1]);
+      int iw = (int)(node / ((int64_t)g.nu[0] * g.nu[1]));
+      int idx[3] = {ix, iy, iw};
+      if (idx[d] != iz) continue;
+      double w = 1.0;
+      for (int e = 0; e < g.dim; ++e) {
+        if (e == d) continue;
+        int m = idx[e];
+        double one;
+        if (m & 1) one = 2.0 / 3.0;
+        else one = ((m > 0) ? 1.0 / 6.0 : 0.0) + ((m < g.nu[e] - 1) ? 1.0 / 6.0 : 0.0);
+        w *= one * g.h[e];
+      }
+      h[d * g.nnode + node] = -value * w;
+    }
+  } else if (kind == BIOT_LOAD_MMS2D_CONST || kind == BIOT_LOAD_MMS2D_LINEAR) {
+    if (g.dim != 2) fail(BIOT_EINVAL, "MMS preset is 2-D");
+    const double b = c->b, invM = c->invM, mu = c->mu, lam = c->lam;
+    const double kov = c->Kcell[0] / c->eta;
+    const bool lin = (kind == BIOT_LOAD_MMS2D_LINEAR);
+    for (int cy = 0; cy < g.n[1]; ++cy)
+      for (int cx = 0; cx < g.n[0]; ++cx)
+        for (int qy = 0; qy < 4; ++qy)
+          for (int qx = 0; qx < 4; ++qx) {
+            double sx = g4x[qx], sy = g4x[qy];
+            double x = (cx + sx) * g.h[0], y = (cy + sy) * g.h[1];
+            double W = g4w[qx] * g4w[qy] * g.h[0] * g.h[1];
+            double S = std::sin(PI * x) * std::sin(PI * y), C = std::cos(PI * x) * std::cos(PI * y);
+            double fu[2] = {0, 0}, fp;
+            if (lin) {
+              double cxy = std::cos(PI * (x + y));
+              fu[0] = 2 * mu * PI * PI * S - (mu + lam) * PI * PI * cxy - b * PI * std::sin(PI * x) * std::cos(PI * y);
+              fu[1] = 2 * mu * PI * PI * S - (mu + lam) * PI * PI * cxy - b * PI * std::cos(PI * x) * std::sin(PI * y);
+              fp = 2 * PI * PI * kov * C;
+            } else {
+              fp = b * PI * std::sin(PI * (x + y)) + invM * C;
+            }
+            for (int ay = 0; ay < 3; ++ay)
+              for (int ax = 0; ax < 3; ++ax) {
+                double ph = q2(ax, sx) * q2(ay, sy) * W;
+                int64_t node = (int64_t)(2 * cy + ay) * g.nu[0] + 2 * cx + ax;
+                h[node] += fu[0] * ph;
+                h[g.nnode + node] += fu[1] * ph;
+              }
+            for (int gy = 0; gy < 2; ++gy)
+              for (int gx = 0; gx < 2; ++gx) {
+                int64_t idx = g.offp + (int64_t)(2 * cy + gy) * g.ng[0] + 2 * cx + gx;
+                h[idx] += fp * gl(gx, sx) * gl(gy, sy) * W;
+              }
+          }
+    if (lin) {
+      // natural pressure: -<p_exact, z.n> with p_exact = C t on every natural-flow face
+      for (int f = 0; f < 4; ++f) {
+        if (g.fbc[f] != F_NATURAL) continue;
+        int dn = f / 2, side = f % 2;
+        int dt = 1 - dn;
+        double nsign = side ? 1.0 : -1.0;
+        int ia = side ? g.nu[dn] - 1 : 0;  // along-normal index of the face DoFs
+        for (int ct = 0; ct < g.n[dt]; ++ct)
+          for (int q = 0; q < 4; ++q) {
+            double s = g4x[q];
+            double xt = (ct + s) * g.h[dt];
+            double xn = side ? 1.0 * g.n[dn] * g.h[dn] : 0.0;
+            double x = dn == 0 ? xn : xt, y = dn == 0 ? xt : xn;
+            double pD = std::cos(PI * x) * std::cos(PI * y);
+            double W = g4w[q] * g.h[dt];
+            for (int gq = 0; gq < 2; ++gq) {
+              // q component dn: grid (along dn: nu, across: ng)
+              int64_t it = 2 * ct + gq;
+              int64_t local = (dn == 0) ? (it * g.nu[0] + ia) : ((int64_t)ia * g.ng[0] + it);
+              h[g.offq[dn] + local] += -pD * nsign * gl(gq, s) * W;
+            }
+          }
+      }
+    }
+  } else {
+    fail(BIOT_EINVAL, "unknown load preset");
+  }
+  CK(cudaMemcpyAsync(f, h.data(), g.N * sizeof(double), cudaMemcpyHostToDevice, (cudaStream_t)stream));
+  CK(cudaStreamSynchronize((cudaStream_t)stream));
+  return BIOT_OK;
+  API_END(c)
+}
+
+extern "C" const char* biot_last_error(biot_t c) {
+  if (!c) return g_err_msg.c_str();
+  return c->err.c_str();
+}
+
+extern "C" void biot_destroy(biot_t c) {
+  if (!c) return;
+  auto F = [](void* p) { if (p) cudaFree(p); };
+  F(c->kscale64); F(c->kscale32); F(c->dmq64); F(c->dmq32); F(c->sb2_64); F(c->sb2_32);
+  F(c->hdev); F(c->partial); F(c->r64); F(c->a64); F(c->d32); F(c->r32); F(c->lvl64); F(c->lvl64b); F(c->Ainv);
+  if (c->hhost) cudaFreeHost(c->hhost);
+  if (c->hptr) cudaFreeHost(c->hptr);
+  F(c->ptrbuf);
+  for (Level& L : c->lv) {
+    F(L.dinv64); F(L.dinv32);
+    F(L.w64.x); F(L.w64.xo); F(L.w64.d); F(L.w64.Ax); F(L.w64.b);
+    F(L.w32.x); F(L.w32.xo); F(L.w32.d); F(L.w32.Ax); F(L.w32.b);
+  }
+  auto FK = [&](auto& K) {
+    for (auto p : K.V) F(p);
+    for (auto p : K.Z) F(p);
+    F((void*)K.dV); F(K.tmp);
+  };
+  FK(c->k64); FK(c->k32);
+  auto FP = [&](auto& w) { F(w.tA); F(w.tB); F(w.fq); F(w.tq); F(w.gp); F(w.pp); F(w.pd); F(w.pAx); F(w.pxo); F(w.pdinv); };
+  FP(c->p64); FP(c->p32);
+  for (void* p : c->extra) F(p);
+  delete c;
+}

@@ -1,0 +1,482 @@
+// Matrix-free slab operator kernels (paper §Monolithic Approach: the coupled
+// operator of all r+1 temporal DoFs of one slab, D (x) S + tau M_t (x) A_s).
+//
+//  * apply_u : displacement rows.  The elasticity block is applied by global sum
+//    factorisation: A = sum of 21 (3-D) / 8 (2-D) Kronecker products of banded
+//    1-D Q2 matrices, evaluated tile by tile in shared memory in three passes
+//    (z, then y, then x).  The E p coupling is gathered from the neighbouring
+//    cells' Gauss-point pressures.
+//  * apply_q : flux rows, Darcy mass with the cellwise eta/K_c and B^T p.
+//  * apply_p : pressure rows, E^T u (storage of the volumetric strain),
+//    Mp p and B q.
+// Every output DoF is computed by exactly one thread (gather form): no atomics,
+// bitwise reproducible.
+#include "internal.h"
+
+namespace biot {
+
+// ---------------------------------------------------------------------------
+// elasticity term tables: out comp i += coef * X_i(Y(Z(u_j)))
+// ops: 0 M, 1 K, 2 G, 3 G^T ; coef: 0 -> 2mu+lam, 1 -> mu, 2 -> lam
+struct Term3 { int j, i, xop, yop, zop, coef; };
+__constant__ Term3 c_terms3[21] = {
+    // output x
+    {0, 0, 1, 0, 0, 0}, {0, 0, 0, 1, 0, 1}, {0, 0, 0, 0, 1, 1},
+    {1, 0, 2, 3, 0, 1}, {2, 0, 2, 0, 3, 1}, {1, 0, 3, 2, 0, 2}, {2, 0, 3, 0, 2, 2},
+    // output y
+    {1, 1, 1, 0, 0, 1}, {1, 1, 0, 1, 0, 0}, {1, 1, 0, 0, 1, 1}, {2, 1, 0, 2, 3, 1}, {2, 1, 0, 3, 2, 2},
+    {0, 1, 3, 2, 0, 1}, {0, 1, 2, 3, 0, 2},
+    // output z
+    {2, 2, 1, 0, 0, 1}, {2, 2, 0, 0, 1, 0}, {2, 2, 0, 1, 0, 1}, {1, 2, 0, 3, 2, 1}, {1, 2, 0, 2, 3, 2},
+    {0, 2, 3, 0, 2, 1}, {0, 2, 2, 0, 3, 2}};
+
+struct Term2 { int j, i, xop, yop, coef; };
+__constant__ Term2 c_terms2[8] = {
+    {0, 0, 1, 0, 0}, {0, 0, 0, 1, 1}, {1, 0, 2, 3, 1}, {1, 0, 3, 2, 2},
+    {1, 1, 1, 0, 1}, {1, 1, 0, 1, 0}, {0, 1, 3, 2, 1}, {0, 1, 2, 3, 2}};
+
+constexpr int T3 = 8;            // output tile edge (nodes), 3-D
+constexpr int H3 = T3 + 4;       // with halo
+constexpr int T2 = 16;           // output tile edge, 2-D
+constexpr int H2 = T2 + 4;
+
+template <typename T>
+__device__ inline T tap5(const T* c, const T* v, int stride) {
+  return c[0] * v[0] + c[1] * v[stride] + c[2] * v[2 * stride] + c[3] * v[3 * stride] + c[4] * v[4 * stride];
+}
+
+// E p gathered at Q2 node (ix,iy,iz), component c, for one pressure level.
+template <typename T, int DIM>
+__device__ inline T gather_Ep(const Grid& g, const TabT<T>& tb, const T* __restrict__ p, int c, int ix, int iy, int iz) {
+  int idx[3] = {ix, iy, iz};
+  int pi[3][4];
+  T pc[3][4];
+  int cnt[3];
+  for (int d = 0; d < 3; ++d) {
+    int k = 0;
+    if (d < DIM) {
+      int m = idx[d];
+      const T(*tab)[2] = (d == c) ? tb.bd[d] : tb.bv[d];
+      if (m & 1) {
+        int j = m >> 1;
+        for (int q = 0; q < 2; ++q) { pi[d][k] = 2 * j + q; pc[d][k] = tab[1][q]; ++k; }
+      } else {
+        int j = m >> 1;
+        if (j >= 1) for (int q = 0; q < 2; ++q) { pi[d][k] = 2 * (j - 1) + q; pc[d][k] = tab[2][q]; ++k; }
+        if (j < g.n[d]) for (int q = 0; q < 2; ++q) { pi[d][k] = 2 * j + q; pc[d][k] = tab[0][q]; ++k; }
+      }
+    } else {
+      pi[d][0] = 0; pc[d][0] = T(1); k = 1;
+    }
+    cnt[d] = k;
+  }
+  T acc = 0;
+  for (int a = 0; a < cnt[2]; ++a)
+    for (int b = 0; b < cnt[1]; ++b) {
+      T cab = pc[2][a] * pc[1][b];
+      const T* row = p + ((int64_t)pi[2][a] * g.ng[1] + pi[1][b]) * g.ng[0];
+      T s = 0;
+      for (int e = 0; e < cnt[0]; ++e) s += pc[0][e] * row[pi[0][e]];
+      acc += cab * s;
+    }
+  return acc;
+}
+
+// ---------------------------------------------------------------------------
+// 3-D displacement rows.  grid: (tiles_x, tiles_y, tiles_z); 256 threads.
+// u_in: nt levels of [u_0|u_1|u_2] at stride su; p_in (may be null): nt levels at stride sp;
+// y: nt levels at stride sy.  Y_k = au[k] A u_k + E(sum_l ep[k][l] p_l) on free rows, u_k on constrained rows.
+template <typename T>
+__global__ void __launch_bounds__(256) k_apply_u3(Grid g, TabT<T> tb, SlabCoef sc, const T* __restrict__ u_in, int64_t su,
+                                                  const T* __restrict__ p_in, int64_t sp, T* __restrict__ y, int64_t sy) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* s_in = reinterpret_cast<T*>(smem_raw);           // 3 * H3^3
+  T* s_zo = s_in + 3 * H3 * H3 * H3;                    // 4 * H3*H3*T3
+  T* s_px = s_zo + 4 * H3 * H3 * T3;                    // 12 * H3*T3*T3
+  __shared__ T s_tab[3][4][4][5];
+  const int tid = threadIdx.x, nth = blockDim.x;
+  for (int i = tid; i < 3 * 4 * 4 * 5; i += nth) (&s_tab[0][0][0][0])[i] = (&tb.q2[0][0][0][0])[i];
+  const int X0 = blockIdx.x * T3, Y0 = blockIdx.y * T3, Z0 = blockIdx.z * T3;
+  const int ex = min(T3, g.nu[0] - X0), ey = min(T3, g.nu[1] - Y0), ez = min(T3, g.nu[2] - Z0);
+  const T cf[3] = {T(2.0 * sc.mu + sc.lam), T(sc.mu), T(sc.lam)};
+  const int64_t nn = g.nnode;
+  // region sizes
+  const int rx = ex + 4, ry = ey + 4, rz = ez + 4;
+  for (int k = 0; k < sc.nt; ++k) {
+    const T* u = u_in + k * su;
+    __syncthreads();
+    // load masked input region
+    for (int i = tid; i < 3 * rx * ry * rz; i += nth) {
+      int c = i / (rx * ry * rz);
+      int rem = i - c * rx * ry * rz;
+      int lz = rem / (rx * ry);
+      rem -= lz * rx * ry;
+      int ly = rem / rx, lx = rem - ly * rx;
+      int gx = X0 + lx - 2, gy = Y0 + ly - 2, gz = Z0 + lz - 2;
+      T v = 0;
+      if (gx >= 0 && gx < g.nu[0] && gy >= 0 && gy < g.nu[1] && gz >= 0 && gz < g.nu[2] && u_free(g, c, gx, gy, gz))
+        v = u[c * nn + ((int64_t)gz * g.nu[1] + gy) * g.nu[0] + gx];
+      s_in[c * H3 * H3 * H3 + (lz * H3 + ly) * H3 + lx] = v;
+    }
+    for (int i = tid; i < 12 * H3 * T3 * T3; i += nth) s_px[i] = 0;
+    for (int j = 0; j < 3; ++j) {
+      __syncthreads();
+      // z pass: zo[op][z][y][x] over x < rx, y < ry, z < ez
+      const T* in = s_in + j * H3 * H3 * H3;
+      for (int i = tid; i < rx * ry * ez; i += nth) {
+        int lz = i / (rx * ry);
+        int rem = i - lz * rx * ry;
+        int ly = rem / rx, lx = rem - ly * rx;
+        int rt = rowtype(Z0 + lz, g.nu[2]);
+        const T* v = in + (lz * H3 + ly) * H3 + lx;  // taps at lz..lz+4 (offset -2..2 around lz+2)
+        for (int op = 0; op < 4; ++op) s_zo[op * H3 * H3 * T3 + (lz * H3 + ly) * H3 + lx] = tap5(s_tab[2][op][rt], v, H3 * H3);
+      }
+      __syncthreads();
+      // y pass: accumulate into px[(i,xop)][z][y][x] over x < rx, y < ey, z < ez
+      for (int i = tid; i < rx * ey * ez; i += nth) {
+        int lz = i / (rx * ey);
+        int rem = i - lz * rx * ey;
+        int ly = rem / rx, lx = rem - ly * rx;
+        int rt = rowtype(Y0 + ly, g.nu[1]);
+#pragma unroll
+        for (int t = 0; t < 21; ++t) {
+          const Term3 tm = c_terms3[t];
+          if (tm.j != j) continue;
+          const T* v = s_zo + tm.zop * H3 * H3 * T3 + (lz * H3 + ly) * H3 + lx;
+          T val = tap5(s_tab[1][tm.yop][rt], v, H3);
+          s_px[(tm.i * 4 + tm.xop) * H3 * T3 * T3 + (lz * T3 + ly) * H3 + lx] += cf[tm.coef] * val;
+        }
+      }
+    }
+    __syncthreads();
+    // x pass and output
+    T* yk = y + k * sy;
+    for (int i = tid; i < ex * ey * ez; i += nth) {
+      int lz = i / (ex * ey);
+      int rem = i - lz * ex * ey;
+      int ly = rem / ex, lx = rem - ly * ex;
+      int gx = X0 + lx, gy = Y0 + ly, gz = Z0 + lz;
+      int rt = rowtype(gx, g.nu[0]);
+      int64_t node = ((int64_t)gz * g.nu[1] + gy) * g.nu[0] + gx;
+      for (int c = 0; c < 3; ++c) {
+        T out;
+        if (u_free(g, c, gx, gy, gz)) {
+          T acc = 0;
+#pragma unroll
+          for (int op = 0; op < 4; ++op)
+            acc += tap5(s_tab[0][op][rt], s_px + (c * 4 + op) * H3 * T3 * T3 + (lz * T3 + ly) * H3 + lx, 1);
+          out = T(sc.au[k]) * acc;
+          if (p_in) {
+            for (int l = 0; l < sc.nt; ++l) {
+              T e = T(sc.ep[k][l]);
+              if (e != T(0)) out += e * gather_Ep<T, 3>(g, tb, p_in + l * sp, c, gx, gy, gz);
+            }
+          }
+        } else {
+          out = u_in[k * su + c * nn + node];
+        }
+        yk[c * nn + node] = out;
+      }
+    }
+  }
+}
+
+// 2-D displacement rows: tiles of 16x16 nodes, passes y then x.
+template <typename T>
+__global__ void __launch_bounds__(256) k_apply_u2(Grid g, TabT<T> tb, SlabCoef sc, const T* __restrict__ u_in, int64_t su,
+                                                  const T* __restrict__ p_in, int64_t sp, T* __restrict__ y, int64_t sy) {
+  __shared__ T s_in[2][H2 * H2];
+  __shared__ T s_px[8][T2 * H2];
+  __shared__ T s_tab[2][4][4][5];
+  const int tid = threadIdx.x, nth = blockDim.x;
+  for (int i = tid; i < 2 * 4 * 4 * 5; i += nth) (&s_tab[0][0][0][0])[i] = (&tb.q2[0][0][0][0])[i];
+  const int X0 = blockIdx.x * T2, Y0 = blockIdx.y * T2;
+  const int ex = min(T2, g.nu[0] - X0), ey = min(T2, g.nu[1] - Y0);
+  const int rx = ex + 4, ry = ey + 4;
+  const T cf[3] = {T(2.0 * sc.mu + sc.lam), T(sc.mu), T(sc.lam)};
+  const int64_t nn = g.nnode;
+  for (int k = 0; k < sc.nt; ++k) {
+    const T* u = u_in + k * su;
+    __syncthreads();
+    for (int i = tid; i < 2 * rx * ry; i += nth) {
+      int c = i / (rx * ry);
+      int rem = i - c * rx * ry;
+      int ly = rem / rx, lx = rem - ly * rx;
+      int gx = X0 + lx - 2, gy = Y0 + ly - 2;
+      T v = 0;
+      if (gx >= 0 && gx < g.nu[0] && gy >= 0 && gy < g.nu[1] && u_free(g, c, gx, gy, 0)) v = u[c * nn + (int64_t)gy * g.nu[0] + gx];
+      s_in[c][ly * H2 + lx] = v;
+    }
+    for (int i = tid; i < 8 * T2 * H2; i += nth) (&s_px[0][0])[i] = 0;
+    for (int j = 0; j < 2; ++j) {
+      __syncthreads();
+      for (int i = tid; i < rx * ey; i += nth) {
+        int ly = i / rx, lx = i - ly * rx;
+        int rt = rowtype(Y0 + ly, g.nu[1]);
+        const T* v = &s_in[j][ly * H2 + lx];
+        T w[4];
+#pragma unroll
+        for (int op = 0; op < 4; ++op) w[op] = tap5(s_tab[1][op][rt], v, H2);
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+          const Term2 tm = c_terms2[t];
+          if (tm.j != j) continue;
+          s_px[tm.i * 4 + tm.xop][ly * H2 + lx] += cf[tm.coef] * w[tm.yop];
+        }
+      }
+    }
+    __syncthreads();
+    T* yk = y + k * sy;
+    for (int i = tid; i < ex * ey; i += nth) {
+      int ly = i / ex, lx = i - ly * ex;
+      int gx = X0 + lx, gy = Y0 + ly;
+      int rt = rowtype(gx, g.nu[0]);
+      int64_t node = (int64_t)gy * g.nu[0] + gx;
+      for (int c = 0; c < 2; ++c) {
+        T out;
+        if (u_free(g, c, gx, gy, 0)) {
+          T acc = 0;
+#pragma unroll
+          for (int op = 0; op < 4; ++op) acc += tap5(s_tab[0][op][rt], &s_px[c * 4 + op][ly * H2 + lx], 1);
+          out = T(sc.au[k]) * acc;
+          if (p_in) {
+            for (int l = 0; l < sc.nt; ++l) {
+              T e = T(sc.ep[k][l]);
+              if (e != T(0)) out += e * gather_Ep<T, 2>(g, tb, p_in + l * sp, c, gx, gy, 0);
+            }
+          }
+        } else {
+          out = u_in[k * su + c * nn + node];
+        }
+        yk[c * nn + node] = out;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// flux rows: one thread per flux DoF (all components).
+template <typename T, int DIM>
+__global__ void k_apply_q(Grid g, TabT<T> tb, SlabCoef sc, const T* __restrict__ kscale, const T* __restrict__ x, int64_t sx,
+                          T* __restrict__ y, int64_t sy) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t nqt = g.nq[0] + g.nq[1] + g.nq[2];
+  if (t >= nqt) return;
+  int c = 0;
+  int64_t r = t;
+  while (r >= g.nq[c]) { r -= g.nq[c]; ++c; }
+  // grid coordinates of this component's DoF grid
+  int sh[3], co[3];
+  for (int d = 0; d < 3; ++d) sh[d] = (d < DIM) ? ((d == c) ? g.nu[d] : g.ng[d]) : 1;
+  co[0] = (int)(r % sh[0]);
+  int64_t rr = r / sh[0];
+  co[1] = (int)(rr % sh[1]);
+  co[2] = (int)(rr / sh[1]);
+  const int64_t qoff = g.offq[c];
+  const int64_t gidx = qoff + r;
+  const int ia = co[c];
+  // stride of the along-c index in this component's grid
+  int64_t stride_c = 1;
+  for (int d = 0; d < c; ++d) stride_c *= sh[d];
+  // transverse weight and transverse cell indices
+  T wt = T(1);
+  int cell[3];
+  for (int d = 0; d < 3; ++d) {
+    if (d < DIM && d != c) { wt *= tb.wg[d]; cell[d] = co[d] >> 1; } else cell[d] = 0;
+  }
+  // adjacent cells along c: (cell index, local node a)
+  int ce[2], la[2], ncell = 0;
+  if (ia & 1) { ce[0] = ia >> 1; la[0] = 1; ncell = 1; }
+  else {
+    int j = ia >> 1;
+    if (j >= 1) { ce[ncell] = j - 1; la[ncell] = 2; ++ncell; }
+    if (j < g.n[c]) { ce[ncell] = j; la[ncell] = 0; ++ncell; }
+  }
+  const bool fr = q_free(g, c, ia);
+  // p-grid strides
+  int64_t pst[3] = {1, g.ng[0], (int64_t)g.ng[0] * g.ng[1]};
+  int64_t pbase = 0;
+  for (int d = 0; d < DIM; ++d) if (d != c) pbase += co[d] * pst[d];
+  for (int k = 0; k < sc.nt; ++k) {
+    const T* xk = x + k * sx;
+    T out;
+    if (!fr) out = xk[gidx];
+    else {
+      T acc = 0;
+      for (int e = 0; e < ncell; ++e) {
+        cell[c] = ce[e];
+        int64_t cid = ((int64_t)cell[2] * g.n[1] + cell[1]) * g.n[0] + cell[0];
+        T s = kscale[cid];
+        T m = 0;
+        for (int b = 0; b < 3; ++b) {
+          int ib = 2 * ce[e] + b;
+          if (!q_free(g, c, ib)) continue;
+          m += tb.mq[c][la[e]][b] * xk[qoff + r + (int64_t)(ib - ia) * stride_c];
+        }
+        acc += s * m;
+      }
+      out = T(sc.aq[k]) * wt * acc;
+      // B^T p
+      for (int l = 0; l < sc.nt; ++l) {
+        T w = T(sc.qp[k][l]);
+        if (w == T(0)) continue;
+        const T* pl = x + l * sx + g.offp + pbase;
+        T bp = 0;
+        for (int e = 0; e < ncell; ++e)
+          for (int q = 0; q < 2; ++q) bp += tb.bd[c][la[e]][q] * pl[(int64_t)(2 * ce[e] + q) * pst[c]];
+        out += w * wt * bp;
+      }
+    }
+    y[k * sy + gidx] = out;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// pressure rows: one thread per Gauss-point pressure DoF.
+template <typename T, int DIM>
+__global__ void k_apply_p(Grid g, TabT<T> tb, SlabCoef sc, const T* __restrict__ x, int64_t sx, T* __restrict__ y, int64_t sy) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= g.Np) return;
+  int co[3];
+  co[0] = (int)(t % g.ng[0]);
+  int64_t rr = t / g.ng[0];
+  co[1] = (int)(rr % g.ng[1]);
+  co[2] = (int)(rr / g.ng[1]);
+  int cell[3], gq[3];
+  for (int d = 0; d < 3; ++d) { cell[d] = (d < DIM) ? co[d] >> 1 : 0; gq[d] = (d < DIM) ? (co[d] & 1) : 0; }
+  T mp = T(1);
+  for (int d = 0; d < DIM; ++d) mp *= tb.wg[d];
+  T eu[MAXR], bq[MAXR], pv[MAXR];
+  for (int l = 0; l < sc.nt; ++l) {
+    const T* xl = x + l * sx;
+    // E^T u: the cell's 3^DIM nodes, all components
+    T acc = 0;
+    for (int c = 0; c < DIM; ++c) {
+      T f[3][3];
+      for (int d = 0; d < 3; ++d)
+        for (int a = 0; a < 3; ++a) f[d][a] = (d < DIM) ? ((d == c) ? tb.bd[d][a][gq[d]] : tb.bv[d][a][gq[d]]) : (a == 0 ? T(1) : T(0));
+      const int az_n = (DIM == 3) ? 3 : 1;
+      for (int az = 0; az < az_n; ++az)
+        for (int ay = 0; ay < 3; ++ay) {
+          int iz = 2 * cell[2] + az, iy = 2 * cell[1] + ay;
+          const T* row = xl + c * g.nnode + ((int64_t)iz * g.nu[1] + iy) * g.nu[0];
+          T s = 0;
+          for (int ax = 0; ax < 3; ++ax) {
+            int ix = 2 * cell[0] + ax;
+            if (u_free(g, c, ix, iy, iz)) s += f[0][ax] * row[ix];
+          }
+          acc += f[2][az] * f[1][ay] * s;
+        }
+    }
+    eu[l] = acc;
+    // B q: for each component c the 3 DoFs along c on this Gauss line
+    T bacc = 0;
+    for (int c = 0; c < DIM; ++c) {
+      int sh[3];
+      for (int d = 0; d < 3; ++d) sh[d] = (d < DIM) ? ((d == c) ? g.nu[d] : g.ng[d]) : 1;
+      T wt = T(1);
+      int64_t base = 0, mul = 1, stride_c = 1;
+      for (int d = 0; d < 3; ++d) {
+        if (d == c) stride_c = mul;
+        else { base += co[d] * mul; if (d < DIM) wt *= tb.wg[d]; }
+        mul *= sh[d];
+      }
+      const T* qc = xl + g.offq[c] + base;
+      T s = 0;
+      for (int a = 0; a < 3; ++a) {
+        int ia = 2 * cell[c] + a;
+        if (q_free(g, c, ia)) s += tb.bd[c][a][gq[c]] * qc[(int64_t)ia * stride_c];
+      }
+      bacc += wt * s;
+    }
+    bq[l] = bacc;
+    pv[l] = xl[g.offp + t];
+  }
+  for (int k = 0; k < sc.nt; ++k) {
+    T out = T(sc.pq[k]) * bq[k];
+    for (int l = 0; l < sc.nt; ++l) out += T(sc.pu[k][l]) * eu[l] + T(sc.pp[k][l]) * mp * pv[l];
+    y[k * sy + g.offp + t] = out;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// diagonal of the elasticity block A (unit tau) per node and component
+template <typename T, int DIM>
+__global__ void k_diag_A(Grid g, TabT<T> tb, double lam, double mu, T* __restrict__ d) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= g.nnode) return;
+  int ix = (int)(t % g.nu[0]);
+  int64_t rr = t / g.nu[0];
+  int iy = (int)(rr % g.nu[1]);
+  int iz = (int)(rr / g.nu[1]);
+  int rt[3] = {rowtype(ix, g.nu[0]), rowtype(iy, g.nu[1]), DIM == 3 ? rowtype(iz, g.nu[2]) : 0};
+  T Mc[3], Kc[3];
+  for (int e = 0; e < DIM; ++e) { Mc[e] = tb.q2[e][0][rt[e]][2]; Kc[e] = tb.q2[e][1][rt[e]][2]; }
+  for (int c = 0; c < DIM; ++c) {
+    T acc = 0;
+    for (int e = 0; e < DIM; ++e) {
+      T term = (e == c) ? T(2 * mu + lam) : T(mu);
+      for (int f = 0; f < DIM; ++f) term *= (f == e) ? Kc[f] : Mc[f];
+      acc += term;
+    }
+    d[c * g.nnode + t] = u_free(g, c, ix, iy, iz) ? acc : T(1);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host launchers
+template <typename T>
+void launch_apply_u(const Grid& g, const TabT<T>& tb, const SlabCoef& sc, const T* u, int64_t su, const T* p, int64_t sp, T* y,
+                    int64_t sy, cudaStream_t st) {
+  if (g.dim == 3) {
+    dim3 grid((g.nu[0] + T3 - 1) / T3, (g.nu[1] + T3 - 1) / T3, (g.nu[2] + T3 - 1) / T3);
+    size_t smem = sizeof(T) * (3 * H3 * H3 * H3 + 4 * H3 * H3 * T3 + 12 * H3 * T3 * T3);
+    static bool attr_set[2] = {false, false};
+    int which = sizeof(T) == 8;
+    if (!attr_set[which]) {
+      cudaFuncSetAttribute(k_apply_u3<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      attr_set[which] = true;
+    }
+    k_apply_u3<T><<<grid, 256, smem, st>>>(g, tb, sc, u, su, p, sp, y, sy);
+  } else {
+    dim3 grid((g.nu[0] + T2 - 1) / T2, (g.nu[1] + T2 - 1) / T2, 1);
+    k_apply_u2<T><<<grid, 256, 0, st>>>(g, tb, sc, u, su, p, sp, y, sy);
+  }
+}
+
+template <typename T>
+void launch_apply_q(const Grid& g, const TabT<T>& tb, const SlabCoef& sc, const T* kscale, const T* x, int64_t sx, T* y,
+                    int64_t sy, cudaStream_t st) {
+  int64_t n = g.nq[0] + g.nq[1] + g.nq[2];
+  int blocks = (int)((n + 255) / 256);
+  if (g.dim == 3) k_apply_q<T, 3><<<blocks, 256, 0, st>>>(g, tb, sc, kscale, x, sx, y, sy);
+  else k_apply_q<T, 2><<<blocks, 256, 0, st>>>(g, tb, sc, kscale, x, sx, y, sy);
+}
+
+template <typename T>
+void launch_apply_p(const Grid& g, const TabT<T>& tb, const SlabCoef& sc, const T* x, int64_t sx, T* y, int64_t sy,
+                    cudaStream_t st) {
+  int blocks = (int)((g.Np + 255) / 256);
+  if (g.dim == 3) k_apply_p<T, 3><<<blocks, 256, 0, st>>>(g, tb, sc, x, sx, y, sy);
+  else k_apply_p<T, 2><<<blocks, 256, 0, st>>>(g, tb, sc, x, sx, y, sy);
+}
+
+template <typename T>
+void launch_diag_A(const Grid& g, const TabT<T>& tb, double lam, double mu, T* d, cudaStream_t st) {
+  int blocks = (int)((g.nnode + 255) / 256);
+  if (g.dim == 3) k_diag_A<T, 3><<<blocks, 256, 0, st>>>(g, tb, lam, mu, d);
+  else k_diag_A<T, 2><<<blocks, 256, 0, st>>>(g, tb, lam, mu, d);
+}
+
+#define INST(T)                                                                                                        \
+  template void launch_apply_u<T>(const Grid&, const TabT<T>&, const SlabCoef&, const T*, int64_t, const T*, int64_t, T*, \
+                                  int64_t, cudaStream_t);                                                              \
+  template void launch_apply_q<T>(const Grid&, const TabT<T>&, const SlabCoef&, const T*, const T*, int64_t, T*, int64_t, \
+                                  cudaStream_t);                                                                       \
+  template void launch_apply_p<T>(const Grid&, const TabT<T>&, const SlabCoef&, const T*, int64_t, T*, int64_t,         \
+                                  cudaStream_t);                                                                       \
+  template void launch_diag_A<T>(const Grid&, const TabT<T>&, double, double, T*, cudaStream_t);
+INST(double)
+INST(float)
+
+}  // namespace biot

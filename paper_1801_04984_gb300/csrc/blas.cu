@@ -1,0 +1,265 @@
+// Vector kernels of the Krylov solver: fused multi-dot, fused multi-axpy with
+// the second Gram-Schmidt pass or the norm folded in, conversions, time-basis
+// mixing.  All reductions are deterministic: fixed grid, per-thread partials
+// reduced in a fixed order, then one block sums the per-block partials.
+//
+// FP32 vectors are reduced with exact products (two-product by fma) and
+// compensated (two-sum) single-precision accumulation per thread, converted to
+// double for the cross-thread reduction, so inner products of FP32 Krylov
+// vectors carry FP64-level accuracy without using the (slow) FP64 pipe per
+// element.
+#include "internal.h"
+
+namespace biot {
+
+constexpr int NV = 8;  // vectors per multi-dot pass
+
+struct Acc {  // compensated accumulator
+  float hi, lo;
+};
+
+__device__ __forceinline__ void acc_add(Acc& a, float x) {
+  float s = __fadd_rn(a.hi, x);
+  float bb = __fsub_rn(s, a.hi);
+  float err = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(x, bb));
+  a.hi = s;
+  a.lo = __fadd_rn(a.lo, err);
+}
+__device__ __forceinline__ void acc_fma(Acc& a, float x, float y) {
+  float p = __fmul_rn(x, y);
+  float e = __fmaf_rn(x, y, -p);
+  acc_add(a, p);
+  a.lo = __fadd_rn(a.lo, e);
+}
+
+template <typename TV>
+struct DotAcc;
+template <>
+struct DotAcc<double> {
+  double s;
+  __device__ void init() { s = 0.0; }
+  __device__ void add(double x, double y) { s = fma(x, y, s); }
+  __device__ double get() const { return s; }
+};
+template <>
+struct DotAcc<float> {
+  Acc a;
+  __device__ void init() { a.hi = 0.f; a.lo = 0.f; }
+  __device__ void add(float x, float y) { acc_fma(a, x, y); }
+  __device__ double get() const { return (double)a.hi + (double)a.lo; }
+};
+
+// block-reduce `cnt` doubles per thread (in smem), write to partial[blockIdx.x * stride + i]
+__device__ inline void block_reduce_store(double* vals, int cnt, double* partial, int stride) {
+  __shared__ double sh[NV + 1][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i = 0; i < cnt; ++i) {
+    double v = vals[i];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) sh[i][warp] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < cnt) {
+    double s = 0;
+    for (int w = 0; w < nw; ++w) s += sh[threadIdx.x][w];
+    partial[(int64_t)blockIdx.x * stride + threadIdx.x] = s;
+  }
+}
+
+template <typename TV>
+__global__ void __launch_bounds__(256) k_multidot(const TV* const* __restrict__ V, int nv, const TV* __restrict__ w, int64_t n,
+                                                  double* __restrict__ partial) {
+  DotAcc<TV> acc[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) acc[i].init();
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += stride) {
+    TV we = w[e];
+#pragma unroll
+    for (int i = 0; i < NV; ++i)
+      if (i < nv) acc[i].add(V[i][e], we);
+  }
+  double vals[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) vals[i] = acc[i].get();
+  block_reduce_store(vals, nv, partial, NV + 1);
+}
+
+// sum partial[b][i] over blocks b (fixed order) -> out[i]
+__global__ void k_final_reduce(const double* __restrict__ partial, int nblocks, int cnt, int stride, double* __restrict__ out) {
+  __shared__ double sh[256];
+  for (int i = 0; i < cnt; ++i) {
+    double s = 0;
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) s += partial[(int64_t)b * stride + i];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+      if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) out[i] = sh[0];
+    __syncthreads();
+  }
+}
+
+template <typename TV>
+void launch_multidot(const TV* const* V, int nv, const TV* w, int64_t n, double* partial, double* out, cudaStream_t st) {
+  for (int c0 = 0; c0 < nv; c0 += NV) {
+    int cnt = (nv - c0 < NV) ? nv - c0 : NV;
+    k_multidot<TV><<<RED_BLOCKS, 256, 0, st>>>(V + c0, cnt, w, n, partial);
+    k_final_reduce<<<1, 256, 0, st>>>(partial, RED_BLOCKS, cnt, NV + 1, out + c0);
+  }
+}
+
+// mode 0: w -= V h ; mode 1: also partial dots V^T w_new ; mode 2: also ||w_new||^2
+template <typename TV>
+__global__ void __launch_bounds__(256) k_multiaxpy(const TV* const* __restrict__ V, int nv, const double* __restrict__ h,
+                                                   TV* __restrict__ w, int64_t n, int mode, double* __restrict__ partial) {
+  TV hv[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) hv[i] = (i < nv) ? (TV)h[i] : TV(0);
+  DotAcc<TV> acc[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) acc[i].init();
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += stride) {
+    TV v[NV];
+    TV we = w[e];
+#pragma unroll
+    for (int i = 0; i < NV; ++i)
+      if (i < nv) { v[i] = V[i][e]; we -= hv[i] * v[i]; }
+    w[e] = we;
+    if (mode == 1) {
+#pragma unroll
+      for (int i = 0; i < NV; ++i)
+        if (i < nv) acc[i].add(v[i], we);
+    } else if (mode == 2) {
+      acc[0].add(we, we);
+    }
+  }
+  if (mode == 0) return;
+  double vals[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) vals[i] = acc[i].get();
+  block_reduce_store(vals, mode == 1 ? nv : 1, partial, NV + 1);
+}
+
+template <typename TV>
+void launch_multiaxpy_dot(const TV* const* V, int nv, const double* h, TV* w, int64_t n, int mode, double* partial,
+                          double* out, cudaStream_t st) {
+  // mode 1 needs every chunk's dots against the final w: apply all axpys first
+  // chunk by chunk, then dot in a separate pass when more than one chunk.
+  if (nv <= NV) {
+    k_multiaxpy<TV><<<RED_BLOCKS, 256, 0, st>>>(V, nv, h, w, n, mode, partial);
+    if (mode == 1) k_final_reduce<<<1, 256, 0, st>>>(partial, RED_BLOCKS, nv, NV + 1, out);
+    if (mode == 2) k_final_reduce<<<1, 256, 0, st>>>(partial, RED_BLOCKS, 1, NV + 1, out);
+    return;
+  }
+  for (int c0 = 0; c0 < nv; c0 += NV) {
+    int cnt = (nv - c0 < NV) ? nv - c0 : NV;
+    bool last = c0 + NV >= nv;
+    int m = (last && mode == 2) ? 2 : 0;
+    k_multiaxpy<TV><<<RED_BLOCKS, 256, 0, st>>>(V + c0, cnt, h + c0, w, n, m, partial);
+    if (m == 2) k_final_reduce<<<1, 256, 0, st>>>(partial, RED_BLOCKS, 1, NV + 1, out);
+  }
+  if (mode == 1) launch_multidot<TV>(V, nv, w, n, partial, out, st);
+}
+
+template <typename TA, typename TB>
+__global__ void k_convert(const TA* __restrict__ a, TB* __restrict__ b, int64_t n) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) b[e] = (TB)a[e];
+}
+template <typename TA, typename TB>
+void launch_convert(const TA* a, TB* b, int64_t n, cudaStream_t st) {
+  k_convert<TA, TB><<<RED_BLOCKS * 2, 256, 0, st>>>(a, b, n);
+}
+
+template <typename T>
+__global__ void k_axpby(T* __restrict__ y, const T* __restrict__ x, T a, T b, int64_t n) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    y[e] = a * x[e] + b * y[e];
+}
+template <typename T>
+void launch_axpby(T* y, const T* x, double a, double b, int64_t n, cudaStream_t st) {
+  k_axpby<T><<<RED_BLOCKS * 2, 256, 0, st>>>(y, x, (T)a, (T)b, n);
+}
+
+template <typename T>
+__global__ void k_scale_into(T* __restrict__ y, const T* __restrict__ x, const double* __restrict__ s, int inv, int64_t n) {
+  double sv = *s;
+  T f = (T)(inv ? 1.0 / sqrt(sv) : sv);
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) y[e] = x[e] * f;
+}
+// inv = 1: y = x / sqrt(*s) (normalisation by a squared norm); inv = 0: y = x * (*s)
+template <typename T>
+void launch_scale_into(T* y, const T* x, const double* s, int inv, int64_t n, cudaStream_t st) {
+  k_scale_into<T><<<RED_BLOCKS * 2, 256, 0, st>>>(y, x, s, inv, n);
+}
+
+template <typename TY, typename TZ>
+__global__ void k_lincomb_add(TY* __restrict__ y, const TZ* const* __restrict__ Z, int nz, const double* __restrict__ c,
+                              int64_t n) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    double s = (double)y[e];
+    for (int i = 0; i < nz; ++i) s += c[i] * (double)Z[i][e];
+    y[e] = (TY)s;
+  }
+}
+template <typename TY, typename TZ>
+void launch_lincomb_add(TY* y, const TZ* const* Z, int nz, const double* c, int64_t n, cudaStream_t st) {
+  k_lincomb_add<TY, TZ><<<RED_BLOCKS * 2, 256, 0, st>>>(y, Z, nz, c, n);
+}
+
+__global__ void k_residual(const double* __restrict__ b, const double* __restrict__ Ax, double* __restrict__ r, int64_t n) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) r[e] = b[e] - Ax[e];
+}
+void launch_residual(const double* b, const double* Ax, double* r, int64_t n, cudaStream_t st) {
+  k_residual<<<RED_BLOCKS * 2, 256, 0, st>>>(b, Ax, r, n);
+}
+
+struct Mix {
+  double c[MAXR][MAXR];
+};
+template <typename TI, typename TO>
+__global__ void k_time_mix(const TI* __restrict__ in, int64_t sin, TO* __restrict__ out, int64_t sout, int nt, Mix m, int64_t n) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    double v[MAXR];
+    for (int l = 0; l < nt; ++l) v[l] = (double)in[l * sin + e];
+    for (int k = 0; k < nt; ++k) {
+      double s = 0;
+      for (int l = 0; l < nt; ++l) s += m.c[k][l] * v[l];
+      out[k * sout + e] = (TO)s;
+    }
+  }
+}
+template <typename TI, typename TO>
+void launch_time_mix(const TI* in, int64_t sin, TO* out, int64_t sout, int nt, const double* C, int64_t n, cudaStream_t st) {
+  Mix m;
+  for (int k = 0; k < MAXR; ++k)
+    for (int l = 0; l < MAXR; ++l) m.c[k][l] = (k < nt && l < nt) ? C[k * nt + l] : 0.0;
+  k_time_mix<TI, TO><<<RED_BLOCKS * 2, 256, 0, st>>>(in, sin, out, sout, nt, m, n);
+}
+
+template void launch_multidot<double>(const double* const*, int, const double*, int64_t, double*, double*, cudaStream_t);
+template void launch_multidot<float>(const float* const*, int, const float*, int64_t, double*, double*, cudaStream_t);
+template void launch_multiaxpy_dot<double>(const double* const*, int, const double*, double*, int64_t, int, double*, double*,
+                                           cudaStream_t);
+template void launch_multiaxpy_dot<float>(const float* const*, int, const double*, float*, int64_t, int, double*, double*,
+                                          cudaStream_t);
+template void launch_convert<double, float>(const double*, float*, int64_t, cudaStream_t);
+template void launch_convert<float, double>(const float*, double*, int64_t, cudaStream_t);
+template void launch_convert<double, double>(const double*, double*, int64_t, cudaStream_t);
+template void launch_convert<float, float>(const float*, float*, int64_t, cudaStream_t);
+template void launch_axpby<double>(double*, const double*, double, double, int64_t, cudaStream_t);
+template void launch_axpby<float>(float*, const float*, double, double, int64_t, cudaStream_t);
+template void launch_scale_into<double>(double*, const double*, const double*, int, int64_t, cudaStream_t);
+template void launch_scale_into<float>(float*, const float*, const double*, int, int64_t, cudaStream_t);
+template void launch_lincomb_add<double, double>(double*, const double* const*, int, const double*, int64_t, cudaStream_t);
+template void launch_lincomb_add<double, float>(double*, const float* const*, int, const double*, int64_t, cudaStream_t);
+template void launch_lincomb_add<float, float>(float*, const float* const*, int, const double*, int64_t, cudaStream_t);
+template void launch_time_mix<double, double>(const double*, int64_t, double*, int64_t, int, const double*, int64_t,
+                                              cudaStream_t);
+template void launch_time_mix<float, float>(const float*, int64_t, float*, int64_t, int, const double*, int64_t, cudaStream_t);
+template void launch_time_mix<double, float>(const double*, int64_t, float*, int64_t, int, const double*, int64_t, cudaStream_t);
+
+}  // namespace biot

@@ -1,0 +1,114 @@
+// Internal (not exported) declarations shared by the library's translation units.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+#include "common.cuh"
+#include "tables.h"
+
+namespace biot {
+
+// ---- slab operator pieces (apply.cu) --------------------------------------
+template <typename T>
+void launch_apply_u(const Grid& g, const TabT<T>& tb, const SlabCoef& sc, const T* u, int64_t su, const T* p, int64_t sp, T* y,
+                    int64_t sy, cudaStream_t st);
+template <typename T>
+void launch_apply_q(const Grid& g, const TabT<T>& tb, const SlabCoef& sc, const T* kscale, const T* x, int64_t sx, T* y,
+                    int64_t sy, cudaStream_t st);
+template <typename T>
+void launch_apply_p(const Grid& g, const TabT<T>& tb, const SlabCoef& sc, const T* x, int64_t sx, T* y, int64_t sy,
+                    cudaStream_t st);
+template <typename T>
+void launch_diag_A(const Grid& g, const TabT<T>& tb, double lam, double mu, T* d, cudaStream_t st);
+
+// ---- vector kernels (blas.cu) ---------------------------------------------
+// Deterministic reductions: per-block partials in a fixed order, then one
+// block sums the partials in a fixed order.  Results land in device memory.
+constexpr int RED_BLOCKS = 608;  // 4 x 152 SMs
+constexpr int MAXDOT = 64;       // max vectors in one multi-dot
+
+template <typename TV>
+void launch_multidot(const TV* const* V, int nv, const TV* w, int64_t n, double* partial, double* out, cudaStream_t st);
+// w = w - sum_i V_i h_i  (h in device memory, double); optionally the dots
+// V_i^T w_new into out (second Gram-Schmidt pass) or ||w_new||^2 into out[nv] when want_norm.
+template <typename TV>
+void launch_multiaxpy_dot(const TV* const* V, int nv, const double* h, TV* w, int64_t n, int mode, double* partial,
+                          double* out, cudaStream_t st);
+template <typename TA, typename TB>
+void launch_convert(const TA* a, TB* b, int64_t n, cudaStream_t st);
+template <typename T>
+void launch_axpby(T* y, const T* x, double a, double b, int64_t n, cudaStream_t st);  // y = a x + b y
+template <typename T>
+void launch_scale_into(T* y, const T* x, const double* s, int inv, int64_t n, cudaStream_t st);  // y = x * s or x / s (s device)
+// y += sum_i Z_i c_i  (c device, double; accumulated in double)
+template <typename TY, typename TZ>
+void launch_lincomb_add(TY* y, const TZ* const* Z, int nz, const double* c, int64_t n, cudaStream_t st);
+void launch_residual(const double* b, const double* Ax, double* r, int64_t n, cudaStream_t st);  // r = b - Ax
+// time transform: out[k] = sum_l C[k][l] in[l] over nt levels of length n (strided)
+template <typename TI, typename TO>
+void launch_time_mix(const TI* in, int64_t sin, TO* out, int64_t sout, int nt, const double* C, int64_t n, cudaStream_t st);
+
+// ---- multigrid / preconditioner pieces (mg.cu) ----------------------------
+template <typename T>
+void launch_prolong_add(const Grid& fine, const Grid& coarse, const T* xc, int64_t sc, T* xf, int64_t sf, int nrhs,
+                        cudaStream_t st);
+template <typename T>
+void launch_restrict(const Grid& fine, const Grid& coarse, const T* rf, int64_t sf, T* rc, int64_t sc, int nrhs,
+                     cudaStream_t st);
+// Chebyshev step on nrhs vectors of length n (u block only):
+// r = b - Ax ; d = c1 d + c2 Dinv r ; xo = x + d   (first step: d = c2 Dinv b, xo = d)
+template <typename T>
+void launch_cheb_update(const T* b, const T* Ax, const T* dinv, T* d, const T* x, T* xo, double c1, double c2, int first,
+                        int64_t n, int nrhs, int64_t stride, cudaStream_t st);
+// x = Ainv * b for nrhs columns (dense FP64 inverse, n x n), scale s
+template <typename T>
+void launch_dense_gemv(const double* Ainv, int n, const T* b, int64_t sb, T* x, int64_t sx, int nrhs, double s,
+                       cudaStream_t st);
+
+// flow-block pieces (mg.cu); flux arrays start at the flux block (offset Nu of a
+// temporal level), pressure arrays at the pressure block.
+template <typename T>
+void launch_diag_Mq(const Grid& g, const TabT<T>& tb, const T* kscale, T* dmq, cudaStream_t st);
+template <typename T>
+void launch_diag_BDBt(const Grid& g, const TabT<T>& tb, const T* dmq, T* out, cudaStream_t st);
+template <typename T>
+void launch_q_jacobi(const Grid& g, const TabT<T>& tb, const T* rq, int64_t srq, const T* dmq, double tau, T* q0, int64_t sq,
+                     int nrhs, cudaStream_t st);
+template <typename T>
+void launch_p_minus_Bq(const Grid& g, const TabT<T>& tb, const T* rp, int64_t srp, const T* q, int64_t sq, double tau, T* out,
+                       int64_t so, int nrhs, cudaStream_t st);
+template <typename T>
+void launch_schur_apply(const Grid& g, const TabT<T>& tb, const T* p, int64_t spp, const T* dmq, T* tq, int64_t sq, double tau,
+                        const double* cm, T* out, int64_t so, int nrhs, cudaStream_t st);
+template <typename T>
+void launch_q_final(const Grid& g, const TabT<T>& tb, const T* rq, int64_t srq, const T* p, int64_t spp, const T* dmq,
+                    double tau, double bt, T* qo, int64_t sq, int nrhs, cudaStream_t st);  // (Rq + bt B^T p)/(tau dmq)
+template <typename T>
+void launch_u_rhs(const Grid& g, const TabT<T>& tb, const T* ru, int64_t sru, const T* p, int64_t spp, double alpha, T* bu,
+                  int64_t sbu, int nrhs, cudaStream_t st);
+// out_p = rp + alpha E^T u (u masked)
+template <typename T>
+void launch_p_plus_ETu(const Grid& g, const TabT<T>& tb, const T* rp, int64_t srp, const T* u, int64_t su, double alpha, T* out,
+                       int64_t so, int nrhs, cudaStream_t st);
+// zero the constrained entries of nrhs spatial vectors (stride s)
+template <typename T>
+void launch_mask(const Grid& g, T* x, int64_t s, int nrhs, cudaStream_t st);
+// displacement block only (buffers of nrhs * Nu)
+template <typename T>
+void launch_mask_u(const Grid& g, T* x, int64_t s, int nrhs, cudaStream_t st);
+// per-cell flux-mass pairing: g[c] += w * kscale[c] * z_c^T Mq_ref x_c (both masked)
+void launch_grad_pair(const Grid& g, const TabT<double>& tb, const double* kscale, const double* z, const double* x, double w,
+                      double* grad, cudaStream_t st);
+// y_k = sum_m c[k][m] f_m (masked) + phi0[k] * sp (pressure block only), k < nt
+void launch_slab_rhs(const Grid& g, const double* const* f, int nterms, const double* c, const double* phi0, int nt,
+                     const double* sp, double* y, cudaStream_t st);
+
+template <typename T>
+void launch_schur_dinv(const Grid& g, const TabT<T>& tb, const T* sb2, const double* cm, double tau, T* dinv, int nrhs,
+                       cudaStream_t st);
+template <typename T>
+void launch_cheb_update_r(const T* b, const T* Ax, const T* dinv, T* d, const T* x, T* xo, double c1, double c2, int first,
+                          int64_t n, int nrhs, cudaStream_t st);
+template <typename TX, typename TD>
+void launch_add_scaled(TX* x, const TD* d, double s, int64_t n, cudaStream_t st);
+
+}  // namespace biot
