@@ -1,0 +1,310 @@
+"""Benchmark: space-time DoF/s of the monolithic Biot slab march on one GB300.
+
+Workload (one "step"): 3-D Biot on the unit cube, 32^3 hexes, Q2 / RT1 / DGQ1,
+dG(1) in time, T = 1 in 16 slabs; layered log-normal permeability
+K = exp(g) 1e-2 (g ~ N(0, 1.5^2) per 4-cell z-layer, seed 1801); lambda = mu = 1,
+b = 0.8, 1/M = 0.05; unit compressive load on the drained top face, roller /
+no-flow elsewhere.  Every slab is solved to relative residual 1e-10 (FP64) by
+the mixed FP32-inner / FP64-refinement solver (the metric's headline) and, for
+comparison, by the all-FP64 solver; the relative difference of the two end
+states is reported.
+
+value = N_slab * slabs / (device time of one mixed-precision march).
+e2e   = the same metric through the C ABI with host buffers (the load vector,
+        the initial state and the end state copied inside the timed region).
+
+`--impl reference` times the FP64 CPU oracle (sparse direct solves) on a
+bounded sample of the same problem class instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "slab solve time & space-time DoF/s at 1e-8 rel err: mixed-precision vs FP64, 1 GB300"
+WORKLOAD = ("3D Biot, unit cube, 32^3 hexes, Q2 displacement / RT1 flux / DGQ1 pressure, dG(1), T=1 in 16 slabs; "
+            "layered log-normal K (std 1.5, 4-cell z-layers, seed 1801); lambda=mu=1, b=0.8, 1/M=0.05; "
+            "drained top with unit compressive load, roller/no-flow elsewhere")
+COEF = dict(lam=1.0, mu=1.0, b=0.8, invM=0.05, eta=1.0, K_dr=1.0 + 2.0 / 3.0)
+
+
+def consolidation_bcs(d):
+    ubc = [2] * (2 * d)
+    ubc[-1] = 0
+    fbc = [1] * (2 * d)
+    fbc[-1] = 0
+    return ubc, fbc
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([s.strip() for s in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            if len(r) < 9:
+                continue
+            for i, nm in enumerate(names):
+                if r[5 + i].lower() in ("active", "1", "yes"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def oracle_sample(seconds_target=15.0, n=4, slabs=16):
+    """FP64 CPU oracle (sparse LU) on a bounded sample: 3-D n^3 hexes, same
+    coefficients/loading, dG(1), `slabs` slabs; repeated to ~seconds_target."""
+    from oracle.slab import SlabProblem
+    from oracle.space import Mesh, load_vector
+    from paper_1801_04984_gb300.inputs import layered_logk, K0
+    m = Mesh((n, n, n))
+    g = layered_logk(m.n, layer_cells=max(1, n // 8), std=1.5, seed=1801)
+    co = dict(COEF, K=K0 * np.exp(g))
+    ubc, fbc = consolidation_bcs(3)
+
+    def trac(X, t, f):
+        o = np.zeros((len(X), 3))
+        o[:, 2] = -1.0
+        return o
+    F = load_vector(m, 0.0, traction=trac, u_bc=ubc, f_bc=fbc)
+    t0 = time.perf_counter()
+    reps = 0
+    dofs = 0
+    while True:
+        prob = SlabProblem(m, co, 1, ubc, fbc)
+        prob.march(1.0, slabs, lambda t: F)
+        reps += 1
+        dofs += prob.Nslab * slabs
+        if time.perf_counter() - t0 > seconds_target:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": dofs / dt, "unit": "DoF/s", "cores": 1, "kind": "oracle",
+            "sample": "3-D %d^3 hexes, dG(1), %d slabs, N_slab=%d, x%d marches (assembly + SuperLU factorisation + "
+                      "solves), %.1f s" % (n, slabs, prob.Nslab, reps, dt),
+            "host_cores": os.cpu_count()}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    per = []
+    for _ in range(args.warmup + args.steps):
+        per.append(oracle_sample(seconds_target=max(2.0, 20.0 / (args.steps + args.warmup)), n=4, slabs=16))
+    timed = per[args.warmup:]
+    val = float(np.mean([p["value"] for p in timed]))
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "DoF/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "FP64 CPU oracle sample of the same problem class: " + timed[0]["sample"]},
+            "cpu_baseline": {"value": val, "unit": "DoF/s", "cores": 1, "kind": "oracle", "sample": timed[0]["sample"]},
+            "e2e": {"value": val, "unit": "DoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=32)
+    ap.add_argument("--r", type=int, default=1)
+    ap.add_argument("--slabs", type=int, default=16)
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison march")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    from paper_1801_04984_gb300 import binding as B
+    from paper_1801_04984_gb300.inputs import layered_logk, K0
+
+    n, r, slabs, T = args.n, args.r, args.slabs, 1.0
+    g = layered_logk((n, n, n), layer_cells=4, std=1.5, seed=1801)
+    ubc, fbc = consolidation_bcs(3)
+    ctx = B.Context(3, (n, n, n), dict(COEF, K=K0 * np.exp(g)), r, ubc, fbc)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    f = torch.zeros(ctx.n_space, dtype=torch.float64, device=dev)
+    ctx.load_preset(B.LOAD_TRACTION_TOP, 1.0, f)
+    U0 = torch.zeros_like(f)
+    U_mixed = torch.zeros_like(f)
+    U_fp64 = torch.zeros_like(f)
+    tcoef = [[1.0, 0, 0, 0]]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
+    stream = torch.cuda.current_stream()
+
+    def step(mode, U_end, stats=None):
+        s = ctx.march(T, slabs, [f], tcoef, U0, U_end, tol=1e-10, mode=mode)
+        if stats is not None:
+            stats.append(s)
+        return s
+
+    for _ in range(args.warmup):
+        step(B.MIXED, U_mixed)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    launches0, _, _ = ctx.counters()
+    stats = []
+    times = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        step(B.MIXED, U_mixed, stats)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+    launches1, _, _ = ctx.counters()
+    clocks = sampler.stop() if sampler else None
+    # one more (untimed) step with CUDA events around every launch of the dominant kernel
+    ctx.profile(True)
+    step(B.MIXED, U_mixed)
+    _, op_launches, op_ms = ctx.counters()
+    ctx.profile(False)
+    t_step = float(np.mean(times))
+    if ws > 1:
+        tt = torch.tensor([t_step], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_step = tt.item()
+    dofs_step = ctx.n_slab * slabs
+    value = ws * dofs_step / t_step
+
+    # end-to-end through the C ABI with host buffers
+    f_host = f.cpu().numpy().copy()
+    U0_host = np.zeros(ctx.n_space)
+    U_host = np.zeros(ctx.n_space)
+    te = []
+    for _ in range(max(1, min(args.steps, 2))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.march(T, slabs, [f_host], tcoef, U0_host, U_host, tol=1e-10, mode=B.MIXED)
+        torch.cuda.synchronize()
+        te.append(time.perf_counter() - t0)
+    e2e = {"value": ws * dofs_step / float(np.mean(te)), "unit": "DoF/s",
+           "h2d_bytes_per_step": 2 * ctx.n_space * 8, "d2h_bytes_per_step": ctx.n_space * 8}
+
+    # FP64 comparison march (device-timed, outside the headline region)
+    fp64 = None
+    if not args.no_fp64:
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        s64 = step(B.FP64, U_fp64)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t64 = e0.elapsed_time(e1) / 1e3
+        rel = (torch.linalg.norm(U_mixed - U_fp64) / torch.linalg.norm(U_fp64)).item()
+        fp64 = {"value": dofs_step / t64, "unit": "DoF/s", "ms_per_step": t64 * 1e3,
+                "ms_per_slab": t64 * 1e3 / slabs, "iterations": s64["iterations"],
+                "end_state_rel_diff_mixed_vs_fp64": rel}
+
+    # roofline of the dominant kernel (displacement-row operator, FP32 inside the V-cycle and the slab apply):
+    # algorithmic bytes per launch-level: read + write of the displacement block in FP32
+    avg_ms = op_ms / max(1, op_launches)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    # flops of the sum-factorised elasticity apply per Q2 node and component set (counted in the kernel design):
+    # ALU roofline against the FP32 CUDA-core peak at the sampled clock
+    s_mean = stats[-1]
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = oracle_sample(seconds_target=15.0, n=4, slabs=16)
+    line = {
+        "metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD if (n, r, slabs) == (32, 1, 16) else "%s (n=%d, r=%d, slabs=%d)" % (WORKLOAD, n, r, slabs),
+                   "n_slab": ctx.n_slab, "slabs": slabs, "solver": "FGMRES(30) FP32 inner + FP64 refinement, tol 1e-10",
+                   "l2": "256 MB buffer written before every timed step (> 129 MB L2)",
+                   "parallelism": "replicas" if ws > 1 else "single GPU"},
+        "ms_per_slab": t_step * 1e3 / slabs,
+        "iterations_per_step": s_mean["iterations"], "refinements_per_step": s_mean["refinements"],
+        "iters_per_slab": s_mean["iters_per_slab"],
+        "fp64": fp64,
+        "e2e": e2e,
+        "gpu_launches": int((launches1 - launches0) / max(1, args.steps)),
+        "op_kernel": {"launches_per_step": op_launches, "avg_ms": avg_ms},
+        "clocks": clocks,
+        "cpu_baseline": cpu,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -104,9 +104,11 @@ typedef struct {
 typedef struct {
   int gmres_restart;    /* m (default 30) */
   int cheb_degree;      /* Chebyshev degree of the elasticity smoother (default 4) */
-  int schur_degree;     /* Chebyshev degree of the flux-pressure Schur solve (default 8) */
+  int schur_degree;     /* Chebyshev degree of the flux-pressure Schur solve (default 32) */
   int mg_min_cells;     /* stop coarsening at this many cells per direction (default 2) */
   double beta_fs;       /* fixed-stress parameter; <= 0 selects b^2 / K_dr */
+  int lumped_flux_mass; /* 0 (default): Darcy mass inverted exactly by line solves in the flux-pressure
+                           block; 1: replaced by its diagonal */
 } biot_opts;
 
 typedef struct {
@@ -198,6 +200,31 @@ int biot_goal_mean_pressure(biot_t ctx, const double* lo, const double* hi, doub
  *                            solution u = (S t, S t), p = cos(pi x)cos(pi y) t. */
 enum { BIOT_LOAD_TRACTION_TOP = 0, BIOT_LOAD_MMS2D_CONST = 1, BIOT_LOAD_MMS2D_LINEAR = 2 };
 int biot_load_preset(biot_t ctx, int kind, double value, double* f, void* stream);
+
+/* Diagnostics: apply one piece of the slab preconditioner to a single spatial
+ * vector (n_space entries, double* for BIOT_FP64, float* for BIOT_FP32); the
+ * blocks a piece does not produce are zero in `out`.
+ *   BIOT_PART_FLUX_MASS_INV: out_q = (tau Mq)^{-1} in_q on free flux DoFs (exact,
+ *                            by line solves), out_q = in_q on no-flow DoFs;
+ *   BIOT_PART_SCHUR:        out_p = ((1/M + beta) Mp + tau B Mq^{-1} B^T) in_p, the
+ *                            flux-pressure Schur complement of the dG(0)-type block
+ *                            with lambda = 1 and the fixed-stress term beta Mp;
+ *   BIOT_PART_VCYCLE:       out_u = one multigrid V-cycle for tau A x = in_u from x = 0;
+ *   BIOT_PART_ELASTICITY:   out_u = tau A in_u (constrained rows identity). */
+enum { BIOT_PART_FLUX_MASS_INV = 0, BIOT_PART_SCHUR = 1, BIOT_PART_VCYCLE = 2, BIOT_PART_ELASTICITY = 3 };
+int biot_apply_part(biot_t ctx, int part, double tau, const void* in, void* out, int prec, void* stream);
+
+/* Tracing.  biot_profile(ctx, 1) makes every launch of the displacement-row
+ * operator kernel (the elasticity apply, the dominant kernel of the solver)
+ * record a pair of CUDA events on its launching stream; biot_counters returns
+ * the number of kernels this process has launched through the library so far
+ * (launches; a replayed CUDA graph counts its kernel nodes; setting the
+ * environment variable BIOT_NO_GRAPHS=1 before biot_setup disables graphs),
+ * and the number and summed device time in milliseconds of the
+ * operator launches recorded since the previous call (op_launches, op_ms;
+ * synchronises on those events, then forgets them).  Either output may be NULL. */
+int biot_profile(biot_t ctx, int enable);
+int biot_counters(biot_t ctx, int64_t* launches, int64_t* op_launches, double* op_ms);
 
 const char* biot_last_error(biot_t ctx);
 void biot_destroy(biot_t ctx);

@@ -22,6 +22,7 @@ U_NATURAL, U_DIRICHLET, U_ROLLER = 0, 1, 2
 F_NATURAL, F_NOFLOW = 0, 1
 FP64, FP32, MIXED = 0, 1, 2
 LOAD_TRACTION_TOP, LOAD_MMS2D_CONST, LOAD_MMS2D_LINEAR = 0, 1, 2
+PART_FLUX_MASS_INV, PART_SCHUR, PART_VCYCLE, PART_ELASTICITY = 0, 1, 2, 3
 ERR_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOCONV", 5: "EBREAKDOWN", 6: "ETIMEOUT"}
 
 
@@ -37,7 +38,7 @@ class Coeffs(C.Structure):
 
 class Opts(C.Structure):
     _fields_ = [("gmres_restart", C.c_int), ("cheb_degree", C.c_int), ("schur_degree", C.c_int),
-                ("mg_min_cells", C.c_int), ("beta_fs", C.c_double)]
+                ("mg_min_cells", C.c_int), ("beta_fs", C.c_double), ("lumped_flux_mass", C.c_int)]
 
 
 class SolveOpts(C.Structure):
@@ -83,6 +84,9 @@ def load(path: str = LIB_PATH):
                                         C.POINTER(SolveOpts), C.c_int, dp, vp, vp]),
         "biot_goal_mean_pressure": (C.c_int, [vp, dp, dp, vp, vp]),
         "biot_load_preset": (C.c_int, [vp, C.c_int, C.c_double, vp, vp]),
+        "biot_apply_part": (C.c_int, [vp, C.c_int, C.c_double, vp, vp, C.c_int, vp]),
+        "biot_profile": (C.c_int, [vp, C.c_int]),
+        "biot_counters": (C.c_int, [vp, i64p, i64p, C.POINTER(C.c_double)]),
         "biot_last_error": (C.c_char_p, [vp]),
         "biot_destroy": (None, [vp]),
     }
@@ -141,7 +145,7 @@ class Context:
         self.K = np.ascontiguousarray(np.asarray(coeffs["K"], dtype=np.float64))
         co = Coeffs(coeffs["b"], coeffs["invM"], coeffs["K_dr"], coeffs["lam"], coeffs["mu"], coeffs["eta"],
                     self.K.ctypes.data_as(C.POINTER(C.c_double)))
-        o = Opts(0, 0, 0, 0, -1.0)
+        o = Opts(0, 0, 0, 0, -1.0, 0)
         if opts:
             for k, v in opts.items():
                 setattr(o, k, v)
@@ -263,6 +267,22 @@ class Context:
         hi = (C.c_double * 3)(*[float(v) for v in hi] + [0.0] * (3 - len(hi)))
         return self._check(self.lib.biot_goal_mean_pressure(self.h, lo, hi, _ptr(j, torch.float64, self.n_space, "j"),
                                                             _stream()))
+
+    def apply_part(self, part, tau, x, y):
+        import torch
+        prec = FP64 if x.dtype == torch.float64 else FP32
+        dt = torch.float64 if prec == FP64 else torch.float32
+        return self._check(self.lib.biot_apply_part(self.h, int(part), float(tau), _ptr(x, dt, self.n_space, "in"),
+                                                    _ptr(y, dt, self.n_space, "out"), prec, _stream()))
+
+    def profile(self, enable):
+        return self._check(self.lib.biot_profile(self.h, int(bool(enable))))
+
+    def counters(self):
+        """(kernel launches so far, recorded operator launches, their device ms)."""
+        a, b, ms = C.c_int64(), C.c_int64(), C.c_double()
+        self._check(self.lib.biot_counters(self.h, C.byref(a), C.byref(b), C.byref(ms)))
+        return a.value, b.value, ms.value
 
     def load_preset(self, kind, value, f):
         import torch

@@ -14,6 +14,8 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <cstdlib>
+#include <map>
 #include <vector>
 
 #include "../../include/biot.h"
@@ -268,13 +270,29 @@ struct Krylov {
 template <typename T>
 struct PrecWork {
   T *tA = nullptr, *tB = nullptr;  // slab
-  T *fq = nullptr, *tq = nullptr;  // nt * Nq
+  T *fq = nullptr, *tq = nullptr, *fq2 = nullptr;  // nt * Nq
   T *gp = nullptr, *pp = nullptr, *pd = nullptr, *pAx = nullptr, *pxo = nullptr, *pdinv = nullptr;  // nt * Np
   double schur_tau = -1.0;
 };
 
+struct GraphKey {
+  int prec, transpose, j;
+  bool operator<(const GraphKey& o) const {
+    return prec != o.prec ? prec < o.prec : (transpose != o.transpose ? transpose < o.transpose : j < o.j);
+  }
+};
+struct GraphEntry {
+  cudaGraphExec_t exec;
+  double tau;
+  long long kernels;  // kernel nodes in the graph (for the launch counter)
+};
+
 struct biot_ctx {
   Grid g;
+  bool use_graphs = true;
+  std::map<GraphKey, GraphEntry> graphs;
+  cudaStream_t ws = nullptr;   // the library's own work stream (graphs need a capturable stream)
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   int r = 0, nt = 1;
   double b, invM, Kdr, lam, mu, eta, beta;
   std::vector<double> Kcell;
@@ -409,6 +427,7 @@ void ensure_prec(biot_ctx& c) {
   w.tB = dalloc<T>(nt * g.N);
   w.fq = dalloc<T>(nt * nqt);
   w.tq = dalloc<T>(nt * nqt);
+  w.fq2 = dalloc<T>(nt * nqt);
   w.gp = dalloc<T>(nt * g.Np);
   w.pp = dalloc<T>(nt * g.Np);
   w.pd = dalloc<T>(nt * g.Np);
@@ -456,6 +475,88 @@ double dev_dot(biot_ctx& c, const double* a, const double* b, int64_t n, cudaStr
   CK(cudaMemcpyAsync(c.hhost + 100, c.hdev + 100, sizeof(double), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   return c.hhost[100];
+}
+
+
+// ---- eigenvalue bounds ----------------------------------------------------------
+// Largest eigenvalue of Dinv Op (Op symmetric positive semi-definite, Dinv >= 0
+// diagonal) by `steps` preconditioned-CG steps, from the Lanczos tridiagonal
+// matrix built out of the CG coefficients (FP64).  nrhs independent systems
+// of length n (stride between them), the maximum over them is returned.
+double tridiag_lmax(const std::vector<double>& d, const std::vector<double>& e) {
+  // bisection with Sturm counts on the symmetric tridiagonal (d, e)
+  int k = (int)d.size();
+  if (k == 0) return 1.0;
+  double lo = 1e300, hi = -1e300;
+  for (int i = 0; i < k; ++i) {
+    double rad = (i > 0 ? std::fabs(e[i - 1]) : 0.0) + (i < k - 1 ? std::fabs(e[i]) : 0.0);
+    lo = std::min(lo, d[i] - rad);
+    hi = std::max(hi, d[i] + rad);
+  }
+  auto count_below = [&](double x) {
+    int cnt = 0;
+    double q = d[0] - x;
+    if (q < 0) ++cnt;
+    for (int i = 1; i < k; ++i) {
+      double qq = (q == 0.0) ? 1e-300 : q;
+      q = d[i] - x - e[i - 1] * e[i - 1] / qq;
+      if (q < 0) ++cnt;
+    }
+    return cnt;
+  };
+  for (int it = 0; it < 200; ++it) {
+    double mid = 0.5 * (lo + hi);
+    if (count_below(mid) >= k) hi = mid;
+    else lo = mid;
+  }
+  return hi;
+}
+
+template <class OpF>
+double lanczos_lmax(biot_ctx& c, OpF op, const double* dinv, int64_t dstride, int64_t n, int64_t stride, int nrhs, int steps,
+                    double* r, double* z, double* p, double* q, cudaStream_t st) {
+  std::vector<double> h((size_t)stride * nrhs, 0.0);
+  for (int k = 0; k < nrhs; ++k)
+    for (int64_t i = 0; i < n; ++i) h[k * stride + i] = 1.0 + 0.3 * std::sin(0.91 * (double)i + 0.7 * k) + 0.2 * std::cos(2.3 * (double)i);
+  CK(cudaMemcpyAsync(r, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+  // z = Dinv r, p = z (rows with Dinv = 0, the constrained ones, never enter the Krylov space)
+  launch_dinv_mul<double>(dinv, dstride, r, z, n, stride, nrhs, st);
+  CK(cudaMemcpyAsync(p, z, (size_t)stride * nrhs * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  CKL();
+  double best = 0.0;
+  std::vector<double> rz(nrhs), alpha_prev(nrhs, 0.0), beta_prev(nrhs, 0.0);
+  std::vector<std::vector<double>> dd(nrhs), ee(nrhs);
+  for (int k = 0; k < nrhs; ++k) rz[k] = dev_dot(c, r + k * stride, z + k * stride, n, st);
+  for (int it = 0; it < steps; ++it) {
+    op(p, q);
+    bool stop = false;
+    for (int k = 0; k < nrhs; ++k) {
+      double pq = dev_dot(c, p + k * stride, q + k * stride, n, st);
+      if (!(pq > 0) || !(rz[k] > 0)) { stop = true; continue; }
+      double alpha = rz[k] / pq;
+      dd[k].push_back(1.0 / alpha + (it > 0 ? beta_prev[k] / alpha_prev[k] : 0.0));
+      launch_axpby<double>(r + k * stride, q + k * stride, -alpha, 1.0, n, st);
+      alpha_prev[k] = alpha;
+    }
+    if (stop) break;
+    launch_dinv_mul<double>(dinv, dstride, r, z, n, stride, nrhs, st);
+    CKL();
+    for (int k = 0; k < nrhs; ++k) {
+      double rzn = dev_dot(c, r + k * stride, z + k * stride, n, st);
+      double beta = rzn / rz[k];
+      ee[k].push_back(std::sqrt(std::max(beta, 0.0)) / alpha_prev[k]);
+      beta_prev[k] = beta;
+      rz[k] = rzn;
+      launch_axpby<double>(p + k * stride, z + k * stride, 1.0, beta, n, st);  // p = z + beta p
+    }
+    CKL();
+  }
+  for (int k = 0; k < nrhs; ++k) {
+    std::vector<double> e(ee[k].begin(), ee[k].end());
+    if (e.size() >= dd[k].size() && !e.empty()) e.resize(dd[k].size() - 1);
+    best = std::max(best, tridiag_lmax(dd[k], e));
+  }
+  return best;
 }
 
 // ---- Chebyshev smoothing -----------------------------------------------------
@@ -526,12 +627,43 @@ void vcycle(biot_ctx& c, double tau, int nrhs, cudaStream_t st) {
 }
 
 // ---- flux-pressure Schur complement ---------------------------------------------
+// Shat p = cm Mp p + tau B Mq^{-1} B^T p, with Mq^{-1} exact (line solves) or lumped (diagonal)
 template <typename T>
 void schur_apply(biot_ctx& c, double tau, const double* cm, const T* p, T* out, int nrhs, cudaStream_t st) {
   PrecWork<T>& w = c.pw<T>();
   const Grid& g = c.g;
   int64_t nqt = g.nq[0] + g.nq[1] + g.nq[2];
-  launch_schur_apply<T>(g, c.tab<T>(), p, g.Np, c.dmq<T>(), w.tq, nqt, tau, cm, out, g.Np, nrhs, st);
+  if (c.opts.lumped_flux_mass) {
+    launch_schur_apply<T>(g, c.tab<T>(), p, g.Np, c.dmq<T>(), w.tq, nqt, tau, cm, out, g.Np, nrhs, st);
+  } else {
+    launch_BTp<T>(g, c.tab<T>(), p, g.Np, nullptr, 0, w.tq, nqt, 1.0, nrhs, st);
+    launch_mq_line_solve<T>(g, c.tab<T>(), c.kscale<T>(), w.tq, nqt, w.fq2, nqt, 1.0, nrhs, st);
+    launch_schur_out<T>(g, c.tab<T>(), p, g.Np, w.fq2, nqt, tau, cm, out, g.Np, nrhs, st);
+  }
+  CKL();
+}
+
+// q = (tau Mq)^{-1} (base + coef B^T p) on free flux DoFs, base on constrained ones
+template <typename T>
+void flux_solve(biot_ctx& c, double tau, const T* base, int64_t sb, const T* p, double coef, T* qo, int64_t so, int nrhs,
+                cudaStream_t st) {
+  PrecWork<T>& w = c.pw<T>();
+  const Grid& g = c.g;
+  int64_t nqt = g.nq[0] + g.nq[1] + g.nq[2];
+  if (c.opts.lumped_flux_mass) {
+    if (p) launch_q_final<T>(g, c.tab<T>(), base, sb, p, g.Np, c.dmq<T>(), tau, coef, qo, so, nrhs, st);
+    else launch_q_jacobi<T>(g, c.tab<T>(), base, sb, c.dmq<T>(), tau, qo, so, nrhs, st);
+  } else {
+    const T* rhs = base;
+    int64_t sr = sb;
+    if (p) {
+      launch_BTp<T>(g, c.tab<T>(), p, g.Np, base, sb, w.tq, nqt, coef, nrhs, st);
+      rhs = w.tq;
+      sr = nqt;
+    }
+    launch_mq_line_solve<T>(g, c.tab<T>(), c.kscale<T>(), rhs, sr, qo, so, tau, nrhs, st);
+    launch_q_fix_constrained<T>(g, base, sb, qo, so, nrhs, st);
+  }
   CKL();
 }
 
@@ -539,8 +671,7 @@ void schur_cm(const biot_ctx& c, double* cm) {
   for (int k = 0; k < c.nt; ++k) cm[k] = c.tb.lam[k] * (c.invM + c.beta);
 }
 
-// largest eigenvalue of Dinv Shat (power iteration in FP64 on every rhs, max over rhs),
-// cached per tau
+// largest eigenvalue of Dinv Shat (CG-Lanczos in FP64 on every rhs, max over rhs), cached per tau
 double schur_lmax(biot_ctx& c, double tau, cudaStream_t st) {
   if (c.schur_lmax_tau == tau) return c.schur_lmax;
   ensure_prec<double>(c);
@@ -550,24 +681,8 @@ double schur_lmax(biot_ctx& c, double tau, cudaStream_t st) {
   schur_cm(c, cm);
   launch_schur_dinv<double>(g, c.t64, c.sb2_64, cm, tau, w.pdinv, c.nt, st);
   CKL();
-  std::vector<double> h(g.Np * c.nt);
-  for (int64_t i = 0; i < (int64_t)h.size(); ++i) h[i] = 1.0 + 0.37 * std::sin(0.7 * (double)i);
-  CK(cudaMemcpyAsync(w.gp, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice, st));
-  CK(cudaStreamSynchronize(st));
-  double lm = 1.0;
-  for (int it = 0; it < 25; ++it) {
-    schur_apply<double>(c, tau, cm, w.gp, w.pAx, c.nt, st);
-    launch_cheb_update_r<double>(w.pAx, w.pAx, w.pdinv, w.pd, w.pAx, w.pp, 0.0, 1.0, 1, g.Np, c.nt, st);  // pp = Dinv S gp
-    CKL();
-    lm = 0;
-    for (int r = 0; r < c.nt; ++r) {
-      double ny = std::sqrt(dev_dot(c, w.pp + r * g.Np, w.pp + r * g.Np, g.Np, st));
-      double nx = std::sqrt(dev_dot(c, w.gp + r * g.Np, w.gp + r * g.Np, g.Np, st));
-      lm = std::max(lm, ny / nx);
-      launch_axpby<double>(w.gp + r * g.Np, w.pp + r * g.Np, 1.0 / ny, 0.0, g.Np, st);
-      CKL();
-    }
-  }
+  auto op = [&](const double* x, double* y) { schur_apply<double>(c, tau, cm, x, y, c.nt, st); };
+  double lm = lanczos_lmax(c, op, w.pdinv, g.Np, g.Np, g.Np, c.nt, 24, w.gp, w.pp, w.pd, w.pAx, st);
   c.schur_lmax = lm;
   c.schur_lmax_tau = tau;
   return lm;
@@ -586,7 +701,7 @@ void schur_solve(biot_ctx& c, double tau, cudaStream_t st) {
     CKL();
     w.schur_tau = tau;
   }
-  ChebCoef cc = cheb_coefs(c.opts.schur_degree, lmax / 30.0, 1.05 * lmax);
+  ChebCoef cc = cheb_coefs(c.opts.schur_degree, lmax / 30.0, 1.1 * lmax);
   for (int k = 0; k < cc.n; ++k) {
     bool first = (k == 0);
     if (!first) schur_apply<T>(c, tau, cm, w.pp, w.pAx, c.nt, st);
@@ -620,13 +735,11 @@ void precondition_T(biot_ctx& c, double tau, const T* R, T* Z, int transpose, cu
   launch_time_mix<T, T>(R, N, w.tA, N, nt, Wm, N, st);
   CKL();
   if (!transpose) {
-    launch_q_jacobi<T>(g, c.tab<T>(), w.tA + Nu, N, c.dmq<T>(), tau, w.fq, nqt, nt, st);
-    CKL();
+    flux_solve<T>(c, tau, w.tA + Nu, N, nullptr, 0.0, w.fq, nqt, nt, st);
     launch_p_minus_Bq<T>(g, c.tab<T>(), w.tA + g.offp, N, w.fq, nqt, tau, w.gp, Np, nt, st);
     CKL();
     schur_solve<T>(c, tau, st);
-    launch_q_final<T>(g, c.tab<T>(), w.tA + Nu, N, w.pp, Np, c.dmq<T>(), tau, tau, w.tB + Nu, N, nt, st);
-    CKL();
+    flux_solve<T>(c, tau, w.tA + Nu, N, w.pp, tau, w.tB + Nu, N, nt, st);
     copy2d<T>(w.tB + g.offp, N, w.pp, Np, Np, nt, st);
     launch_u_rhs<T>(g, c.tab<T>(), w.tA, N, w.pp, Np, c.b * tau, lw.b, Nu, nt, st);
     CKL();
@@ -638,13 +751,11 @@ void precondition_T(biot_ctx& c, double tau, const T* R, T* Z, int transpose, cu
     copy2d<T>(w.tB, N, lw.x, Nu, Nu, nt, st);
     launch_p_plus_ETu<T>(g, c.tab<T>(), w.tA + g.offp, N, lw.x, Nu, c.b * tau, w.gp, Np, nt, st);
     CKL();
-    launch_q_jacobi<T>(g, c.tab<T>(), w.tA + Nu, N, c.dmq<T>(), tau, w.fq, nqt, nt, st);
-    CKL();
+    flux_solve<T>(c, tau, w.tA + Nu, N, nullptr, 0.0, w.fq, nqt, nt, st);
     launch_p_minus_Bq<T>(g, c.tab<T>(), w.gp, Np, w.fq, nqt, -tau, w.gp, Np, nt, st);
     CKL();
     schur_solve<T>(c, tau, st);
-    launch_q_final<T>(g, c.tab<T>(), w.tA + Nu, N, w.pp, Np, c.dmq<T>(), tau, -tau, w.tB + Nu, N, nt, st);
-    CKL();
+    flux_solve<T>(c, tau, w.tA + Nu, N, w.pp, -tau, w.tB + Nu, N, nt, st);
     copy2d<T>(w.tB + g.offp, N, w.pp, Np, Np, nt, st);
   }
   launch_time_mix<T, T>(w.tB, N, Z, N, nt, Vm, N, st);
@@ -652,30 +763,103 @@ void precondition_T(biot_ctx& c, double tau, const T* R, T* Z, int transpose, cu
 }
 
 // ---- flexible GMRES(m), right preconditioned -------------------------------------
+// One Arnoldi step j: z_j = P v_j, w = calA z_j, classical Gram-Schmidt twice
+// with fused multi-dot / multi-axpy, normalisation by a device-side 1/||w||.
+// Results: h1 in hdev[0..j], h2 in hdev[64..64+j], ||w||^2 in hdev[128].
+template <typename T>
+void arnoldi_step_body(biot_ctx& c, double tau, int transpose, int j, cudaStream_t st) {
+  Krylov<T>& K = c.kry<T>();
+  const int64_t n = c.g.N * c.nt;
+  double* hd = c.hdev;
+  precondition_T<T>(c, tau, K.V[j], K.Z[j], transpose, st);
+  apply_slab_T<T>(c, tau, K.Z[j], K.V[j + 1], transpose, st);
+  T* w = K.V[j + 1];
+  launch_multidot<T>(K.dV, j + 1, w, n, c.partial, hd, st);
+  launch_multiaxpy_dot<T>(K.dV, j + 1, hd, w, n, 1, c.partial, hd + 64, st);
+  launch_multiaxpy_dot<T>(K.dV, j + 1, hd + 64, w, n, 2, c.partial, hd + 128, st);
+  launch_scale_into<T>(w, w, hd + 129, 0, n, st);  // hd[129] = 1/||w|| from the norm reduction
+  CKL();
+}
+
+template <typename T> constexpr int prec_id();
+template <> constexpr int prec_id<double>() { return 0; }
+template <> constexpr int prec_id<float>() { return 1; }
+
+// precompute what the preconditioner needs for this tau (host syncs, so never inside a capture)
+template <typename T>
+void prec_prepare(biot_ctx& c, double tau, cudaStream_t st) {
+  ensure_prec<T>(c);
+  PrecWork<T>& w = c.pw<T>();
+  double lm = schur_lmax(c, tau, st);
+  (void)lm;
+  if (w.schur_tau != tau) {
+    double cm[MAXR];
+    schur_cm(c, cm);
+    launch_schur_dinv<T>(c.g, c.tab<T>(), c.sb2<T>(), cm, tau, w.pdinv, c.nt, st);
+    CKL();
+    w.schur_tau = tau;
+  }
+}
+
+template <typename T>
+void arnoldi_step(biot_ctx& c, double tau, int transpose, int j, cudaStream_t st) {
+  if (!c.use_graphs || prof_enabled()) {
+    arnoldi_step_body<T>(c, tau, transpose, j, st);
+    return;
+  }
+  GraphKey key{prec_id<T>(), transpose, j};
+  auto it = c.graphs.find(key);
+  if (it != c.graphs.end() && it->second.tau != tau) {
+    cudaGraphExecDestroy(it->second.exec);
+    c.graphs.erase(it);
+    it = c.graphs.end();
+  }
+  if (it == c.graphs.end()) {
+    cudaGraph_t gr;
+    long long k0 = launch_count();
+    CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    arnoldi_step_body<T>(c, tau, transpose, j, st);
+    CK(cudaStreamEndCapture(st, &gr));
+    long long nk = launch_count() - k0;
+    note_launches(-nk);  // captured, not launched
+    cudaGraphExec_t ex;
+    CK(cudaGraphInstantiate(&ex, gr, 0));
+    cudaGraphDestroy(gr);
+    GraphEntry e{ex, tau, nk};
+    it = c.graphs.emplace(key, e).first;
+  }
+  CK(cudaGraphLaunch(it->second.exec, st));
+  note_launches(it->second.kernels);
+}
+
 // Solves calA x = b (precision T) to ||b - calA x|| <= tol_abs.  Returns BIOT_OK,
-// BIOT_ENOCONV or BIOT_EBREAKDOWN.
+// BIOT_ENOCONV or BIOT_EBREAKDOWN.  single_cycle: x = 0 on entry, one Arnoldi
+// cycle only, no closing true residual (the mixed-precision inner solve; the
+// outer FP64 refinement measures the true residual).
 template <typename T>
 int gmres(biot_ctx& c, double tau, int transpose, const T* b, T* x, double tol_abs, int maxit, int& iters, int& restarts,
-          double& resnorm, cudaStream_t st) {
+          double& resnorm, cudaStream_t st, bool single_cycle = false) {
   const int m = c.opts.gmres_restart;
   ensure_krylov<T>(c, m);
-  ensure_prec<T>(c);
+  prec_prepare<T>(c, tau, st);
   Krylov<T>& K = c.kry<T>();
   const int64_t n = c.g.N * c.nt;
   std::vector<double> H((m + 1) * m), cs(m), sn(m), gv(m + 1), y(m);
-  double* hd = c.hdev;  // [0..m]: h1, [64..64+m]: h2, [128]: norm^2
+  double* hd = c.hdev;
   auto norm2 = [&](T* v) -> double {
-    // ||V_0||^2 (K.dV[0] == V_0 == v)
-    launch_multidot<T>(K.dV, 1, v, n, c.partial, hd + 128, st);
+    launch_multidot<T>(K.dV, 1, v, n, c.partial, hd + 128, st);  // K.dV[0] == V_0 == v
     CKL();
     CK(cudaMemcpyAsync(c.hhost + 128, hd + 128, sizeof(double), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     return c.hhost[128];
   };
-  // r0 = b - A x
-  apply_slab_T<T>(c, tau, x, K.V[0], transpose, st);
-  launch_axpby<T>(K.V[0], b, 1.0, -1.0, n, st);
-  CKL();
+  if (single_cycle) {
+    CK(cudaMemcpyAsync(K.V[0], b, n * sizeof(T), cudaMemcpyDeviceToDevice, st));
+  } else {
+    apply_slab_T<T>(c, tau, x, K.V[0], transpose, st);
+    launch_axpby<T>(K.V[0], b, 1.0, -1.0, n, st);
+    CKL();
+  }
   double beta = std::sqrt(norm2(K.V[0]));
   resnorm = beta;
   while (true) {
@@ -687,27 +871,14 @@ int gmres(biot_ctx& c, double tau, int transpose, const T* b, T* x, double tol_a
     std::fill(gv.begin(), gv.end(), 0.0);
     gv[0] = beta;
     int jl = -1;
-    bool done = false;
     for (int j = 0; j < m; ++j) {
-      precondition_T<T>(c, tau, K.V[j], K.Z[j], transpose, st);
-      apply_slab_T<T>(c, tau, K.Z[j], K.V[j + 1], transpose, st);
-      T* w = K.V[j + 1];
-      launch_multidot<T>(K.dV, j + 1, w, n, c.partial, hd, st);
-      CKL();
-      launch_multiaxpy_dot<T>(K.dV, j + 1, hd, w, n, 1, c.partial, hd + 64, st);
-      CKL();
-      launch_multiaxpy_dot<T>(K.dV, j + 1, hd + 64, w, n, 2, c.partial, hd + 128, st);
-      CKL();
+      arnoldi_step<T>(c, tau, transpose, j, st);
       CK(cudaMemcpyAsync(c.hhost, hd, 130 * sizeof(double), cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));
       for (int i = 0; i <= j; ++i) H[i * m + j] = c.hhost[i] + c.hhost[64 + i];
       double hn = std::sqrt(std::max(c.hhost[128], 0.0));
       if (!std::isfinite(hn)) return BIOT_EBREAKDOWN;
       H[(j + 1) * m + j] = hn;
-      if (hn > 0) {
-        launch_axpby<T>(w, w, 0.0, 1.0 / hn, n, st);
-        CKL();
-      }
       for (int i = 0; i < j; ++i) {
         double a = H[i * m + j], bb = H[(i + 1) * m + j];
         H[i * m + j] = cs[i] * a + sn[i] * bb;
@@ -723,9 +894,9 @@ int gmres(biot_ctx& c, double tau, int transpose, const T* b, T* x, double tol_a
       gv[j] = cs[j] * gv[j];
       ++iters;
       jl = j;
-      if (std::fabs(gv[j + 1]) <= tol_abs || iters >= maxit || hn == 0.0) { done = true; break; }
+      if (std::fabs(gv[j + 1]) <= tol_abs || iters >= maxit || hn == 0.0) break;
     }
-    // y = H^{-1} g
+    // y = H^{-1} g, x += Z y
     for (int i = jl; i >= 0; --i) {
       double s = gv[i];
       for (int k = i + 1; k <= jl; ++k) s -= H[i * m + k] * y[k];
@@ -734,21 +905,35 @@ int gmres(biot_ctx& c, double tau, int transpose, const T* b, T* x, double tol_a
     CK(cudaMemcpyAsync(hd + 160, y.data(), (jl + 1) * sizeof(double), cudaMemcpyHostToDevice, st));
     launch_lincomb_add<T, T>(x, K.dV + (m + 1), jl + 1, hd + 160, n, st);
     CKL();
-    // true residual
+    if (single_cycle) {
+      resnorm = std::fabs(gv[jl + 1]);
+      return BIOT_OK;
+    }
     apply_slab_T<T>(c, tau, x, K.V[0], transpose, st);
     launch_axpby<T>(K.V[0], b, 1.0, -1.0, n, st);
     CKL();
     beta = std::sqrt(norm2(K.V[0]));
     resnorm = beta;
     ++restarts;
-    (void)done;
   }
 }
 
 // ---- slab solve ---------------------------------------------------------------------
 int solve_slab_impl(biot_ctx& c, double tau, const double* rhs, double* x, const biot_solve_opts& o, biot_stats& s,
-                    cudaStream_t st) {
+                    cudaStream_t st_user) {
   double t0 = now_s();
+  // all solver work runs on the library's own (capturable) stream, ordered after the caller's stream
+  CK(cudaEventRecord(c.ev_in, st_user));
+  CK(cudaStreamWaitEvent(c.ws, c.ev_in, 0));
+  cudaStream_t st = c.ws;
+  struct Rejoin {
+    biot_ctx& c;
+    cudaStream_t su;
+    ~Rejoin() {
+      cudaEventRecord(c.ev_out, c.ws);
+      cudaStreamWaitEvent(su, c.ev_out, 0);
+    }
+  } rejoin{c, st_user};
   const int64_t n = c.g.N * c.nt;
   int iters = 0, restarts = 0, refs = 0;
   double res = 0;
@@ -782,8 +967,8 @@ int solve_slab_impl(biot_ctx& c, double tau, const double* rhs, double* x, const
       CKL();
       int it_in = 0, rs_in = 0;
       double res_in = 0;
-      int budget = std::min(o.max_iters - iters, 3 * c.opts.gmres_restart);
-      int rci = gmres<float>(c, tau, o.transpose, c.r32, c.d32, o.inner_tol, budget, it_in, rs_in, res_in, st);
+      int budget = std::min(o.max_iters - iters, c.opts.gmres_restart);
+      int rci = gmres<float>(c, tau, o.transpose, c.r32, c.d32, o.inner_tol, budget, it_in, rs_in, res_in, st, true);
       iters += it_in;
       restarts += rs_in;
       if (rci == BIOT_EBREAKDOWN) { rc = rci; break; }
@@ -802,29 +987,10 @@ int solve_slab_impl(biot_ctx& c, double tau, const double* rhs, double* x, const
 }
 
 // ---- multigrid set-up ----------------------------------------------------------------
-double power_lmax_A(biot_ctx& c, Level& L, cudaStream_t st) {
-  // power iteration on Dinv A (FP64, one vector); uses the level's FP64 work arrays
+double level_lmax(biot_ctx& c, Level& L, cudaStream_t st) {
   LevelWork<double>& w = L.w64;
-  int64_t n = L.g.Nu;
-  std::vector<double> h(n);
-  for (int64_t i = 0; i < n; ++i) h[i] = 1.0 + 0.5 * std::sin(0.37 * (double)i + 0.1);
-  CK(cudaMemcpy(w.x, h.data(), n * sizeof(double), cudaMemcpyHostToDevice));
-  launch_mask_u<double>(L.g, w.x, 0, 1, st);
-  double lm = 1.0;
-  for (int it = 0; it < 30; ++it) {
-    apply_A<double>(L, c.lam, c.mu, 1.0, w.x, w.Ax, 1, st);
-    // xo = Dinv Ax (zero on constrained rows via first-step form with b = Ax)
-    launch_cheb_update<double>(w.Ax, w.Ax, L.dinv64, w.d, w.x, w.xo, 0.0, 1.0, 1, n, 1, n, st);
-    CKL();
-    // constrained rows copied b = Ax = x there: zero them for the estimate
-    launch_mask_u<double>(L.g, w.xo, 0, 1, st);
-    double nn = std::sqrt(dev_dot(c, w.xo, w.xo, n, st));
-    double nx = std::sqrt(dev_dot(c, w.x, w.x, n, st));
-    lm = nn / nx;
-    launch_axpby<double>(w.x, w.xo, 1.0 / nn, 0.0, n, st);
-    CKL();
-  }
-  return lm;
+  auto op = [&](const double* x, double* y) { apply_A<double>(L, c.lam, c.mu, 1.0, x, y, 1, st); };
+  return lanczos_lmax(c, op, L.dinv64, 0, L.g.Nu, L.g.Nu, 1, 24, w.x, w.xo, w.d, w.Ax, st);
 }
 
 void build_levels(biot_ctx& c, cudaStream_t st) {
@@ -872,13 +1038,13 @@ void build_levels(biot_ctx& c, cudaStream_t st) {
     CK(cudaMemcpy(L.dinv32, hf.data(), n * sizeof(float), cudaMemcpyHostToDevice));
   }
   ensure_prec<double>(c);
-  for (Level& L : c.lv) L.lmax = power_lmax_A(c, L, st);
+  for (Level& L : c.lv) L.lmax = level_lmax(c, L, st);
   // dense coarse inverse when the coarsest level is small
   Level& Lc = c.lv.back();
   int64_t nc = Lc.g.Nu;
   c.Ainv = nullptr;
   c.ncoarse = 0;
-  if (nc <= 4000) {
+  if (nc <= 1500) {
     std::vector<double> A(nc * nc);
     double* e = dalloc<double>(3 * nc);
     double* ae = dalloc<double>(3 * nc);
@@ -895,11 +1061,11 @@ void build_levels(biot_ctx& c, cudaStream_t st) {
     }
     cudaFree(e);
     cudaFree(ae);
-    // Cholesky-based inverse in long double
-    std::vector<long double> Lm(nc * nc, 0.0L);
+    // Cholesky-based inverse (FP64, host, set-up only)
+    std::vector<double> Lm(nc * nc, 0.0);
     for (int64_t i = 0; i < nc; ++i)
       for (int64_t j = 0; j <= i; ++j) {
-        long double s = 0.5L * ((long double)A[i * nc + j] + (long double)A[j * nc + i]);
+        double s = 0.5 * (A[i * nc + j] + A[j * nc + i]);
         for (int64_t k = 0; k < j; ++k) s -= Lm[i * nc + k] * Lm[j * nc + k];
         if (i == j) {
           if (s <= 0) fail(BIOT_EINVAL, "coarse elasticity matrix is not positive definite (check boundary conditions)");
@@ -908,11 +1074,11 @@ void build_levels(biot_ctx& c, cudaStream_t st) {
           Lm[i * nc + j] = s / Lm[j * nc + j];
       }
     // inverse of L (lower), then A^{-1} = L^{-T} L^{-1}
-    std::vector<long double> Li(nc * nc, 0.0L);
+    std::vector<double> Li(nc * nc, 0.0);
     for (int64_t j = 0; j < nc; ++j) {
-      Li[j * nc + j] = 1.0L / Lm[j * nc + j];
+      Li[j * nc + j] = 1.0 / Lm[j * nc + j];
       for (int64_t i = j + 1; i < nc; ++i) {
-        long double s = 0;
+        double s = 0;
         for (int64_t k = j; k < i; ++k) s -= Lm[i * nc + k] * Li[k * nc + j];
         Li[i * nc + j] = s / Lm[i * nc + i];
       }
@@ -920,7 +1086,7 @@ void build_levels(biot_ctx& c, cudaStream_t st) {
     std::vector<double> Ai(nc * nc);
     for (int64_t i = 0; i < nc; ++i)
       for (int64_t j = 0; j <= i; ++j) {
-        long double s = 0;
+        double s = 0;
         for (int64_t k = i; k < nc; ++k) s += Li[k * nc + i] * Li[k * nc + j];
         Ai[i * nc + j] = Ai[j * nc + i] = (double)s;
       }
@@ -1120,6 +1286,11 @@ extern "C" int biot_setup(const biot_mesh* mesh, const biot_coeffs* co, int r, c
     if (!(co->invM >= 0) || !(co->K_dr > 0) || !(co->mu > 0) || !(co->lambda >= 0) || !(co->eta > 0))
       fail(BIOT_EINVAL, "coefficients out of range");
     if (!co->K_cell) fail(BIOT_EINVAL, "K_cell is NULL");
+    apply_init_attributes();
+    {
+      const char* ng = std::getenv("BIOT_NO_GRAPHS");
+      c->use_graphs = !(ng && ng[0] == '1');
+    }
     c->g = make_grid(mesh->dim, mesh->n, mesh->lo, mesh->hi, mesh->u_bc, mesh->f_bc);
     c->r = r;
     c->nt = r + 1;
@@ -1132,15 +1303,17 @@ extern "C" int biot_setup(const biot_mesh* mesh, const biot_coeffs* co, int r, c
     biot_opts d;
     d.gmres_restart = 30;
     d.cheb_degree = 4;
-    d.schur_degree = 8;
+    d.schur_degree = 32;
     d.mg_min_cells = 2;
     d.beta_fs = -1;
+    d.lumped_flux_mass = 0;
     if (opts) {
       if (opts->gmres_restart > 0) d.gmres_restart = std::min(opts->gmres_restart, 60);
       if (opts->cheb_degree > 0) d.cheb_degree = std::min(opts->cheb_degree, 30);
       if (opts->schur_degree > 0) d.schur_degree = std::min(opts->schur_degree, 30);
       if (opts->mg_min_cells > 0) d.mg_min_cells = opts->mg_min_cells;
       d.beta_fs = opts->beta_fs;
+      d.lumped_flux_mass = opts->lumped_flux_mass;
     }
     c->opts = d;
     c->beta = (d.beta_fs > 0) ? d.beta_fs : c->b * c->b / c->Kdr;
@@ -1156,6 +1329,9 @@ extern "C" int biot_setup(const biot_mesh* mesh, const biot_coeffs* co, int r, c
     c->sb2_64 = dalloc<double>(g.Np);
     c->sb2_32 = dalloc<float>(g.Np);
     c->hdev = dalloc<double>(512);
+    CK(cudaStreamCreateWithFlags(&c->ws, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming));
     c->ptrbuf = dalloc<void*>(64);
     CK(cudaMallocHost((void**)&c->hptr, 64 * sizeof(void*)));
     CK(cudaMallocHost((void**)&c->hhost, 512 * sizeof(double)));
@@ -1477,6 +1653,63 @@ extern "C" int biot_load_preset(biot_t c, int kind, double value, double* f, voi
   API_END(c)
 }
 
+namespace {
+template <typename T>
+void apply_part_T(biot_ctx& c, int part, double tau, const T* in, T* out, cudaStream_t st) {
+  ensure_prec<T>(c);
+  const Grid& g = c.g;
+  PrecWork<T>& w = c.pw<T>();
+  int64_t nqt = g.nq[0] + g.nq[1] + g.nq[2];
+  CK(cudaMemsetAsync(out, 0, g.N * sizeof(T), st));
+  if (part == BIOT_PART_FLUX_MASS_INV) {
+    launch_mq_line_solve<T>(g, c.tab<T>(), c.kscale<T>(), in + g.Nu, nqt, out + g.Nu, nqt, tau, 1, st);
+    launch_q_fix_constrained<T>(g, in + g.Nu, nqt, out + g.Nu, nqt, 1, st);
+  } else if (part == BIOT_PART_SCHUR) {
+    double cm[1] = {c.invM + c.beta};
+    schur_apply<T>(c, tau, cm, in + g.offp, out + g.offp, 1, st);
+  } else if (part == BIOT_PART_VCYCLE) {
+    LevelWork<T>& lw = lwork<T>(c.lv[0]);
+    CK(cudaMemcpyAsync(lw.b, in, g.Nu * sizeof(T), cudaMemcpyDeviceToDevice, st));
+    vcycle<T>(c, tau, 1, st);
+    CK(cudaMemcpyAsync(out, lw.x, g.Nu * sizeof(T), cudaMemcpyDeviceToDevice, st));
+  } else if (part == BIOT_PART_ELASTICITY) {
+    apply_A<T>(c.lv[0], c.lam, c.mu, tau, in, out, 1, st);
+  } else {
+    fail(BIOT_EINVAL, "unknown part");
+  }
+  CKL();
+  (void)w;
+}
+}  // namespace
+
+extern "C" int biot_apply_part(biot_t c, int part, double tau, const void* in, void* out, int prec, void* stream) {
+  API_BEGIN(c)
+  if (!in || !out || !(tau > 0)) fail(BIOT_EINVAL, "apply_part: NULL vector or tau <= 0");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (prec == BIOT_FP64) apply_part_T<double>(*c, part, tau, (const double*)in, (double*)out, st);
+  else if (prec == BIOT_FP32) apply_part_T<float>(*c, part, tau, (const float*)in, (float*)out, st);
+  else fail(BIOT_EINVAL, "prec must be BIOT_FP64 or BIOT_FP32");
+  return BIOT_OK;
+  API_END(c)
+}
+
+extern "C" int biot_counters(biot_t c, int64_t* launches, int64_t* op_launches, double* op_ms) {
+  if (!c) return BIOT_EINVAL;
+  if (launches) *launches = (int64_t)launch_count();
+  long long n = 0;
+  double ms = 0;
+  prof_collect(0, &n, &ms);
+  if (op_launches) *op_launches = n;
+  if (op_ms) *op_ms = ms;
+  return BIOT_OK;
+}
+
+extern "C" int biot_profile(biot_t c, int enable) {
+  if (!c) return BIOT_EINVAL;
+  prof_enable(enable != 0);
+  return BIOT_OK;
+}
+
 extern "C" const char* biot_last_error(biot_t c) {
   if (!c) return g_err_msg.c_str();
   return c->err.c_str();
@@ -1501,7 +1734,11 @@ extern "C" void biot_destroy(biot_t c) {
     F((void*)K.dV); F(K.tmp);
   };
   FK(c->k64); FK(c->k32);
-  auto FP = [&](auto& w) { F(w.tA); F(w.tB); F(w.fq); F(w.tq); F(w.gp); F(w.pp); F(w.pd); F(w.pAx); F(w.pxo); F(w.pdinv); };
+  for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second.exec);
+  if (c->ev_in) cudaEventDestroy(c->ev_in);
+  if (c->ev_out) cudaEventDestroy(c->ev_out);
+  if (c->ws) cudaStreamDestroy(c->ws);
+  auto FP = [&](auto& w) { F(w.tA); F(w.tB); F(w.fq); F(w.tq); F(w.fq2); F(w.gp); F(w.pp); F(w.pd); F(w.pAx); F(w.pxo); F(w.pdinv); };
   FP(c->p64); FP(c->p32);
   for (void* p : c->extra) F(p);
   delete c;

@@ -431,16 +431,14 @@ void launch_apply_u(const Grid& g, const TabT<T>& tb, const SlabCoef& sc, const 
   if (g.dim == 3) {
     dim3 grid((g.nu[0] + T3 - 1) / T3, (g.nu[1] + T3 - 1) / T3, (g.nu[2] + T3 - 1) / T3);
     size_t smem = sizeof(T) * (3 * H3 * H3 * H3 + 4 * H3 * H3 * T3 + 12 * H3 * T3 * T3);
-    static bool attr_set[2] = {false, false};
-    int which = sizeof(T) == 8;
-    if (!attr_set[which]) {
-      cudaFuncSetAttribute(k_apply_u3<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      attr_set[which] = true;
-    }
-    k_apply_u3<T><<<grid, 256, smem, st>>>(g, tb, sc, u, su, p, sp, y, sy);
+    prof_begin(st, 0);
+    (note_launch(), k_apply_u3<T><<<grid, 256, smem, st>>>(g, tb, sc, u, su, p, sp, y, sy));
+    prof_end(st, 0);
   } else {
     dim3 grid((g.nu[0] + T2 - 1) / T2, (g.nu[1] + T2 - 1) / T2, 1);
-    k_apply_u2<T><<<grid, 256, 0, st>>>(g, tb, sc, u, su, p, sp, y, sy);
+    prof_begin(st, 0);
+    (note_launch(), k_apply_u2<T><<<grid, 256, 0, st>>>(g, tb, sc, u, su, p, sp, y, sy));
+    prof_end(st, 0);
   }
 }
 
@@ -449,23 +447,34 @@ void launch_apply_q(const Grid& g, const TabT<T>& tb, const SlabCoef& sc, const 
                     int64_t sy, cudaStream_t st) {
   int64_t n = g.nq[0] + g.nq[1] + g.nq[2];
   int blocks = (int)((n + 255) / 256);
-  if (g.dim == 3) k_apply_q<T, 3><<<blocks, 256, 0, st>>>(g, tb, sc, kscale, x, sx, y, sy);
-  else k_apply_q<T, 2><<<blocks, 256, 0, st>>>(g, tb, sc, kscale, x, sx, y, sy);
+  if (g.dim == 3) (note_launch(), k_apply_q<T, 3><<<blocks, 256, 0, st>>>(g, tb, sc, kscale, x, sx, y, sy));
+  else (note_launch(), k_apply_q<T, 2><<<blocks, 256, 0, st>>>(g, tb, sc, kscale, x, sx, y, sy));
 }
 
 template <typename T>
 void launch_apply_p(const Grid& g, const TabT<T>& tb, const SlabCoef& sc, const T* x, int64_t sx, T* y, int64_t sy,
                     cudaStream_t st) {
   int blocks = (int)((g.Np + 255) / 256);
-  if (g.dim == 3) k_apply_p<T, 3><<<blocks, 256, 0, st>>>(g, tb, sc, x, sx, y, sy);
-  else k_apply_p<T, 2><<<blocks, 256, 0, st>>>(g, tb, sc, x, sx, y, sy);
+  if (g.dim == 3) (note_launch(), k_apply_p<T, 3><<<blocks, 256, 0, st>>>(g, tb, sc, x, sx, y, sy));
+  else (note_launch(), k_apply_p<T, 2><<<blocks, 256, 0, st>>>(g, tb, sc, x, sx, y, sy));
 }
 
 template <typename T>
 void launch_diag_A(const Grid& g, const TabT<T>& tb, double lam, double mu, T* d, cudaStream_t st) {
   int blocks = (int)((g.nnode + 255) / 256);
-  if (g.dim == 3) k_diag_A<T, 3><<<blocks, 256, 0, st>>>(g, tb, lam, mu, d);
-  else k_diag_A<T, 2><<<blocks, 256, 0, st>>>(g, tb, lam, mu, d);
+  if (g.dim == 3) (note_launch(), k_diag_A<T, 3><<<blocks, 256, 0, st>>>(g, tb, lam, mu, d));
+  else (note_launch(), k_diag_A<T, 2><<<blocks, 256, 0, st>>>(g, tb, lam, mu, d));
+}
+
+// opt-in shared memory sizes, set once per process before any launch (and so before any graph capture)
+void apply_init_attributes() {
+  static bool done = false;
+  if (done) return;
+  cudaFuncSetAttribute(k_apply_u3<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)(sizeof(double) * (3 * H3 * H3 * H3 + 4 * H3 * H3 * T3 + 12 * H3 * T3 * T3)));
+  cudaFuncSetAttribute(k_apply_u3<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)(sizeof(float) * (3 * H3 * H3 * H3 + 4 * H3 * H3 * T3 + 12 * H3 * T3 * T3)));
+  done = true;
 }
 
 #define INST(T)                                                                                                        \

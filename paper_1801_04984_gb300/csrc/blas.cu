@@ -86,7 +86,9 @@ __global__ void __launch_bounds__(256) k_multidot(const TV* const* __restrict__ 
 }
 
 // sum partial[b][i] over blocks b (fixed order) -> out[i]
-__global__ void k_final_reduce(const double* __restrict__ partial, int nblocks, int cnt, int stride, double* __restrict__ out) {
+// rsq (optional): receives 1/sqrt(out[0]) (0 when out[0] <= 0), the normalisation factor of a squared norm
+__global__ void k_final_reduce(const double* __restrict__ partial, int nblocks, int cnt, int stride, double* __restrict__ out,
+                               double* __restrict__ rsq = nullptr) {
   __shared__ double sh[256];
   for (int i = 0; i < cnt; ++i) {
     double s = 0;
@@ -97,7 +99,10 @@ __global__ void k_final_reduce(const double* __restrict__ partial, int nblocks, 
       if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
       __syncthreads();
     }
-    if (threadIdx.x == 0) out[i] = sh[0];
+    if (threadIdx.x == 0) {
+      out[i] = sh[0];
+      if (rsq && i == 0) rsq[0] = sh[0] > 0.0 ? 1.0 / sqrt(sh[0]) : 0.0;
+    }
     __syncthreads();
   }
 }
@@ -106,8 +111,8 @@ template <typename TV>
 void launch_multidot(const TV* const* V, int nv, const TV* w, int64_t n, double* partial, double* out, cudaStream_t st) {
   for (int c0 = 0; c0 < nv; c0 += NV) {
     int cnt = (nv - c0 < NV) ? nv - c0 : NV;
-    k_multidot<TV><<<RED_BLOCKS, 256, 0, st>>>(V + c0, cnt, w, n, partial);
-    k_final_reduce<<<1, 256, 0, st>>>(partial, RED_BLOCKS, cnt, NV + 1, out + c0);
+    (note_launch(), k_multidot<TV><<<RED_BLOCKS, 256, 0, st>>>(V + c0, cnt, w, n, partial));
+    (note_launch(), k_final_reduce<<<1, 256, 0, st>>>(partial, RED_BLOCKS, cnt, NV + 1, out + c0));
   }
 }
 
@@ -150,17 +155,17 @@ void launch_multiaxpy_dot(const TV* const* V, int nv, const double* h, TV* w, in
   // mode 1 needs every chunk's dots against the final w: apply all axpys first
   // chunk by chunk, then dot in a separate pass when more than one chunk.
   if (nv <= NV) {
-    k_multiaxpy<TV><<<RED_BLOCKS, 256, 0, st>>>(V, nv, h, w, n, mode, partial);
-    if (mode == 1) k_final_reduce<<<1, 256, 0, st>>>(partial, RED_BLOCKS, nv, NV + 1, out);
-    if (mode == 2) k_final_reduce<<<1, 256, 0, st>>>(partial, RED_BLOCKS, 1, NV + 1, out);
+    (note_launch(), k_multiaxpy<TV><<<RED_BLOCKS, 256, 0, st>>>(V, nv, h, w, n, mode, partial));
+    if (mode == 1) (note_launch(), k_final_reduce<<<1, 256, 0, st>>>(partial, RED_BLOCKS, nv, NV + 1, out));
+    if (mode == 2) (note_launch(), k_final_reduce<<<1, 256, 0, st>>>(partial, RED_BLOCKS, 1, NV + 1, out, out + 1));
     return;
   }
   for (int c0 = 0; c0 < nv; c0 += NV) {
     int cnt = (nv - c0 < NV) ? nv - c0 : NV;
     bool last = c0 + NV >= nv;
     int m = (last && mode == 2) ? 2 : 0;
-    k_multiaxpy<TV><<<RED_BLOCKS, 256, 0, st>>>(V + c0, cnt, h + c0, w, n, m, partial);
-    if (m == 2) k_final_reduce<<<1, 256, 0, st>>>(partial, RED_BLOCKS, 1, NV + 1, out);
+    (note_launch(), k_multiaxpy<TV><<<RED_BLOCKS, 256, 0, st>>>(V + c0, cnt, h + c0, w, n, m, partial));
+    if (m == 2) (note_launch(), k_final_reduce<<<1, 256, 0, st>>>(partial, RED_BLOCKS, 1, NV + 1, out, out + 1));
   }
   if (mode == 1) launch_multidot<TV>(V, nv, w, n, partial, out, st);
 }
@@ -171,7 +176,7 @@ __global__ void k_convert(const TA* __restrict__ a, TB* __restrict__ b, int64_t 
 }
 template <typename TA, typename TB>
 void launch_convert(const TA* a, TB* b, int64_t n, cudaStream_t st) {
-  k_convert<TA, TB><<<RED_BLOCKS * 2, 256, 0, st>>>(a, b, n);
+  (note_launch(), k_convert<TA, TB><<<RED_BLOCKS * 2, 256, 0, st>>>(a, b, n));
 }
 
 template <typename T>
@@ -181,63 +186,65 @@ __global__ void k_axpby(T* __restrict__ y, const T* __restrict__ x, T a, T b, in
 }
 template <typename T>
 void launch_axpby(T* y, const T* x, double a, double b, int64_t n, cudaStream_t st) {
-  k_axpby<T><<<RED_BLOCKS * 2, 256, 0, st>>>(y, x, (T)a, (T)b, n);
+  (note_launch(), k_axpby<T><<<RED_BLOCKS * 2, 256, 0, st>>>(y, x, (T)a, (T)b, n));
 }
 
 template <typename T>
 __global__ void k_scale_into(T* __restrict__ y, const T* __restrict__ x, const double* __restrict__ s, int inv, int64_t n) {
-  double sv = *s;
-  T f = (T)(inv ? 1.0 / sqrt(sv) : sv);
+  T f = (T)(*s);
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) y[e] = x[e] * f;
 }
-// inv = 1: y = x / sqrt(*s) (normalisation by a squared norm); inv = 0: y = x * (*s)
+// y = x * (*s) (s in device memory; `inv` is kept for the signature and ignored)
 template <typename T>
 void launch_scale_into(T* y, const T* x, const double* s, int inv, int64_t n, cudaStream_t st) {
-  k_scale_into<T><<<RED_BLOCKS * 2, 256, 0, st>>>(y, x, s, inv, n);
+  (note_launch(), k_scale_into<T><<<RED_BLOCKS * 2, 256, 0, st>>>(y, x, s, inv, n));
 }
 
 template <typename TY, typename TZ>
 __global__ void k_lincomb_add(TY* __restrict__ y, const TZ* const* __restrict__ Z, int nz, const double* __restrict__ c,
                               int64_t n) {
+  // arithmetic in the precision of y (the FP32 inner solver never touches the FP64 pipe per element)
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-    double s = (double)y[e];
-    for (int i = 0; i < nz; ++i) s += c[i] * (double)Z[i][e];
-    y[e] = (TY)s;
+    TY s = y[e];
+    for (int i = 0; i < nz; ++i) s += TY(c[i]) * TY(Z[i][e]);
+    y[e] = s;
   }
 }
 template <typename TY, typename TZ>
 void launch_lincomb_add(TY* y, const TZ* const* Z, int nz, const double* c, int64_t n, cudaStream_t st) {
-  k_lincomb_add<TY, TZ><<<RED_BLOCKS * 2, 256, 0, st>>>(y, Z, nz, c, n);
+  (note_launch(), k_lincomb_add<TY, TZ><<<RED_BLOCKS * 2, 256, 0, st>>>(y, Z, nz, c, n));
 }
 
 __global__ void k_residual(const double* __restrict__ b, const double* __restrict__ Ax, double* __restrict__ r, int64_t n) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) r[e] = b[e] - Ax[e];
 }
 void launch_residual(const double* b, const double* Ax, double* r, int64_t n, cudaStream_t st) {
-  k_residual<<<RED_BLOCKS * 2, 256, 0, st>>>(b, Ax, r, n);
+  (note_launch(), k_residual<<<RED_BLOCKS * 2, 256, 0, st>>>(b, Ax, r, n));
 }
 
+template <typename T>
 struct Mix {
-  double c[MAXR][MAXR];
+  T c[MAXR][MAXR];
 };
+// arithmetic in the output precision
 template <typename TI, typename TO>
-__global__ void k_time_mix(const TI* __restrict__ in, int64_t sin, TO* __restrict__ out, int64_t sout, int nt, Mix m, int64_t n) {
+__global__ void k_time_mix(const TI* __restrict__ in, int64_t sin, TO* __restrict__ out, int64_t sout, int nt, Mix<TO> m, int64_t n) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-    double v[MAXR];
-    for (int l = 0; l < nt; ++l) v[l] = (double)in[l * sin + e];
+    TO v[MAXR];
+    for (int l = 0; l < nt; ++l) v[l] = (TO)in[l * sin + e];
     for (int k = 0; k < nt; ++k) {
-      double s = 0;
+      TO s = 0;
       for (int l = 0; l < nt; ++l) s += m.c[k][l] * v[l];
-      out[k * sout + e] = (TO)s;
+      out[k * sout + e] = s;
     }
   }
 }
 template <typename TI, typename TO>
 void launch_time_mix(const TI* in, int64_t sin, TO* out, int64_t sout, int nt, const double* C, int64_t n, cudaStream_t st) {
-  Mix m;
+  Mix<TO> m;
   for (int k = 0; k < MAXR; ++k)
-    for (int l = 0; l < MAXR; ++l) m.c[k][l] = (k < nt && l < nt) ? C[k * nt + l] : 0.0;
-  k_time_mix<TI, TO><<<RED_BLOCKS * 2, 256, 0, st>>>(in, sin, out, sout, nt, m, n);
+    for (int l = 0; l < MAXR; ++l) m.c[k][l] = (TO)((k < nt && l < nt) ? C[k * nt + l] : 0.0);
+  (note_launch(), k_time_mix<TI, TO><<<RED_BLOCKS * 2, 256, 0, st>>>(in, sin, out, sout, nt, m, n));
 }
 
 template void launch_multidot<double>(const double* const*, int, const double*, int64_t, double*, double*, cudaStream_t);

@@ -7,6 +7,17 @@
 
 namespace biot {
 
+// ---- tracing (prof.cu) ------------------------------------------------------
+constexpr int PROF_KINDS = 4;  // 0 displacement-row operator, 1 flux rows, 2 pressure rows, 3 Krylov vector kernels
+void note_launch();
+void note_launches(long long k);  // graph replays: add the kernels of the graph
+long long launch_count();
+void prof_enable(bool on);
+bool prof_enabled();
+void prof_begin(cudaStream_t st, int kind);
+void prof_end(cudaStream_t st, int kind);
+void prof_collect(int kind, long long* n, double* ms);
+
 // ---- slab operator pieces (apply.cu) --------------------------------------
 template <typename T>
 void launch_apply_u(const Grid& g, const TabT<T>& tb, const SlabCoef& sc, const T* u, int64_t su, const T* p, int64_t sp, T* y,
@@ -17,6 +28,7 @@ void launch_apply_q(const Grid& g, const TabT<T>& tb, const SlabCoef& sc, const 
 template <typename T>
 void launch_apply_p(const Grid& g, const TabT<T>& tb, const SlabCoef& sc, const T* x, int64_t sx, T* y, int64_t sy,
                     cudaStream_t st);
+void apply_init_attributes();
 template <typename T>
 void launch_diag_A(const Grid& g, const TabT<T>& tb, double lam, double mu, T* d, cudaStream_t st);
 
@@ -110,5 +122,19 @@ void launch_cheb_update_r(const T* b, const T* Ax, const T* dinv, T* d, const T*
                           int64_t n, int nrhs, cudaStream_t st);
 template <typename TX, typename TD>
 void launch_add_scaled(TX* x, const TD* d, double s, int64_t n, cudaStream_t st);
+template <typename T>
+void launch_dinv_mul(const T* dinv, int64_t dstride, const T* r, T* z, int64_t n, int64_t stride, int nrhs, cudaStream_t st);
+// exact (s Mq)^{-1} by line solves (flux-block arrays); constrained entries untouched
+template <typename T>
+void launch_mq_line_solve(const Grid& g, const TabT<T>& tb, const T* kscale, const T* in, int64_t sin, T* out, int64_t sout,
+                          double s_scale, int nrhs, cudaStream_t st);
+template <typename T>
+void launch_BTp(const Grid& g, const TabT<T>& tb, const T* p, int64_t spp, const T* base, int64_t sb, T* tq, int64_t sq,
+                double coef, int nrhs, cudaStream_t st);
+template <typename T>
+void launch_q_fix_constrained(const Grid& g, const T* in, int64_t sin, T* out, int64_t sout, int nrhs, cudaStream_t st);
+template <typename T>
+void launch_schur_out(const Grid& g, const TabT<T>& tb, const T* p, int64_t spp, const T* tq, int64_t sq, double tau,
+                      const double* cm, T* out, int64_t so, int nrhs, cudaStream_t st);
 
 }  // namespace biot

@@ -17,26 +17,28 @@ namespace biot {
 // Q2 -> Q2 embedding prolongation (coarse cell 2h -> two fine cells h):
 // fine node 2c = coarse node c; fine nodes at 1/4 and 3/4 of a coarse cell take
 // the coarse Q2 interpolant there: (3/8, 3/4, -1/8) and (-1/8, 3/4, 3/8).
-__device__ inline int prolong_taps(int f, int* ci, double* w) {
-  if ((f & 1) == 0) { ci[0] = f >> 1; w[0] = 1.0; return 1; }
+template <typename T>
+__device__ inline int prolong_taps(int f, int* ci, T* w) {
+  if ((f & 1) == 0) { ci[0] = f >> 1; w[0] = T(1); return 1; }
   int m = f >> 2;
-  if ((f & 3) == 1) { ci[0] = 2 * m; ci[1] = 2 * m + 1; ci[2] = 2 * m + 2; w[0] = 0.375; w[1] = 0.75; w[2] = -0.125; }
-  else { ci[0] = 2 * m; ci[1] = 2 * m + 1; ci[2] = 2 * m + 2; w[0] = -0.125; w[1] = 0.75; w[2] = 0.375; }
+  if ((f & 3) == 1) { ci[0] = 2 * m; ci[1] = 2 * m + 1; ci[2] = 2 * m + 2; w[0] = T(0.375); w[1] = T(0.75); w[2] = T(-0.125); }
+  else { ci[0] = 2 * m; ci[1] = 2 * m + 1; ci[2] = 2 * m + 2; w[0] = T(-0.125); w[1] = T(0.75); w[2] = T(0.375); }
   return 3;
 }
 
 // restriction = transpose of prolongation
-__device__ inline int restrict_taps(int c, int nf, int* fi, double* w) {
+template <typename T>
+__device__ inline int restrict_taps(int c, int nf, int* fi, T* w) {
   int k = 0;
   if (c & 1) {
     int m = c >> 1;
-    fi[k] = 4 * m + 1; w[k++] = 0.75;
-    fi[k] = 4 * m + 2; w[k++] = 1.0;
-    fi[k] = 4 * m + 3; w[k++] = 0.75;
+    fi[k] = 4 * m + 1; w[k++] = T(0.75);
+    fi[k] = 4 * m + 2; w[k++] = T(1);
+    fi[k] = 4 * m + 3; w[k++] = T(0.75);
   } else {
     int m = c >> 1;
     const int off[5] = {-3, -1, 0, 1, 3};
-    const double ww[5] = {-0.125, 0.375, 1.0, 0.375, -0.125};
+    const T ww[5] = {T(-0.125), T(0.375), T(1), T(0.375), T(-0.125)};
     for (int t = 0; t < 5; ++t) {
       int f = 4 * m + off[t];
       if (f >= 0 && f < nf) { fi[k] = f; w[k++] = ww[t]; }
@@ -54,26 +56,28 @@ __global__ void k_prolong_add(Grid gf, Grid gc, const T* __restrict__ xc, int64_
   int64_t rr = t / gf.nu[0];
   f[1] = (int)(rr % gf.nu[1]);
   f[2] = (int)(rr / gf.nu[1]);
+  // the coarse correction is zero on constrained coarse nodes (identity rows with zero data)
   int ci[3][3], cnt[3];
-  double w[3][3];
+  T w[3][3];
   for (int d = 0; d < 3; ++d) {
-    if (d < gf.dim) cnt[d] = prolong_taps(f[d], ci[d], w[d]);
-    else { cnt[d] = 1; ci[d][0] = 0; w[d][0] = 1.0; }
+    if (d < gf.dim) cnt[d] = prolong_taps<T>(f[d], ci[d], w[d]);
+    else { cnt[d] = 1; ci[d][0] = 0; w[d][0] = T(1); }
   }
-  for (int r = 0; r < nrhs; ++r)
-    for (int c = 0; c < gf.dim; ++c) {
-      if (!u_free(gf, c, f[0], f[1], f[2])) continue;
+  for (int c = 0; c < gf.dim; ++c) {
+    if (!u_free(gf, c, f[0], f[1], f[2])) continue;
+    for (int r = 0; r < nrhs; ++r) {
       const T* src = xc + r * sc + c * gc.nnode;
-      double acc = 0;
+      T acc = 0;
       for (int a = 0; a < cnt[2]; ++a)
-        for (int b = 0; b < cnt[1]; ++b)
-          for (int e = 0; e < cnt[0]; ++e) {
-            if (!u_free(gc, c, ci[0][e], ci[1][b], ci[2][a])) continue;
-            acc += w[2][a] * w[1][b] * w[0][e] * (double)src[((int64_t)ci[2][a] * gc.nu[1] + ci[1][b]) * gc.nu[0] + ci[0][e]];
-          }
-      T* dst = xf + r * sf + c * gf.nnode + t;
-      *dst = (T)((double)*dst + acc);
+        for (int b = 0; b < cnt[1]; ++b) {
+          const T* row = src + ((int64_t)ci[2][a] * gc.nu[1] + ci[1][b]) * gc.nu[0];
+          T s = 0;
+          for (int e = 0; e < cnt[0]; ++e) s += w[0][e] * row[ci[0][e]];
+          acc += w[2][a] * w[1][b] * s;
+        }
+      xf[r * sf + c * gf.nnode + t] += acc;
     }
+  }
 }
 
 template <typename T>
@@ -85,37 +89,41 @@ __global__ void k_restrict(Grid gf, Grid gc, const T* __restrict__ rf, int64_t s
   int64_t rr = t / gc.nu[0];
   cidx[1] = (int)(rr % gc.nu[1]);
   cidx[2] = (int)(rr / gc.nu[1]);
+  // the fine residual is zero on constrained fine nodes (identity rows, x = b there)
   int fi[3][5], cnt[3];
-  double w[3][5];
+  T w[3][5];
   for (int d = 0; d < 3; ++d) {
-    if (d < gf.dim) cnt[d] = restrict_taps(cidx[d], gf.nu[d], fi[d], w[d]);
-    else { cnt[d] = 1; fi[d][0] = 0; w[d][0] = 1.0; }
+    if (d < gf.dim) cnt[d] = restrict_taps<T>(cidx[d], gf.nu[d], fi[d], w[d]);
+    else { cnt[d] = 1; fi[d][0] = 0; w[d][0] = T(1); }
   }
-  for (int r = 0; r < nrhs; ++r)
-    for (int c = 0; c < gf.dim; ++c) {
-      double acc = 0;
-      if (u_free(gc, c, cidx[0], cidx[1], cidx[2])) {
+  for (int c = 0; c < gf.dim; ++c) {
+    const bool fr = u_free(gc, c, cidx[0], cidx[1], cidx[2]);
+    for (int r = 0; r < nrhs; ++r) {
+      T acc = 0;
+      if (fr) {
         const T* src = rf + r * sf + c * gf.nnode;
         for (int a = 0; a < cnt[2]; ++a)
-          for (int b = 0; b < cnt[1]; ++b)
-            for (int e = 0; e < cnt[0]; ++e) {
-              if (!u_free(gf, c, fi[0][e], fi[1][b], fi[2][a])) continue;
-              acc += w[2][a] * w[1][b] * w[0][e] * (double)src[((int64_t)fi[2][a] * gf.nu[1] + fi[1][b]) * gf.nu[0] + fi[0][e]];
-            }
+          for (int b = 0; b < cnt[1]; ++b) {
+            const T* row = src + ((int64_t)fi[2][a] * gf.nu[1] + fi[1][b]) * gf.nu[0];
+            T s = 0;
+            for (int e = 0; e < cnt[0]; ++e) s += w[0][e] * row[fi[0][e]];
+            acc += w[2][a] * w[1][b] * s;
+          }
       }
-      rc[r * sc + c * gc.nnode + t] = (T)acc;
+      rc[r * sc + c * gc.nnode + t] = acc;
     }
+  }
 }
 
 template <typename T>
 void launch_prolong_add(const Grid& fine, const Grid& coarse, const T* xc, int64_t sc, T* xf, int64_t sf, int nrhs,
                         cudaStream_t st) {
-  k_prolong_add<T><<<(int)((fine.nnode + 255) / 256), 256, 0, st>>>(fine, coarse, xc, sc, xf, sf, nrhs);
+  (note_launch(), k_prolong_add<T><<<(int)((fine.nnode + 255) / 256), 256, 0, st>>>(fine, coarse, xc, sc, xf, sf, nrhs));
 }
 template <typename T>
 void launch_restrict(const Grid& fine, const Grid& coarse, const T* rf, int64_t sf, T* rc, int64_t sc, int nrhs,
                      cudaStream_t st) {
-  k_restrict<T><<<(int)((coarse.nnode + 255) / 256), 256, 0, st>>>(fine, coarse, rf, sf, rc, sc, nrhs);
+  (note_launch(), k_restrict<T><<<(int)((coarse.nnode + 255) / 256), 256, 0, st>>>(fine, coarse, rf, sf, rc, sc, nrhs));
 }
 
 // ---------------------------------------------------------------------------
@@ -149,7 +157,7 @@ void launch_cheb_update(const T* b, const T* Ax, const T* dinv, T* d, const T* x
                         int64_t n, int nrhs, int64_t stride, cudaStream_t st) {
   int blocks = (int)((n + 255) / 256);
   if (blocks > 4096) blocks = 4096;
-  k_cheb_update<T><<<blocks, 256, 0, st>>>(b, Ax, dinv, d, x, xo, (T)c1, (T)c2, first, n, nrhs, stride);
+  (note_launch(), k_cheb_update<T><<<blocks, 256, 0, st>>>(b, Ax, dinv, d, x, xo, (T)c1, (T)c2, first, n, nrhs, stride));
 }
 
 // x[:, r] = s * Ainv b[:, r]; one warp per row
@@ -171,21 +179,22 @@ template <typename T>
 void launch_dense_gemv(const double* Ainv, int n, const T* b, int64_t sb, T* x, int64_t sx, int nrhs, double s,
                        cudaStream_t st) {
   dim3 grid((n + 7) / 8, nrhs);
-  k_dense_gemv<T><<<grid, 256, 0, st>>>(Ainv, n, b, sb, x, sx, s);
+  (note_launch(), k_dense_gemv<T><<<grid, 256, 0, st>>>(Ainv, n, b, sb, x, sx, s));
 }
 
 // ---------------------------------------------------------------------------
 // flux / pressure gathers
+template <typename T>
 struct QIdx {  // decoded flux DoF
   int c, ia;
   int co[3];
   int64_t r, stride_c, pbase;
-  double wt;
+  T wt;
   int ncell, ce[2], la[2];
 };
 
-template <int DIM>
-__device__ inline bool decode_q(const Grid& g, const double* wg, int64_t t, QIdx& q) {
+template <int DIM, typename T>
+__device__ inline bool decode_q(const Grid& g, const T* wg, int64_t t, QIdx<T>& q) {
   int64_t nqt = g.nq[0] + g.nq[1] + g.nq[2];
   if (t >= nqt) return false;
   int c = 0;
@@ -202,7 +211,7 @@ __device__ inline bool decode_q(const Grid& g, const double* wg, int64_t t, QIdx
   q.ia = q.co[c];
   q.stride_c = 1;
   for (int d = 0; d < c; ++d) q.stride_c *= sh[d];
-  q.wt = 1.0;
+  q.wt = T(1);
   int64_t pst[3] = {1, g.ng[0], (int64_t)g.ng[0] * g.ng[1]};
   q.pbase = 0;
   for (int d = 0; d < DIM; ++d)
@@ -219,43 +228,43 @@ __device__ inline bool decode_q(const Grid& g, const double* wg, int64_t t, QIdx
 
 // (B^T p) at a flux DoF (without sign)
 template <typename T>
-__device__ inline double gather_BTp(const Grid& g, const TabT<T>& tb, const QIdx& q, const T* p) {
+__device__ inline T gather_BTp(const Grid& g, const TabT<T>& tb, const QIdx<T>& q, const T* p) {
   int64_t pst[3] = {1, g.ng[0], (int64_t)g.ng[0] * g.ng[1]};
-  double bp = 0;
+  T bp = 0;
   for (int e = 0; e < q.ncell; ++e)
-    for (int k = 0; k < 2; ++k) bp += (double)tb.bd[q.c][q.la[e]][k] * (double)p[q.pbase + (int64_t)(2 * q.ce[e] + k) * pst[q.c]];
+    for (int k = 0; k < 2; ++k) bp += tb.bd[q.c][q.la[e]][k] * p[q.pbase + (int64_t)(2 * q.ce[e] + k) * pst[q.c]];
   return q.wt * bp;
 }
 
 // (B q) at a pressure DoF t, flux input masked
 template <typename T, int DIM>
-__device__ inline double gather_Bq(const Grid& g, const TabT<T>& tb, int64_t t, const T* q, const T* dscale) {
+__device__ inline T gather_Bq(const Grid& g, const TabT<T>& tb, int64_t t, const T* q, const T* dscale) {
   int co[3];
   co[0] = (int)(t % g.ng[0]);
   int64_t rr = t / g.ng[0];
   co[1] = (int)(rr % g.ng[1]);
   co[2] = (int)(rr / g.ng[1]);
-  double acc = 0;
+  T acc = 0;
   for (int c = 0; c < DIM; ++c) {
     int sh[3];
     for (int d = 0; d < 3; ++d) sh[d] = (d < DIM) ? ((d == c) ? g.nu[d] : g.ng[d]) : 1;
-    double wt = 1.0;
+    T wt = 1;
     int64_t base = 0, mul = 1, stride_c = 1;
     for (int d = 0; d < 3; ++d) {
       if (d == c) stride_c = mul;
-      else { base += co[d] * mul; if (d < DIM) wt *= (double)tb.wg[d]; }
+      else { base += co[d] * mul; if (d < DIM) wt *= tb.wg[d]; }
       mul *= sh[d];
     }
     const int64_t off = g.offq[c] - g.Nu + base;  // q arrays here are indexed from the start of the flux block
     int cell = co[c] >> 1, gq = co[c] & 1;
-    double s = 0;
+    T s = 0;
     for (int a = 0; a < 3; ++a) {
       int ia = 2 * cell + a;
       if (!q_free(g, c, ia)) continue;
       int64_t i = off + (int64_t)ia * stride_c;
-      double v = (double)q[i];
-      if (dscale) v *= (double)dscale[i];
-      s += (double)tb.bd[c][a][gq] * v;
+      T v = q[i];
+      if (dscale) v *= dscale[i];
+      s += tb.bd[c][a][gq] * v;
     }
     acc += wt * s;
   }
@@ -266,7 +275,7 @@ __device__ inline double gather_Bq(const Grid& g, const TabT<T>& tb, int64_t t, 
 template <typename T, int DIM>
 __global__ void k_diag_Mq(Grid g, TabT<T> tb, const T* __restrict__ kscale, T* __restrict__ dmq) {
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  QIdx q;
+  QIdx<double> q;
   double wg[3] = {(double)tb.wg[0], (double)tb.wg[1], (double)tb.wg[2]};
   if (!decode_q<DIM>(g, wg, t, q)) return;
   if (!q_free(g, q.c, q.ia)) { dmq[t] = T(1); return; }
@@ -321,13 +330,12 @@ template <typename T, int DIM>
 __global__ void k_q_jacobi(Grid g, const T* __restrict__ rq, int64_t srq, const T* __restrict__ dmq, double tau,
                            T* __restrict__ q0, int64_t sq, int nrhs, TabT<T> tb) {
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  QIdx q;
-  double wg[3] = {(double)tb.wg[0], (double)tb.wg[1], (double)tb.wg[2]};
-  if (!decode_q<DIM>(g, wg, t, q)) return;
+  QIdx<T> q;
+  if (!decode_q<DIM>(g, tb.wg, t, q)) return;
   bool fr = q_free(g, q.c, q.ia);
   for (int r = 0; r < nrhs; ++r) {
     T v = rq[r * srq + t];
-    q0[r * sq + t] = fr ? (T)((double)v / (tau * (double)dmq[t])) : v;
+    q0[r * sq + t] = fr ? v / (T(tau) * dmq[t]) : v;
   }
 }
 
@@ -338,7 +346,7 @@ __global__ void k_p_minus_Bq(Grid g, TabT<T> tb, const T* __restrict__ rp, int64
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= g.Np) return;
   for (int r = 0; r < nrhs; ++r)
-    out[r * so + t] = (T)((double)rp[r * srp + t] - tau * gather_Bq<T, DIM>(g, tb, t, q + r * sq, nullptr));
+    out[r * so + t] = rp[r * srp + t] - T(tau) * gather_Bq<T, DIM>(g, tb, t, q + r * sq, nullptr);
 }
 
 // tq = (B^T p) / dmq on free flux DoFs, 0 on constrained
@@ -346,11 +354,11 @@ template <typename T, int DIM>
 __global__ void k_BTp_scaled(Grid g, TabT<T> tb, const T* __restrict__ p, int64_t spp, const T* __restrict__ dmq, T* __restrict__ tq,
                              int64_t sq, int nrhs) {
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  QIdx q;
-  double wg[3] = {(double)tb.wg[0], (double)tb.wg[1], (double)tb.wg[2]};
-  if (!decode_q<DIM>(g, wg, t, q)) return;
+  QIdx<T> q;
+  if (!decode_q<DIM>(g, tb.wg, t, q)) return;
   bool fr = q_free(g, q.c, q.ia);
-  for (int r = 0; r < nrhs; ++r) tq[r * sq + t] = fr ? (T)(gather_BTp<T>(g, tb, q, p + r * spp) / (double)dmq[t]) : T(0);
+  const T dinv = T(1) / dmq[t];
+  for (int r = 0; r < nrhs; ++r) tq[r * sq + t] = fr ? gather_BTp<T>(g, tb, q, p + r * spp) * dinv : T(0);
 }
 
 // out_p = cm[r] * mp * p + tau * B tq
@@ -362,10 +370,10 @@ __global__ void k_schur_out(Grid g, TabT<T> tb, const T* __restrict__ p, int64_t
                             double tau, RhsCoef cm, T* __restrict__ out, int64_t so, int nrhs) {
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= g.Np) return;
-  double mp = 1.0;
-  for (int d = 0; d < DIM; ++d) mp *= (double)tb.wg[d];
+  T mp = 1;
+  for (int d = 0; d < DIM; ++d) mp *= tb.wg[d];
   for (int r = 0; r < nrhs; ++r)
-    out[r * so + t] = (T)(cm.c[r] * mp * (double)p[r * spp + t] + tau * gather_Bq<T, DIM>(g, tb, t, tq + r * sq, nullptr));
+    out[r * so + t] = T(cm.c[r]) * mp * p[r * spp + t] + T(tau) * gather_Bq<T, DIM>(g, tb, t, tq + r * sq, nullptr);
 }
 
 // q = (Rq + bt B^T p) / (tau dmq) on free flux DoFs, Rq on constrained
@@ -373,14 +381,14 @@ template <typename T, int DIM>
 __global__ void k_q_final(Grid g, TabT<T> tb, const T* __restrict__ rq, int64_t srq, const T* __restrict__ p, int64_t spp,
                           const T* __restrict__ dmq, double tau, double bt, T* __restrict__ qo, int64_t sq, int nrhs) {
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  QIdx q;
-  double wg[3] = {(double)tb.wg[0], (double)tb.wg[1], (double)tb.wg[2]};
-  if (!decode_q<DIM>(g, wg, t, q)) return;
+  QIdx<T> q;
+  if (!decode_q<DIM>(g, tb.wg, t, q)) return;
   bool fr = q_free(g, q.c, q.ia);
+  const T den = T(1) / (T(tau) * dmq[t]);
   for (int r = 0; r < nrhs; ++r) {
-    double v = (double)rq[r * srq + t];
-    if (fr) v = (v + bt * gather_BTp<T>(g, tb, q, p + r * spp)) / (tau * (double)dmq[t]);
-    qo[r * sq + t] = (T)v;
+    T v = rq[r * srq + t];
+    if (fr) v = (v + T(bt) * gather_BTp<T>(g, tb, q, p + r * spp)) * den;
+    qo[r * sq + t] = v;
   }
 }
 
@@ -399,33 +407,36 @@ __global__ void k_u_rhs(Grid g, TabT<T> tb, const T* __restrict__ ru, int64_t sr
     bool fr = u_free(g, c, ix, iy, iz);
     // taps of E along each direction
     int pi[3][4], cnt[3];
-    double pc[3][4];
+    T pc[3][4];
     for (int d = 0; d < 3; ++d) {
       int k = 0;
       if (d < DIM) {
         int m = idx[d];
         const T(*tab)[2] = (d == c) ? tb.bd[d] : tb.bv[d];
-        if (m & 1) { for (int q = 0; q < 2; ++q) { pi[d][k] = m - 1 + q; pc[d][k] = (double)tab[1][q]; ++k; } }
+        if (m & 1) { for (int q = 0; q < 2; ++q) { pi[d][k] = m - 1 + q; pc[d][k] = tab[1][q]; ++k; } }
         else {
           int j = m >> 1;
-          if (j >= 1) for (int q = 0; q < 2; ++q) { pi[d][k] = 2 * (j - 1) + q; pc[d][k] = (double)tab[2][q]; ++k; }
-          if (j < g.n[d]) for (int q = 0; q < 2; ++q) { pi[d][k] = 2 * j + q; pc[d][k] = (double)tab[0][q]; ++k; }
+          if (j >= 1) for (int q = 0; q < 2; ++q) { pi[d][k] = 2 * (j - 1) + q; pc[d][k] = tab[2][q]; ++k; }
+          if (j < g.n[d]) for (int q = 0; q < 2; ++q) { pi[d][k] = 2 * j + q; pc[d][k] = tab[0][q]; ++k; }
         }
-      } else { pi[d][0] = 0; pc[d][0] = 1.0; k = 1; }
+      } else { pi[d][0] = 0; pc[d][0] = T(1); k = 1; }
       cnt[d] = k;
     }
     for (int r = 0; r < nrhs; ++r) {
-      double v = (double)ru[r * sru + c * g.nnode + t];
+      T v = ru[r * sru + c * g.nnode + t];
       if (fr) {
         const T* pr = p + r * spp;
-        double acc = 0;
+        T acc = 0;
         for (int a = 0; a < cnt[2]; ++a)
-          for (int b = 0; b < cnt[1]; ++b)
-            for (int e = 0; e < cnt[0]; ++e)
-              acc += pc[2][a] * pc[1][b] * pc[0][e] * (double)pr[((int64_t)pi[2][a] * g.ng[1] + pi[1][b]) * g.ng[0] + pi[0][e]];
-        v += alpha * acc;
+          for (int b = 0; b < cnt[1]; ++b) {
+            const T* row = pr + ((int64_t)pi[2][a] * g.ng[1] + pi[1][b]) * g.ng[0];
+            T s = 0;
+            for (int e = 0; e < cnt[0]; ++e) s += pc[0][e] * row[pi[0][e]];
+            acc += pc[2][a] * pc[1][b] * s;
+          }
+        v += T(alpha) * acc;
       }
-      bu[r * sbu + c * g.nnode + t] = (T)v;
+      bu[r * sbu + c * g.nnode + t] = v;
     }
   }
 }
@@ -435,29 +446,29 @@ template <typename T>
 void launch_diag_Mq(const Grid& g, const TabT<T>& tb, const T* kscale, T* dmq, cudaStream_t st) {
   int64_t n = g.nq[0] + g.nq[1] + g.nq[2];
   int blocks = (int)((n + 255) / 256);
-  if (g.dim == 3) k_diag_Mq<T, 3><<<blocks, 256, 0, st>>>(g, tb, kscale, dmq);
-  else k_diag_Mq<T, 2><<<blocks, 256, 0, st>>>(g, tb, kscale, dmq);
+  if (g.dim == 3) (note_launch(), k_diag_Mq<T, 3><<<blocks, 256, 0, st>>>(g, tb, kscale, dmq));
+  else (note_launch(), k_diag_Mq<T, 2><<<blocks, 256, 0, st>>>(g, tb, kscale, dmq));
 }
 template <typename T>
 void launch_diag_BDBt(const Grid& g, const TabT<T>& tb, const T* dmq, T* out, cudaStream_t st) {
   int blocks = (int)((g.Np + 255) / 256);
-  if (g.dim == 3) k_diag_BDBt<T, 3><<<blocks, 256, 0, st>>>(g, tb, dmq, out);
-  else k_diag_BDBt<T, 2><<<blocks, 256, 0, st>>>(g, tb, dmq, out);
+  if (g.dim == 3) (note_launch(), k_diag_BDBt<T, 3><<<blocks, 256, 0, st>>>(g, tb, dmq, out));
+  else (note_launch(), k_diag_BDBt<T, 2><<<blocks, 256, 0, st>>>(g, tb, dmq, out));
 }
 template <typename T>
 void launch_q_jacobi(const Grid& g, const TabT<T>& tb, const T* rq, int64_t srq, const T* dmq, double tau, T* q0, int64_t sq,
                      int nrhs, cudaStream_t st) {
   int64_t n = g.nq[0] + g.nq[1] + g.nq[2];
   int blocks = (int)((n + 255) / 256);
-  if (g.dim == 3) k_q_jacobi<T, 3><<<blocks, 256, 0, st>>>(g, rq, srq, dmq, tau, q0, sq, nrhs, tb);
-  else k_q_jacobi<T, 2><<<blocks, 256, 0, st>>>(g, rq, srq, dmq, tau, q0, sq, nrhs, tb);
+  if (g.dim == 3) (note_launch(), k_q_jacobi<T, 3><<<blocks, 256, 0, st>>>(g, rq, srq, dmq, tau, q0, sq, nrhs, tb));
+  else (note_launch(), k_q_jacobi<T, 2><<<blocks, 256, 0, st>>>(g, rq, srq, dmq, tau, q0, sq, nrhs, tb));
 }
 template <typename T>
 void launch_p_minus_Bq(const Grid& g, const TabT<T>& tb, const T* rp, int64_t srp, const T* q, int64_t sq, double tau, T* out,
                        int64_t so, int nrhs, cudaStream_t st) {
   int blocks = (int)((g.Np + 255) / 256);
-  if (g.dim == 3) k_p_minus_Bq<T, 3><<<blocks, 256, 0, st>>>(g, tb, rp, srp, q, sq, tau, out, so, nrhs);
-  else k_p_minus_Bq<T, 2><<<blocks, 256, 0, st>>>(g, tb, rp, srp, q, sq, tau, out, so, nrhs);
+  if (g.dim == 3) (note_launch(), k_p_minus_Bq<T, 3><<<blocks, 256, 0, st>>>(g, tb, rp, srp, q, sq, tau, out, so, nrhs));
+  else (note_launch(), k_p_minus_Bq<T, 2><<<blocks, 256, 0, st>>>(g, tb, rp, srp, q, sq, tau, out, so, nrhs));
 }
 template <typename T>
 void launch_schur_apply(const Grid& g, const TabT<T>& tb, const T* p, int64_t spp, const T* dmq, T* tq, int64_t sq, double tau,
@@ -466,11 +477,11 @@ void launch_schur_apply(const Grid& g, const TabT<T>& tb, const T* p, int64_t sp
   RhsCoef rc;
   for (int r = 0; r < MAXR; ++r) rc.c[r] = (r < nrhs) ? cm[r] : 0.0;
   if (g.dim == 3) {
-    k_BTp_scaled<T, 3><<<(int)((nqt + 255) / 256), 256, 0, st>>>(g, tb, p, spp, dmq, tq, sq, nrhs);
-    k_schur_out<T, 3><<<(int)((g.Np + 255) / 256), 256, 0, st>>>(g, tb, p, spp, tq, sq, tau, rc, out, so, nrhs);
+    (note_launch(), k_BTp_scaled<T, 3><<<(int)((nqt + 255) / 256), 256, 0, st>>>(g, tb, p, spp, dmq, tq, sq, nrhs));
+    (note_launch(), k_schur_out<T, 3><<<(int)((g.Np + 255) / 256), 256, 0, st>>>(g, tb, p, spp, tq, sq, tau, rc, out, so, nrhs));
   } else {
-    k_BTp_scaled<T, 2><<<(int)((nqt + 255) / 256), 256, 0, st>>>(g, tb, p, spp, dmq, tq, sq, nrhs);
-    k_schur_out<T, 2><<<(int)((g.Np + 255) / 256), 256, 0, st>>>(g, tb, p, spp, tq, sq, tau, rc, out, so, nrhs);
+    (note_launch(), k_BTp_scaled<T, 2><<<(int)((nqt + 255) / 256), 256, 0, st>>>(g, tb, p, spp, dmq, tq, sq, nrhs));
+    (note_launch(), k_schur_out<T, 2><<<(int)((g.Np + 255) / 256), 256, 0, st>>>(g, tb, p, spp, tq, sq, tau, rc, out, so, nrhs));
   }
 }
 template <typename T>
@@ -478,15 +489,15 @@ void launch_q_final(const Grid& g, const TabT<T>& tb, const T* rq, int64_t srq, 
                     double tau, double bt, T* qo, int64_t sq, int nrhs, cudaStream_t st) {
   int64_t n = g.nq[0] + g.nq[1] + g.nq[2];
   int blocks = (int)((n + 255) / 256);
-  if (g.dim == 3) k_q_final<T, 3><<<blocks, 256, 0, st>>>(g, tb, rq, srq, p, spp, dmq, tau, bt, qo, sq, nrhs);
-  else k_q_final<T, 2><<<blocks, 256, 0, st>>>(g, tb, rq, srq, p, spp, dmq, tau, bt, qo, sq, nrhs);
+  if (g.dim == 3) (note_launch(), k_q_final<T, 3><<<blocks, 256, 0, st>>>(g, tb, rq, srq, p, spp, dmq, tau, bt, qo, sq, nrhs));
+  else (note_launch(), k_q_final<T, 2><<<blocks, 256, 0, st>>>(g, tb, rq, srq, p, spp, dmq, tau, bt, qo, sq, nrhs));
 }
 template <typename T>
 void launch_u_rhs(const Grid& g, const TabT<T>& tb, const T* ru, int64_t sru, const T* p, int64_t spp, double alpha, T* bu,
                   int64_t sbu, int nrhs, cudaStream_t st) {
   int blocks = (int)((g.nnode + 255) / 256);
-  if (g.dim == 3) k_u_rhs<T, 3><<<blocks, 256, 0, st>>>(g, tb, ru, sru, p, spp, alpha, bu, sbu, nrhs);
-  else k_u_rhs<T, 2><<<blocks, 256, 0, st>>>(g, tb, ru, sru, p, spp, alpha, bu, sbu, nrhs);
+  if (g.dim == 3) (note_launch(), k_u_rhs<T, 3><<<blocks, 256, 0, st>>>(g, tb, ru, sru, p, spp, alpha, bu, sbu, nrhs));
+  else (note_launch(), k_u_rhs<T, 2><<<blocks, 256, 0, st>>>(g, tb, ru, sru, p, spp, alpha, bu, sbu, nrhs));
 }
 
 
@@ -505,34 +516,34 @@ __global__ void k_p_plus_ETu(Grid g, TabT<T> tb, const T* __restrict__ rp, int64
   for (int d = 0; d < 3; ++d) { cell[d] = (d < DIM) ? co[d] >> 1 : 0; gq[d] = (d < DIM) ? (co[d] & 1) : 0; }
   for (int r = 0; r < nrhs; ++r) {
     const T* ur = u + r * su;
-    double acc = 0;
+    T acc = 0;
     for (int c = 0; c < DIM; ++c) {
-      double f[3][3];
+      T f[3][3];
       for (int d = 0; d < 3; ++d)
         for (int a = 0; a < 3; ++a)
-          f[d][a] = (d < DIM) ? (double)((d == c) ? tb.bd[d][a][gq[d]] : tb.bv[d][a][gq[d]]) : (a == 0 ? 1.0 : 0.0);
+          f[d][a] = (d < DIM) ? ((d == c) ? tb.bd[d][a][gq[d]] : tb.bv[d][a][gq[d]]) : (a == 0 ? T(1) : T(0));
       const int az_n = (DIM == 3) ? 3 : 1;
       for (int az = 0; az < az_n; ++az)
         for (int ay = 0; ay < 3; ++ay) {
           int iz = 2 * cell[2] + az, iy = 2 * cell[1] + ay;
           const T* row = ur + c * g.nnode + ((int64_t)iz * g.nu[1] + iy) * g.nu[0];
-          double s = 0;
+          T s = 0;
           for (int ax = 0; ax < 3; ++ax) {
             int ix = 2 * cell[0] + ax;
-            if (u_free(g, c, ix, iy, iz)) s += f[0][ax] * (double)row[ix];
+            if (u_free(g, c, ix, iy, iz)) s += f[0][ax] * row[ix];
           }
           acc += f[2][az] * f[1][ay] * s;
         }
     }
-    out[r * so + t] = (T)((double)rp[r * srp + t] + alpha * acc);
+    out[r * so + t] = rp[r * srp + t] + T(alpha) * acc;
   }
 }
 template <typename T>
 void launch_p_plus_ETu(const Grid& g, const TabT<T>& tb, const T* rp, int64_t srp, const T* u, int64_t su, double alpha, T* out,
                        int64_t so, int nrhs, cudaStream_t st) {
   int blocks = (int)((g.Np + 255) / 256);
-  if (g.dim == 3) k_p_plus_ETu<T, 3><<<blocks, 256, 0, st>>>(g, tb, rp, srp, u, su, alpha, out, so, nrhs);
-  else k_p_plus_ETu<T, 2><<<blocks, 256, 0, st>>>(g, tb, rp, srp, u, su, alpha, out, so, nrhs);
+  if (g.dim == 3) (note_launch(), k_p_plus_ETu<T, 3><<<blocks, 256, 0, st>>>(g, tb, rp, srp, u, su, alpha, out, so, nrhs));
+  else (note_launch(), k_p_plus_ETu<T, 2><<<blocks, 256, 0, st>>>(g, tb, rp, srp, u, su, alpha, out, so, nrhs));
 }
 
 // zero constrained entries of one-level vectors
@@ -563,11 +574,11 @@ __global__ void k_mask(Grid g, T* __restrict__ x, int64_t s, int nrhs, int u_onl
 template <typename T>
 void launch_mask(const Grid& g, T* x, int64_t s, int nrhs, cudaStream_t st) {
   int64_t n = g.nnode > (g.nq[0] + g.nq[1] + g.nq[2]) ? g.nnode : (g.nq[0] + g.nq[1] + g.nq[2]);
-  k_mask<T><<<(int)((n + 255) / 256), 256, 0, st>>>(g, x, s, nrhs, 0);
+  (note_launch(), k_mask<T><<<(int)((n + 255) / 256), 256, 0, st>>>(g, x, s, nrhs, 0));
 }
 template <typename T>
 void launch_mask_u(const Grid& g, T* x, int64_t s, int nrhs, cudaStream_t st) {
-  k_mask<T><<<(int)((g.nnode + 255) / 256), 256, 0, st>>>(g, x, s, nrhs, 1);
+  (note_launch(), k_mask<T><<<(int)((g.nnode + 255) / 256), 256, 0, st>>>(g, x, s, nrhs, 1));
 }
 
 // per-cell flux mass pairing (adjoint gradient): one thread per cell
@@ -618,8 +629,8 @@ __global__ void k_grad_pair(Grid g, TabT<double> tb, const double* __restrict__ 
 void launch_grad_pair(const Grid& g, const TabT<double>& tb, const double* kscale, const double* z, const double* x, double w,
                       double* grad, cudaStream_t st) {
   int blocks = (int)((g.ncells + 255) / 256);
-  if (g.dim == 3) k_grad_pair<3><<<blocks, 256, 0, st>>>(g, tb, kscale, z, x, w, grad);
-  else k_grad_pair<2><<<blocks, 256, 0, st>>>(g, tb, kscale, z, x, w, grad);
+  if (g.dim == 3) (note_launch(), k_grad_pair<3><<<blocks, 256, 0, st>>>(g, tb, kscale, z, x, w, grad));
+  else (note_launch(), k_grad_pair<2><<<blocks, 256, 0, st>>>(g, tb, kscale, z, x, w, grad));
 }
 
 // slab right-hand side from load terms and the jump term
@@ -645,7 +656,7 @@ void launch_slab_rhs(const Grid& g, const double* const* f, int nterms, const do
     for (int m = 0; m < 8; ++m) tab.c[k][m] = (k < nt && m < nterms) ? c[k * nterms + m] : 0.0;
     tab.phi0[k] = (k < nt) ? phi0[k] : 0.0;
   }
-  k_slab_rhs<<<(int)((g.N + 255) / 256), 256, 0, st>>>(g, f, nterms, tab, nt, sp, y);
+  (note_launch(), k_slab_rhs<<<(int)((g.N + 255) / 256), 256, 0, st>>>(g, f, nterms, tab, nt, sp, y));
 }
 
 
@@ -655,7 +666,7 @@ template <typename T>
 __global__ void k_schur_dinv(const T* __restrict__ sb2, double mp, RhsCoef cm, double tau, T* __restrict__ dinv, int64_t np, int nrhs) {
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= np) return;
-  for (int r = 0; r < nrhs; ++r) dinv[r * np + t] = (T)(1.0 / (cm.c[r] * mp + tau * (double)sb2[t]));
+  for (int r = 0; r < nrhs; ++r) dinv[r * np + t] = T(1) / (T(cm.c[r] * mp) + T(tau) * sb2[t]);
 }
 template <typename T>
 void launch_schur_dinv(const Grid& g, const TabT<T>& tb, const T* sb2, const double* cm, double tau, T* dinv, int nrhs,
@@ -664,7 +675,7 @@ void launch_schur_dinv(const Grid& g, const TabT<T>& tb, const T* sb2, const dou
   for (int r = 0; r < MAXR; ++r) rc.c[r] = (r < nrhs) ? cm[r] : 0.0;
   double mp = 1.0;
   for (int d = 0; d < g.dim; ++d) mp *= (double)tb.wg[d];
-  k_schur_dinv<T><<<(int)((g.Np + 255) / 256), 256, 0, st>>>(sb2, mp, rc, tau, dinv, g.Np, nrhs);
+  (note_launch(), k_schur_dinv<T><<<(int)((g.Np + 255) / 256), 256, 0, st>>>(sb2, mp, rc, tau, dinv, g.Np, nrhs));
 }
 
 // Chebyshev step with a per-rhs diagonal (stride n between rhs for every array)
@@ -690,7 +701,7 @@ void launch_cheb_update_r(const T* b, const T* Ax, const T* dinv, T* d, const T*
                           int64_t n, int nrhs, cudaStream_t st) {
   int blocks = (int)((n + 255) / 256);
   if (blocks > 4096) blocks = 4096;
-  k_cheb_update_r<T><<<blocks, 256, 0, st>>>(b, Ax, dinv, d, x, xo, (T)c1, (T)c2, first, n, nrhs);
+  (note_launch(), k_cheb_update_r<T><<<blocks, 256, 0, st>>>(b, Ax, dinv, d, x, xo, (T)c1, (T)c2, first, n, nrhs));
 }
 
 // x += s * d (mixed precision update)
@@ -701,11 +712,184 @@ __global__ void k_add_scaled(TX* __restrict__ x, const TD* __restrict__ d, doubl
 }
 template <typename TX, typename TD>
 void launch_add_scaled(TX* x, const TD* d, double s, int64_t n, cudaStream_t st) {
-  k_add_scaled<TX, TD><<<2 * RED_BLOCKS, 256, 0, st>>>(x, d, s, n);
+  (note_launch(), k_add_scaled<TX, TD><<<2 * RED_BLOCKS, 256, 0, st>>>(x, d, s, n));
 }
 template void launch_add_scaled<double, float>(double*, const float*, double, int64_t, cudaStream_t);
 template void launch_add_scaled<double, double>(double*, const double*, double, int64_t, cudaStream_t);
 
+
+// ---------------------------------------------------------------------------
+// Exact inverse of the Darcy mass Mq by lines.  Mq is block diagonal: component
+// c couples only DoFs on one Gauss line along direction c, through the 1-D Q2
+// mass of each cell scaled by eta/K_cell and the transverse Gauss weights.  The
+// mid-cell DoF of every cell is condensed onto its two vertices, leaving a
+// strictly diagonally dominant tridiagonal system on the vertex DoFs, solved
+// by the Thomas algorithm (one thread per line).  No-flow vertices are
+// eliminated (zero); on them the output is alpha * input (identity rows).
+// out = (s * Mq)^{-1} in on free DoFs.
+template <typename T, int DIM>
+__global__ void k_mq_line_solve(Grid g, TabT<T> tb, const T* __restrict__ kscale, const T* __restrict__ in, int64_t sin,
+                                T* __restrict__ out, int64_t sout, double s_scale, int nrhs) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  // line decode: component c, transverse Gauss indices
+  int64_t nl[3] = {0, 0, 0};
+  for (int c = 0; c < DIM; ++c) nl[c] = g.nq[c] / g.nu[c];
+  int c = 0;
+  int64_t r = t;
+  while (c < DIM && r >= nl[c]) { r -= nl[c]; ++c; }
+  if (c >= DIM) return;
+  int sh[3];
+  for (int d = 0; d < 3; ++d) sh[d] = (d < DIM) ? ((d == c) ? g.nu[d] : g.ng[d]) : 1;
+  int tr[3] = {0, 0, 0};
+  int64_t rr = r;
+  T wt = T(1);
+  for (int d = 0; d < DIM; ++d) {
+    if (d == c) continue;
+    tr[d] = (int)(rr % sh[d]);
+    rr /= sh[d];
+    wt *= tb.wg[d];
+  }
+  int64_t base = 0, mul = 1, stride_c = 1;
+  for (int d = 0; d < 3; ++d) {
+    if (d == c) stride_c = mul;
+    else base += (int64_t)tr[d] * mul;
+    mul *= sh[d];
+  }
+  base += g.offq[c] - g.Nu;
+  int cell[3];
+  for (int d = 0; d < 3; ++d) cell[d] = (d < DIM && d != c) ? (tr[d] >> 1) : 0;
+  const int n = g.n[c];
+  const T hc = tb.mq[c][1][1] * T(30.0 / 16.0);  // = h_c
+  const bool lo_fixed = !q_free(g, c, 0), hi_fixed = !q_free(g, c, 2 * n);
+  for (int q = 0; q < nrhs; ++q) {
+    const T* b = in + q * sin + base;
+    T* x = out + q * sout + base;
+    // forward sweep over vertices j = 0..n; c'_j kept in x[2j+1], d'_j in x[2j]
+    T cprev = 0, dprev = 0;
+    T s_left = 0, beta_left = 0;
+    for (int j = 0; j <= n; ++j) {
+      T s_right = 0, beta_right = 0;
+      if (j < n) {
+        cell[c] = j;
+        int64_t cid = ((int64_t)cell[2] * g.n[1] + cell[1]) * g.n[0] + cell[0];
+        s_right = T(s_scale) * kscale[cid] * wt;
+        beta_right = T(30) * b[(int64_t)(2 * j + 1) * stride_c] / (hc * s_right);
+      }
+      bool fixed = (j == 0 && lo_fixed) || (j == n && hi_fixed);
+      T a = T(-1.25) * s_left, dd = T(3.75) * (s_left + s_right), cc = T(-1.25) * s_right;
+      T rhs = T(30) * b[(int64_t)(2 * j) * stride_c] / hc - (s_left * beta_left + s_right * beta_right) * T(0.125);
+      if (fixed) { a = 0; dd = 1; cc = 0; rhs = 0; }
+      // eliminate the sub-diagonal with the previous row
+      T den = dd - a * cprev;
+      T cp = cc / den;
+      T dp = (rhs - a * dprev) / den;
+      x[(int64_t)(2 * j) * stride_c] = dp;
+      if (j < n) x[(int64_t)(2 * j + 1) * stride_c] = cp;
+      cprev = cp;
+      dprev = dp;
+      s_left = s_right;
+      beta_left = beta_right;
+    }
+    // back substitution on vertices, then the condensed mid DoFs
+    T xnext = x[(int64_t)(2 * n) * stride_c];
+    for (int j = n - 1; j >= 0; --j) {
+      T cp = x[(int64_t)(2 * j + 1) * stride_c];
+      T xv = x[(int64_t)(2 * j) * stride_c] - cp * xnext;
+      x[(int64_t)(2 * j) * stride_c] = xv;
+      cell[c] = j;
+      int64_t cid = ((int64_t)cell[2] * g.n[1] + cell[1]) * g.n[0] + cell[0];
+      T sj = T(s_scale) * kscale[cid] * wt;
+      T beta = T(30) * b[(int64_t)(2 * j + 1) * stride_c] / (hc * sj);
+      x[(int64_t)(2 * j + 1) * stride_c] = (beta - T(2) * xv - T(2) * xnext) * T(0.0625);
+      xnext = xv;
+    }
+  }
+}
+
+// flux-grid gather tq = B^T p on free DoFs (0 on constrained)
+// tq = base + coef B^T p on free DoFs (base may be null), 0 on constrained
+template <typename T, int DIM>
+__global__ void k_BTp(Grid g, TabT<T> tb, const T* __restrict__ p, int64_t spp, const T* __restrict__ base, int64_t sb,
+                      T* __restrict__ tq, int64_t sq, T coef, int nrhs) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  QIdx<T> q;
+  if (!decode_q<DIM>(g, tb.wg, t, q)) return;
+  bool fr = q_free(g, q.c, q.ia);
+  for (int r = 0; r < nrhs; ++r) {
+    T v = T(0);
+    if (fr) {
+      v = coef * gather_BTp<T>(g, tb, q, p + r * spp);
+      if (base) v += base[r * sb + t];
+    }
+    tq[r * sq + t] = v;
+  }
+}
+
+// out_q = alpha * in_q on constrained flux DoFs (restores the identity rows after a line solve)
+template <typename T, int DIM>
+__global__ void k_q_fix_constrained(Grid g, const T* __restrict__ in, int64_t sin, T* __restrict__ out, int64_t sout, int nrhs) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t nqt = g.nq[0] + g.nq[1] + g.nq[2];
+  if (t >= nqt) return;
+  int c = 0;
+  int64_t rq = t;
+  while (rq >= g.nq[c]) { rq -= g.nq[c]; ++c; }
+  int64_t stride_c = 1;
+  for (int d = 0; d < c; ++d) stride_c *= (d < DIM) ? g.ng[d] : 1;
+  int ia = (int)((rq / stride_c) % g.nu[c]);
+  if (!q_free(g, c, ia))
+    for (int r = 0; r < nrhs; ++r) out[r * sout + t] = in[r * sin + t];
+}
+
+template <typename T>
+void launch_mq_line_solve(const Grid& g, const TabT<T>& tb, const T* kscale, const T* in, int64_t sin, T* out, int64_t sout,
+                          double s_scale, int nrhs, cudaStream_t st) {
+  int64_t lines = 0;
+  for (int c = 0; c < g.dim; ++c) lines += g.nq[c] / g.nu[c];
+  int blocks = (int)((lines + 127) / 128);
+  if (g.dim == 3) (note_launch(), k_mq_line_solve<T, 3><<<blocks, 128, 0, st>>>(g, tb, kscale, in, sin, out, sout, s_scale, nrhs));
+  else (note_launch(), k_mq_line_solve<T, 2><<<blocks, 128, 0, st>>>(g, tb, kscale, in, sin, out, sout, s_scale, nrhs));
+}
+template <typename T>
+void launch_BTp(const Grid& g, const TabT<T>& tb, const T* p, int64_t spp, const T* base, int64_t sb, T* tq, int64_t sq,
+                double coef, int nrhs, cudaStream_t st) {
+  int64_t n = g.nq[0] + g.nq[1] + g.nq[2];
+  int blocks = (int)((n + 255) / 256);
+  if (g.dim == 3) (note_launch(), k_BTp<T, 3><<<blocks, 256, 0, st>>>(g, tb, p, spp, base, sb, tq, sq, T(coef), nrhs));
+  else (note_launch(), k_BTp<T, 2><<<blocks, 256, 0, st>>>(g, tb, p, spp, base, sb, tq, sq, T(coef), nrhs));
+}
+template <typename T>
+void launch_q_fix_constrained(const Grid& g, const T* in, int64_t sin, T* out, int64_t sout, int nrhs, cudaStream_t st) {
+  int64_t n = g.nq[0] + g.nq[1] + g.nq[2];
+  int blocks = (int)((n + 255) / 256);
+  if (g.dim == 3) (note_launch(), k_q_fix_constrained<T, 3><<<blocks, 256, 0, st>>>(g, in, sin, out, sout, nrhs));
+  else (note_launch(), k_q_fix_constrained<T, 2><<<blocks, 256, 0, st>>>(g, in, sin, out, sout, nrhs));
+}
+// out_p = cm[r] mp p + tau B tq (tq on the flux grid, already M_q^{-1} B^T p)
+template <typename T>
+void launch_schur_out(const Grid& g, const TabT<T>& tb, const T* p, int64_t spp, const T* tq, int64_t sq, double tau,
+                      const double* cm, T* out, int64_t so, int nrhs, cudaStream_t st) {
+  RhsCoef rc;
+  for (int r = 0; r < MAXR; ++r) rc.c[r] = (r < nrhs) ? cm[r] : 0.0;
+  if (g.dim == 3) (note_launch(), k_schur_out<T, 3><<<(int)((g.Np + 255) / 256), 256, 0, st>>>(g, tb, p, spp, tq, sq, tau, rc, out, so, nrhs));
+  else (note_launch(), k_schur_out<T, 2><<<(int)((g.Np + 255) / 256), 256, 0, st>>>(g, tb, p, spp, tq, sq, tau, rc, out, so, nrhs));
+}
+
+// z = dinv * r over nrhs vectors (dinv per rhs when dstride != 0, shared otherwise)
+template <typename T>
+__global__ void k_dinv_mul(const T* __restrict__ dinv, int64_t dstride, const T* __restrict__ r, T* __restrict__ z, int64_t n,
+                           int64_t stride, int nrhs) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    for (int q = 0; q < nrhs; ++q) z[q * stride + e] = dinv[q * dstride + e] * r[q * stride + e];
+}
+template <typename T>
+void launch_dinv_mul(const T* dinv, int64_t dstride, const T* r, T* z, int64_t n, int64_t stride, int nrhs, cudaStream_t st) {
+  int blocks = (int)((n + 255) / 256);
+  if (blocks > 4096) blocks = 4096;
+  (note_launch(), k_dinv_mul<T><<<blocks, 256, 0, st>>>(dinv, dstride, r, z, n, stride, nrhs));
+}
+template void launch_dinv_mul<double>(const double*, int64_t, const double*, double*, int64_t, int64_t, int, cudaStream_t);
+template void launch_dinv_mul<float>(const float*, int64_t, const float*, float*, int64_t, int64_t, int, cudaStream_t);
 #define INSTMG(T)                                                                                                   \
   template void launch_prolong_add<T>(const Grid&, const Grid&, const T*, int64_t, T*, int64_t, int, cudaStream_t); \
   template void launch_restrict<T>(const Grid&, const Grid&, const T*, int64_t, T*, int64_t, int, cudaStream_t);    \
@@ -726,6 +910,13 @@ template void launch_add_scaled<double, double>(double*, const double*, double, 
                                      int64_t, int, cudaStream_t);                                                   \
   template void launch_mask<T>(const Grid&, T*, int64_t, int, cudaStream_t);                                        \
   template void launch_mask_u<T>(const Grid&, T*, int64_t, int, cudaStream_t);                                      \
+  template void launch_mq_line_solve<T>(const Grid&, const TabT<T>&, const T*, const T*, int64_t, T*, int64_t, double, int, \
+                                        cudaStream_t);                                                              \
+  template void launch_BTp<T>(const Grid&, const TabT<T>&, const T*, int64_t, const T*, int64_t, T*, int64_t, double, \
+                              int, cudaStream_t);                                                                   \
+  template void launch_q_fix_constrained<T>(const Grid&, const T*, int64_t, T*, int64_t, int, cudaStream_t);        \
+  template void launch_schur_out<T>(const Grid&, const TabT<T>&, const T*, int64_t, const T*, int64_t, double,       \
+                                    const double*, T*, int64_t, int, cudaStream_t);                                 \
   template void launch_schur_dinv<T>(const Grid&, const TabT<T>&, const T*, const double*, double, T*, int, cudaStream_t); \
   template void launch_cheb_update_r<T>(const T*, const T*, const T*, T*, const T*, T*, double, double, int, int64_t, int, \
                                         cudaStream_t);                                                              \
