@@ -107,8 +107,8 @@ typedef struct {
   int schur_degree;     /* Chebyshev degree of the flux-pressure Schur solve (default 32) */
   int mg_min_cells;     /* stop coarsening at this many cells per direction (default 2) */
   double beta_fs;       /* fixed-stress parameter; <= 0 selects b^2 / K_dr */
-  int lumped_flux_mass; /* 0 (default): Darcy mass inverted exactly by line solves in the flux-pressure
-                           block; 1: replaced by its diagonal */
+  int flux_mass_exact;  /* flux-pressure block: 0 (default) replaces the Darcy mass by its diagonal;
+                           1 inverts it exactly by line solves */
 } biot_opts;
 
 typedef struct {

@@ -38,7 +38,7 @@ class Coeffs(C.Structure):
 
 class Opts(C.Structure):
     _fields_ = [("gmres_restart", C.c_int), ("cheb_degree", C.c_int), ("schur_degree", C.c_int),
-                ("mg_min_cells", C.c_int), ("beta_fs", C.c_double), ("lumped_flux_mass", C.c_int)]
+                ("mg_min_cells", C.c_int), ("beta_fs", C.c_double), ("flux_mass_exact", C.c_int)]
 
 
 class SolveOpts(C.Structure):

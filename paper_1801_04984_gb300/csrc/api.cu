@@ -289,6 +289,7 @@ struct GraphEntry {
 
 struct biot_ctx {
   Grid g;
+  int lumped_flux = 1;
   bool use_graphs = true;
   std::map<GraphKey, GraphEntry> graphs;
   cudaStream_t ws = nullptr;   // the library's own work stream (graphs need a capturable stream)
@@ -633,7 +634,7 @@ void schur_apply(biot_ctx& c, double tau, const double* cm, const T* p, T* out, 
   PrecWork<T>& w = c.pw<T>();
   const Grid& g = c.g;
   int64_t nqt = g.nq[0] + g.nq[1] + g.nq[2];
-  if (c.opts.lumped_flux_mass) {
+  if (c.lumped_flux) {
     launch_schur_apply<T>(g, c.tab<T>(), p, g.Np, c.dmq<T>(), w.tq, nqt, tau, cm, out, g.Np, nrhs, st);
   } else {
     launch_BTp<T>(g, c.tab<T>(), p, g.Np, nullptr, 0, w.tq, nqt, 1.0, nrhs, st);
@@ -650,7 +651,7 @@ void flux_solve(biot_ctx& c, double tau, const T* base, int64_t sb, const T* p, 
   PrecWork<T>& w = c.pw<T>();
   const Grid& g = c.g;
   int64_t nqt = g.nq[0] + g.nq[1] + g.nq[2];
-  if (c.opts.lumped_flux_mass) {
+  if (c.lumped_flux) {
     if (p) launch_q_final<T>(g, c.tab<T>(), base, sb, p, g.Np, c.dmq<T>(), tau, coef, qo, so, nrhs, st);
     else launch_q_jacobi<T>(g, c.tab<T>(), base, sb, c.dmq<T>(), tau, qo, so, nrhs, st);
   } else {
@@ -702,6 +703,15 @@ void schur_solve(biot_ctx& c, double tau, cudaStream_t st) {
     w.schur_tau = tau;
   }
   ChebCoef cc = cheb_coefs(c.opts.schur_degree, lmax / 30.0, 1.1 * lmax);
+  if (c.lumped_flux) {
+    for (int k = 0; k < cc.n; ++k) {
+      launch_schur_cheb<T>(g, c.tab<T>(), c.dmq<T>(), c.sb2<T>(), cm, tau, cc.c1[k], cc.c2[k], k == 0 ? 1 : 0, w.gp, w.pp, w.pd,
+                           w.pxo, c.nt, st);
+      CKL();
+      std::swap(w.pp, w.pxo);
+    }
+    return;
+  }
   for (int k = 0; k < cc.n; ++k) {
     bool first = (k == 0);
     if (!first) schur_apply<T>(c, tau, cm, w.pp, w.pAx, c.nt, st);
@@ -1306,16 +1316,17 @@ extern "C" int biot_setup(const biot_mesh* mesh, const biot_coeffs* co, int r, c
     d.schur_degree = 32;
     d.mg_min_cells = 2;
     d.beta_fs = -1;
-    d.lumped_flux_mass = 0;
+    d.flux_mass_exact = 0;
     if (opts) {
       if (opts->gmres_restart > 0) d.gmres_restart = std::min(opts->gmres_restart, 60);
       if (opts->cheb_degree > 0) d.cheb_degree = std::min(opts->cheb_degree, 30);
       if (opts->schur_degree > 0) d.schur_degree = std::min(opts->schur_degree, 30);
       if (opts->mg_min_cells > 0) d.mg_min_cells = opts->mg_min_cells;
       d.beta_fs = opts->beta_fs;
-      d.lumped_flux_mass = opts->lumped_flux_mass;
+      d.flux_mass_exact = opts->flux_mass_exact ? 1 : 0;
     }
     c->opts = d;
+    c->lumped_flux = d.flux_mass_exact ? 0 : 1;
     c->beta = (d.beta_fs > 0) ? d.beta_fs : c->b * c->b / c->Kdr;
     build_tables(c->g, c->t64);
     c->t32 = cast_tables<float>(c->t64);

@@ -19,16 +19,20 @@ namespace biot {
 // elasticity term tables: out comp i += coef * X_i(Y(Z(u_j)))
 // ops: 0 M, 1 K, 2 G, 3 G^T ; coef: 0 -> 2mu+lam, 1 -> mu, 2 -> lam
 struct Term3 { int j, i, xop, yop, zop, coef; };
-__constant__ Term3 c_terms3[21] = {
-    // output x
-    {0, 0, 1, 0, 0, 0}, {0, 0, 0, 1, 0, 1}, {0, 0, 0, 0, 1, 1},
-    {1, 0, 2, 3, 0, 1}, {2, 0, 2, 0, 3, 1}, {1, 0, 3, 2, 0, 2}, {2, 0, 3, 0, 2, 2},
-    // output y
-    {1, 1, 1, 0, 0, 1}, {1, 1, 0, 1, 0, 0}, {1, 1, 0, 0, 1, 1}, {2, 1, 0, 2, 3, 1}, {2, 1, 0, 3, 2, 2},
-    {0, 1, 3, 2, 0, 1}, {0, 1, 2, 3, 0, 2},
-    // output z
-    {2, 2, 1, 0, 0, 1}, {2, 2, 0, 0, 1, 0}, {2, 2, 0, 1, 0, 1}, {1, 2, 0, 3, 2, 1}, {1, 2, 0, 2, 3, 2},
-    {0, 2, 3, 0, 2, 1}, {0, 2, 2, 0, 3, 2}};
+// compile-time table (folded after unrolling, so per-thread accumulators stay in registers)
+__host__ __device__ constexpr Term3 term3(int t) {
+  constexpr Term3 tab[21] = {
+      // output x
+      {0, 0, 1, 0, 0, 0}, {0, 0, 0, 1, 0, 1}, {0, 0, 0, 0, 1, 1},
+      {1, 0, 2, 3, 0, 1}, {2, 0, 2, 0, 3, 1}, {1, 0, 3, 2, 0, 2}, {2, 0, 3, 0, 2, 2},
+      // output y
+      {1, 1, 1, 0, 0, 1}, {1, 1, 0, 1, 0, 0}, {1, 1, 0, 0, 1, 1}, {2, 1, 0, 2, 3, 1}, {2, 1, 0, 3, 2, 2},
+      {0, 1, 3, 2, 0, 1}, {0, 1, 2, 3, 0, 2},
+      // output z
+      {2, 2, 1, 0, 0, 1}, {2, 2, 0, 0, 1, 0}, {2, 2, 0, 1, 0, 1}, {1, 2, 0, 3, 2, 1}, {1, 2, 0, 2, 3, 2},
+      {0, 2, 3, 0, 2, 1}, {0, 2, 2, 0, 3, 2}};
+  return tab[t];
+}
 
 struct Term2 { int j, i, xop, yop, coef; };
 __constant__ Term2 c_terms2[8] = {
@@ -83,100 +87,136 @@ __device__ inline T gather_Ep(const Grid& g, const TabT<T>& tb, const T* __restr
 }
 
 // ---------------------------------------------------------------------------
-// 3-D displacement rows.  grid: (tiles_x, tiles_y, tiles_z); 256 threads.
+// 3-D displacement rows.  grid: (tiles_x, tiles_y, tiles_z * nt); 256 threads;
+// one block = one 8^3-node output tile of one temporal level k.
 // u_in: nt levels of [u_0|u_1|u_2] at stride su; p_in (may be null): nt levels at stride sp;
 // y: nt levels at stride sy.  Y_k = au[k] A u_k + E(sum_l ep[k][l] p_l) on free rows, u_k on constrained rows.
-template <typename T>
-__global__ void __launch_bounds__(256) k_apply_u3(Grid g, TabT<T> tb, SlabCoef sc, const T* __restrict__ u_in, int64_t su,
-                                                  const T* __restrict__ p_in, int64_t sp, T* __restrict__ y, int64_t sy) {
+// ALLJ: the z pass runs for all three input components at once (3 barriers per
+// tile; needs 12 z-pass arrays in shared memory, used for FP32), otherwise
+// component by component (4 arrays, used for FP64 where shared memory is 2x).
+// bit (2*dir + side) set when that face constrains component c
+__device__ inline int face_mask(const Grid& g, int c) {
+  int m = 0;
+  for (int f = 0; f < 2 * g.dim; ++f) {
+    int b = g.ubc[f];
+    if (b == U_DIRICHLET || (b == U_ROLLER && c == f / 2)) m |= 1 << f;
+  }
+  return m;
+}
+__device__ __forceinline__ bool free_fast(int m, int gx, int gy, int gz, int nx, int ny, int nz) {
+  return !(((m & 1) && gx == 0) || ((m & 2) && gx == nx - 1) || ((m & 4) && gy == 0) || ((m & 8) && gy == ny - 1) ||
+           ((m & 16) && gz == 0) || ((m & 32) && gz == nz - 1));
+}
+
+constexpr int U3_THREADS = 384;
+
+template <typename T, bool ALLJ>
+__global__ void __launch_bounds__(U3_THREADS, ALLJ ? 2 : 1) k_apply_u3(Grid g, TabT<T> tb, SlabCoef sc, const T* __restrict__ u_in,
+                                                                        int64_t su, const T* __restrict__ p_in, int64_t sp,
+                                                                        T* __restrict__ y, int64_t sy) {
+  constexpr int NZO = ALLJ ? 12 : 4;
+  constexpr int HH = H3 * H3, HHH = H3 * H3 * H3;
+  constexpr int ZO = H3 * H3 * T3;   // one z-pass array
+  constexpr int PX = H3 * T3 * T3;   // one pre-x array
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* s_in = reinterpret_cast<T*>(smem_raw);           // 3 * H3^3
-  T* s_zo = s_in + 3 * H3 * H3 * H3;                    // 4 * H3*H3*T3
-  T* s_px = s_zo + 4 * H3 * H3 * T3;                    // 12 * H3*T3*T3
+  T* s_in = reinterpret_cast<T*>(smem_raw);  // 3 * H3^3
+  T* s_zo = s_in + 3 * HHH;                  // NZO * ZO
+  T* s_px = s_zo + NZO * ZO;                 // 12 * PX
   __shared__ T s_tab[3][4][4][5];
-  const int tid = threadIdx.x, nth = blockDim.x;
-  for (int i = tid; i < 3 * 4 * 4 * 5; i += nth) (&s_tab[0][0][0][0])[i] = (&tb.q2[0][0][0][0])[i];
-  const int X0 = blockIdx.x * T3, Y0 = blockIdx.y * T3, Z0 = blockIdx.z * T3;
-  const int ex = min(T3, g.nu[0] - X0), ey = min(T3, g.nu[1] - Y0), ez = min(T3, g.nu[2] - Z0);
-  const T cf[3] = {T(2.0 * sc.mu + sc.lam), T(sc.mu), T(sc.lam)};
+  const int tid = threadIdx.x;
+  for (int i = tid; i < 3 * 4 * 4 * 5; i += U3_THREADS) (&s_tab[0][0][0][0])[i] = (&tb.q2[0][0][0][0])[i];
+  const int nx = g.nu[0], ny = g.nu[1], nz = g.nu[2];
+  const int ntz = (nz + T3 - 1) / T3;
+  const int k = blockIdx.z / ntz;
+  const int X0 = blockIdx.x * T3, Y0 = blockIdx.y * T3, Z0 = (blockIdx.z - k * ntz) * T3;
+  const T cf0 = T(2.0 * sc.mu + sc.lam), cf1 = T(sc.mu), cf2 = T(sc.lam);
   const int64_t nn = g.nnode;
-  // region sizes
-  const int rx = ex + 4, ry = ey + 4, rz = ez + 4;
-  for (int k = 0; k < sc.nt; ++k) {
-    const T* u = u_in + k * su;
+  const T* u = u_in + k * su;
+  const int fm0 = face_mask(g, 0), fm1 = face_mask(g, 1), fm2 = face_mask(g, 2);
+  // load the masked input region (zero outside the domain and on constrained nodes); full-size
+  // regions with compile-time extents, partial tiles simply see more zero padding
+  for (int i = tid; i < 3 * HHH; i += U3_THREADS) {
+    const int c = i / HHH;
+    const int rem = i - c * HHH;
+    const int lz = rem / HH, ly = (rem / H3) % H3, lx = rem % H3;
+    const int gx = X0 + lx - 2, gy = Y0 + ly - 2, gz = Z0 + lz - 2;
+    const int fm = c == 0 ? fm0 : (c == 1 ? fm1 : fm2);
+    T v = 0;
+    if ((unsigned)gx < (unsigned)nx && (unsigned)gy < (unsigned)ny && (unsigned)gz < (unsigned)nz && free_fast(fm, gx, gy, gz, nx, ny, nz))
+      v = u[c * nn + ((int64_t)gz * ny + gy) * nx + gx];
+    s_in[i] = v;
+  }
+  for (int i = tid; i < 12 * PX; i += U3_THREADS) s_px[i] = 0;
+  constexpr int NJ = ALLJ ? 1 : 3;
+  for (int jj = 0; jj < NJ; ++jj) {
     __syncthreads();
-    // load masked input region
-    for (int i = tid; i < 3 * rx * ry * rz; i += nth) {
-      int c = i / (rx * ry * rz);
-      int rem = i - c * rx * ry * rz;
-      int lz = rem / (rx * ry);
-      rem -= lz * rx * ry;
-      int ly = rem / rx, lx = rem - ly * rx;
-      int gx = X0 + lx - 2, gy = Y0 + ly - 2, gz = Z0 + lz - 2;
-      T v = 0;
-      if (gx >= 0 && gx < g.nu[0] && gy >= 0 && gy < g.nu[1] && gz >= 0 && gz < g.nu[2] && u_free(g, c, gx, gy, gz))
-        v = u[c * nn + ((int64_t)gz * g.nu[1] + gy) * g.nu[0] + gx];
-      s_in[c * H3 * H3 * H3 + (lz * H3 + ly) * H3 + lx] = v;
-    }
-    for (int i = tid; i < 12 * H3 * T3 * T3; i += nth) s_px[i] = 0;
-    for (int j = 0; j < 3; ++j) {
-      __syncthreads();
-      // z pass: zo[op][z][y][x] over x < rx, y < ry, z < ez
-      const T* in = s_in + j * H3 * H3 * H3;
-      for (int i = tid; i < rx * ry * ez; i += nth) {
-        int lz = i / (rx * ry);
-        int rem = i - lz * rx * ry;
-        int ly = rem / rx, lx = rem - ly * rx;
-        int rt = rowtype(Z0 + lz, g.nu[2]);
-        const T* v = in + (lz * H3 + ly) * H3 + lx;  // taps at lz..lz+4 (offset -2..2 around lz+2)
-        for (int op = 0; op < 4; ++op) s_zo[op * H3 * H3 * T3 + (lz * H3 + ly) * H3 + lx] = tap5(s_tab[2][op][rt], v, H3 * H3);
-      }
-      __syncthreads();
-      // y pass: accumulate into px[(i,xop)][z][y][x] over x < rx, y < ey, z < ez
-      for (int i = tid; i < rx * ey * ez; i += nth) {
-        int lz = i / (rx * ey);
-        int rem = i - lz * rx * ey;
-        int ly = rem / rx, lx = rem - ly * rx;
-        int rt = rowtype(Y0 + ly, g.nu[1]);
+    // z pass over the (H3 x H3 x T3) region
+    for (int i = tid; i < ZO; i += U3_THREADS) {
+      const int lz = i / HH, rem = i - lz * HH;  // rem = ly * H3 + lx
+      const T* tz = &s_tab[2][0][rowtype(Z0 + lz, nz)][0];
 #pragma unroll
-        for (int t = 0; t < 21; ++t) {
-          const Term3 tm = c_terms3[t];
-          if (tm.j != j) continue;
-          const T* v = s_zo + tm.zop * H3 * H3 * T3 + (lz * H3 + ly) * H3 + lx;
-          T val = tap5(s_tab[1][tm.yop][rt], v, H3);
-          s_px[(tm.i * 4 + tm.xop) * H3 * T3 * T3 + (lz * T3 + ly) * H3 + lx] += cf[tm.coef] * val;
+      for (int j = 0; j < (ALLJ ? 3 : 1); ++j) {
+        const int jin = ALLJ ? j : jj;
+        const T* v = s_in + jin * HHH + lz * HH + rem;
+        const T w0 = v[0], w1 = v[HH], w2 = v[2 * HH], w3 = v[3 * HH], w4 = v[4 * HH];
+#pragma unroll
+        for (int op = 0; op < 4; ++op) {
+          const T* cz = tz + op * 4 * 5;
+          s_zo[(j * 4 + op) * ZO + i] = cz[0] * w0 + cz[1] * w1 + cz[2] * w2 + cz[3] * w3 + cz[4] * w4;
         }
       }
     }
     __syncthreads();
-    // x pass and output
-    T* yk = y + k * sy;
-    for (int i = tid; i < ex * ey * ez; i += nth) {
-      int lz = i / (ex * ey);
-      int rem = i - lz * ex * ey;
-      int ly = rem / ex, lx = rem - ly * ex;
-      int gx = X0 + lx, gy = Y0 + ly, gz = Z0 + lz;
-      int rt = rowtype(gx, g.nu[0]);
-      int64_t node = ((int64_t)gz * g.nu[1] + gy) * g.nu[0] + gx;
-      for (int c = 0; c < 3; ++c) {
-        T out;
-        if (u_free(g, c, gx, gy, gz)) {
-          T acc = 0;
+    // y pass over the (H3 x T3 x T3) region, accumulated into the pre-x arrays
+    for (int i = tid; i < PX; i += U3_THREADS) {
+      const int lz = i / (T3 * H3), rem = i - lz * (T3 * H3);
+      const int ly = rem / H3, lx = rem - ly * H3;
+      const int rt = rowtype(Y0 + ly, ny);
+      const int zoff = lz * HH + ly * H3 + lx;
+      T acc[12];
 #pragma unroll
-          for (int op = 0; op < 4; ++op)
-            acc += tap5(s_tab[0][op][rt], s_px + (c * 4 + op) * H3 * T3 * T3 + (lz * T3 + ly) * H3 + lx, 1);
-          out = T(sc.au[k]) * acc;
-          if (p_in) {
-            for (int l = 0; l < sc.nt; ++l) {
-              T e = T(sc.ep[k][l]);
-              if (e != T(0)) out += e * gather_Ep<T, 3>(g, tb, p_in + l * sp, c, gx, gy, gz);
-            }
+      for (int q = 0; q < 12; ++q) acc[q] = 0;
+#pragma unroll
+      for (int t = 0; t < 21; ++t) {
+        const Term3 tm = term3(t);
+        if (!ALLJ && tm.j != jj) continue;
+        const int slot = ALLJ ? (tm.j * 4 + tm.zop) : tm.zop;
+        const T cfv = tm.coef == 0 ? cf0 : (tm.coef == 1 ? cf1 : cf2);
+        acc[tm.i * 4 + tm.xop] += cfv * tap5(s_tab[1][tm.yop][rt], s_zo + slot * ZO + zoff, H3);
+      }
+#pragma unroll
+      for (int q = 0; q < 12; ++q) s_px[q * PX + i] += acc[q];
+    }
+  }
+  __syncthreads();
+  // x pass and output over the (T3 x T3 x T3) tile
+  T* yk = y + k * sy;
+  for (int i = tid; i < T3 * T3 * T3; i += U3_THREADS) {
+    const int lz = i / (T3 * T3), ly = (i / T3) % T3, lx = i % T3;
+    const int gx = X0 + lx, gy = Y0 + ly, gz = Z0 + lz;
+    if (gx >= nx || gy >= ny || gz >= nz) continue;
+    const int rt = rowtype(gx, nx);
+    const int64_t node = ((int64_t)gz * ny + gy) * nx + gx;
+    const int poff = (lz * T3 + ly) * H3 + lx;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const int fm = c == 0 ? fm0 : (c == 1 ? fm1 : fm2);
+      T out;
+      if (free_fast(fm, gx, gy, gz, nx, ny, nz)) {
+        T acc = 0;
+#pragma unroll
+        for (int op = 0; op < 4; ++op) acc += tap5(s_tab[0][op][rt], s_px + (c * 4 + op) * PX + poff, 1);
+        out = T(sc.au[k]) * acc;
+        if (p_in) {
+          for (int l = 0; l < sc.nt; ++l) {
+            T e = T(sc.ep[k][l]);
+            if (e != T(0)) out += e * gather_Ep<T, 3>(g, tb, p_in + l * sp, c, gx, gy, gz);
           }
-        } else {
-          out = u_in[k * su + c * nn + node];
         }
-        yk[c * nn + node] = out;
+      } else {
+        out = u[c * nn + node];
       }
+      yk[c * nn + node] = out;
     }
   }
 }
@@ -347,30 +387,44 @@ __global__ void k_apply_p(Grid g, TabT<T> tb, SlabCoef sc, const T* __restrict__
   T mp = T(1);
   for (int d = 0; d < DIM; ++d) mp *= tb.wg[d];
   T eu[MAXR], bq[MAXR], pv[MAXR];
+  // the cell's Q2 node block and the per-component face masks, shared by all levels
+  int fm[3];
+  for (int c = 0; c < DIM; ++c) fm[c] = face_mask(g, c);
+  T f[DIM][3][3];  // f[c][d][a]: 1-D factor of E^T for component c along direction d
+#pragma unroll
+  for (int c = 0; c < DIM; ++c)
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+        f[c][d][a] = (d < DIM) ? ((d == c) ? tb.bd[d][a][gq[d]] : tb.bv[d][a][gq[d]]) : (a == 0 ? T(1) : T(0));
+  const int nx = g.nu[0], ny = g.nu[1], nz = g.nu[2];
   for (int l = 0; l < sc.nt; ++l) {
     const T* xl = x + l * sx;
     // E^T u: the cell's 3^DIM nodes, all components
     T acc = 0;
+#pragma unroll
     for (int c = 0; c < DIM; ++c) {
-      T f[3][3];
-      for (int d = 0; d < 3; ++d)
-        for (int a = 0; a < 3; ++a) f[d][a] = (d < DIM) ? ((d == c) ? tb.bd[d][a][gq[d]] : tb.bv[d][a][gq[d]]) : (a == 0 ? T(1) : T(0));
-      const int az_n = (DIM == 3) ? 3 : 1;
-      for (int az = 0; az < az_n; ++az)
+      constexpr int AZ = (DIM == 3) ? 3 : 1;
+#pragma unroll
+      for (int az = 0; az < AZ; ++az)
+#pragma unroll
         for (int ay = 0; ay < 3; ++ay) {
-          int iz = 2 * cell[2] + az, iy = 2 * cell[1] + ay;
-          const T* row = xl + c * g.nnode + ((int64_t)iz * g.nu[1] + iy) * g.nu[0];
+          const int iz = 2 * cell[2] + az, iy = 2 * cell[1] + ay;
+          const T* row = xl + c * g.nnode + ((int64_t)iz * ny + iy) * nx;
           T s = 0;
+#pragma unroll
           for (int ax = 0; ax < 3; ++ax) {
-            int ix = 2 * cell[0] + ax;
-            if (u_free(g, c, ix, iy, iz)) s += f[0][ax] * row[ix];
+            const int ix = 2 * cell[0] + ax;
+            if (free_fast(fm[c], ix, iy, iz, nx, ny, nz)) s += f[c][0][ax] * row[ix];
           }
-          acc += f[2][az] * f[1][ay] * s;
+          acc += f[c][2][az] * f[c][1][ay] * s;
         }
     }
     eu[l] = acc;
     // B q: for each component c the 3 DoFs along c on this Gauss line
     T bacc = 0;
+#pragma unroll
     for (int c = 0; c < DIM; ++c) {
       int sh[3];
       for (int d = 0; d < 3; ++d) sh[d] = (d < DIM) ? ((d == c) ? g.nu[d] : g.ng[d]) : 1;
@@ -383,6 +437,7 @@ __global__ void k_apply_p(Grid g, TabT<T> tb, SlabCoef sc, const T* __restrict__
       }
       const T* qc = xl + g.offq[c] + base;
       T s = 0;
+#pragma unroll
       for (int a = 0; a < 3; ++a) {
         int ia = 2 * cell[c] + a;
         if (q_free(g, c, ia)) s += tb.bd[c][a][gq[c]] * qc[(int64_t)ia * stride_c];
@@ -429,10 +484,11 @@ template <typename T>
 void launch_apply_u(const Grid& g, const TabT<T>& tb, const SlabCoef& sc, const T* u, int64_t su, const T* p, int64_t sp, T* y,
                     int64_t sy, cudaStream_t st) {
   if (g.dim == 3) {
-    dim3 grid((g.nu[0] + T3 - 1) / T3, (g.nu[1] + T3 - 1) / T3, (g.nu[2] + T3 - 1) / T3);
-    size_t smem = sizeof(T) * (3 * H3 * H3 * H3 + 4 * H3 * H3 * T3 + 12 * H3 * T3 * T3);
+    constexpr bool ALLJ = sizeof(T) == 4;
+    dim3 grid((g.nu[0] + T3 - 1) / T3, (g.nu[1] + T3 - 1) / T3, ((g.nu[2] + T3 - 1) / T3) * sc.nt);
+    size_t smem = sizeof(T) * (3 * H3 * H3 * H3 + (ALLJ ? 12 : 4) * H3 * H3 * T3 + 12 * H3 * T3 * T3);
     prof_begin(st, 0);
-    (note_launch(), k_apply_u3<T><<<grid, 256, smem, st>>>(g, tb, sc, u, su, p, sp, y, sy));
+    (note_launch(), k_apply_u3<T, ALLJ><<<grid, U3_THREADS, smem, st>>>(g, tb, sc, u, su, p, sp, y, sy));
     prof_end(st, 0);
   } else {
     dim3 grid((g.nu[0] + T2 - 1) / T2, (g.nu[1] + T2 - 1) / T2, 1);
@@ -470,10 +526,10 @@ void launch_diag_A(const Grid& g, const TabT<T>& tb, double lam, double mu, T* d
 void apply_init_attributes() {
   static bool done = false;
   if (done) return;
-  cudaFuncSetAttribute(k_apply_u3<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaFuncSetAttribute(k_apply_u3<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)(sizeof(double) * (3 * H3 * H3 * H3 + 4 * H3 * H3 * T3 + 12 * H3 * T3 * T3)));
-  cudaFuncSetAttribute(k_apply_u3<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)(sizeof(float) * (3 * H3 * H3 * H3 + 4 * H3 * H3 * T3 + 12 * H3 * T3 * T3)));
+  cudaFuncSetAttribute(k_apply_u3<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)(sizeof(float) * (3 * H3 * H3 * H3 + 12 * H3 * H3 * T3 + 12 * H3 * T3 * T3)));
   done = true;
 }
 

@@ -51,11 +51,13 @@ template <typename T>
 __global__ void k_prolong_add(Grid gf, Grid gc, const T* __restrict__ xc, int64_t sc, T* __restrict__ xf, int64_t sf, int nrhs) {
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= gf.nnode) return;
+  const int c = blockIdx.y % gf.dim, r = blockIdx.y / gf.dim;
   int f[3];
   f[0] = (int)(t % gf.nu[0]);
   int64_t rr = t / gf.nu[0];
   f[1] = (int)(rr % gf.nu[1]);
   f[2] = (int)(rr / gf.nu[1]);
+  if (!u_free(gf, c, f[0], f[1], f[2])) return;
   // the coarse correction is zero on constrained coarse nodes (identity rows with zero data)
   int ci[3][3], cnt[3];
   T w[3][3];
@@ -63,67 +65,60 @@ __global__ void k_prolong_add(Grid gf, Grid gc, const T* __restrict__ xc, int64_
     if (d < gf.dim) cnt[d] = prolong_taps<T>(f[d], ci[d], w[d]);
     else { cnt[d] = 1; ci[d][0] = 0; w[d][0] = T(1); }
   }
-  for (int c = 0; c < gf.dim; ++c) {
-    if (!u_free(gf, c, f[0], f[1], f[2])) continue;
-    for (int r = 0; r < nrhs; ++r) {
-      const T* src = xc + r * sc + c * gc.nnode;
-      T acc = 0;
-      for (int a = 0; a < cnt[2]; ++a)
-        for (int b = 0; b < cnt[1]; ++b) {
-          const T* row = src + ((int64_t)ci[2][a] * gc.nu[1] + ci[1][b]) * gc.nu[0];
-          T s = 0;
-          for (int e = 0; e < cnt[0]; ++e) s += w[0][e] * row[ci[0][e]];
-          acc += w[2][a] * w[1][b] * s;
-        }
-      xf[r * sf + c * gf.nnode + t] += acc;
+  const T* src = xc + r * sc + c * gc.nnode;
+  T acc = 0;
+  for (int a = 0; a < cnt[2]; ++a)
+    for (int b = 0; b < cnt[1]; ++b) {
+      const T* row = src + ((int64_t)ci[2][a] * gc.nu[1] + ci[1][b]) * gc.nu[0];
+      T s = 0;
+      for (int e = 0; e < cnt[0]; ++e) s += w[0][e] * row[ci[0][e]];
+      acc += w[2][a] * w[1][b] * s;
     }
-  }
+  xf[r * sf + c * gf.nnode + t] += acc;
 }
 
 template <typename T>
 __global__ void k_restrict(Grid gf, Grid gc, const T* __restrict__ rf, int64_t sf, T* __restrict__ rc, int64_t sc, int nrhs) {
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= gc.nnode) return;
+  const int c = blockIdx.y % gf.dim, r = blockIdx.y / gf.dim;
   int cidx[3];
   cidx[0] = (int)(t % gc.nu[0]);
   int64_t rr = t / gc.nu[0];
   cidx[1] = (int)(rr % gc.nu[1]);
   cidx[2] = (int)(rr / gc.nu[1]);
+  T acc = 0;
   // the fine residual is zero on constrained fine nodes (identity rows, x = b there)
-  int fi[3][5], cnt[3];
-  T w[3][5];
-  for (int d = 0; d < 3; ++d) {
-    if (d < gf.dim) cnt[d] = restrict_taps<T>(cidx[d], gf.nu[d], fi[d], w[d]);
-    else { cnt[d] = 1; fi[d][0] = 0; w[d][0] = T(1); }
-  }
-  for (int c = 0; c < gf.dim; ++c) {
-    const bool fr = u_free(gc, c, cidx[0], cidx[1], cidx[2]);
-    for (int r = 0; r < nrhs; ++r) {
-      T acc = 0;
-      if (fr) {
-        const T* src = rf + r * sf + c * gf.nnode;
-        for (int a = 0; a < cnt[2]; ++a)
-          for (int b = 0; b < cnt[1]; ++b) {
-            const T* row = src + ((int64_t)fi[2][a] * gf.nu[1] + fi[1][b]) * gf.nu[0];
-            T s = 0;
-            for (int e = 0; e < cnt[0]; ++e) s += w[0][e] * row[fi[0][e]];
-            acc += w[2][a] * w[1][b] * s;
-          }
-      }
-      rc[r * sc + c * gc.nnode + t] = acc;
+  if (u_free(gc, c, cidx[0], cidx[1], cidx[2])) {
+    int fi[3][5], cnt[3];
+    T w[3][5];
+    for (int d = 0; d < 3; ++d) {
+      if (d < gf.dim) cnt[d] = restrict_taps<T>(cidx[d], gf.nu[d], fi[d], w[d]);
+      else { cnt[d] = 1; fi[d][0] = 0; w[d][0] = T(1); }
     }
+    const T* src = rf + r * sf + c * gf.nnode;
+    for (int a = 0; a < cnt[2]; ++a)
+      for (int b = 0; b < cnt[1]; ++b) {
+        const T* row = src + ((int64_t)fi[2][a] * gf.nu[1] + fi[1][b]) * gf.nu[0];
+        T s = 0;
+        for (int e = 0; e < cnt[0]; ++e) s += w[0][e] * row[fi[0][e]];
+        acc += w[2][a] * w[1][b] * s;
+      }
   }
+  rc[r * sc + c * gc.nnode + t] = acc;
 }
 
 template <typename T>
 void launch_prolong_add(const Grid& fine, const Grid& coarse, const T* xc, int64_t sc, T* xf, int64_t sf, int nrhs,
                         cudaStream_t st) {
-  (note_launch(), k_prolong_add<T><<<(int)((fine.nnode + 255) / 256), 256, 0, st>>>(fine, coarse, xc, sc, xf, sf, nrhs));
+  dim3 grid((unsigned)((fine.nnode + 255) / 256), fine.dim * nrhs);
+  (note_launch(), k_prolong_add<T><<<grid, 256, 0, st>>>(fine, coarse, xc, sc, xf, sf, nrhs));
 }
 template <typename T>
 void launch_restrict(const Grid& fine, const Grid& coarse, const T* rf, int64_t sf, T* rc, int64_t sc, int nrhs,
                      cudaStream_t st) {
-  (note_launch(), k_restrict<T><<<(int)((coarse.nnode + 255) / 256), 256, 0, st>>>(fine, coarse, rf, sf, rc, sc, nrhs));
+  dim3 grid((unsigned)((coarse.nnode + 255) / 256), fine.dim * nrhs);
+  (note_launch(), k_restrict<T><<<grid, 256, 0, st>>>(fine, coarse, rf, sf, rc, sc, nrhs));
 }
 
 // ---------------------------------------------------------------------------
@@ -403,7 +398,8 @@ __global__ void k_u_rhs(Grid g, TabT<T> tb, const T* __restrict__ ru, int64_t sr
   int iy = (int)(rr % g.nu[1]);
   int iz = (int)(rr / g.nu[1]);
   int idx[3] = {ix, iy, iz};
-  for (int c = 0; c < DIM; ++c) {
+  {
+    const int c = blockIdx.y;
     bool fr = u_free(g, c, ix, iy, iz);
     // taps of E along each direction
     int pi[3][4], cnt[3];
@@ -495,9 +491,9 @@ void launch_q_final(const Grid& g, const TabT<T>& tb, const T* rq, int64_t srq, 
 template <typename T>
 void launch_u_rhs(const Grid& g, const TabT<T>& tb, const T* ru, int64_t sru, const T* p, int64_t spp, double alpha, T* bu,
                   int64_t sbu, int nrhs, cudaStream_t st) {
-  int blocks = (int)((g.nnode + 255) / 256);
-  if (g.dim == 3) (note_launch(), k_u_rhs<T, 3><<<blocks, 256, 0, st>>>(g, tb, ru, sru, p, spp, alpha, bu, sbu, nrhs));
-  else (note_launch(), k_u_rhs<T, 2><<<blocks, 256, 0, st>>>(g, tb, ru, sru, p, spp, alpha, bu, sbu, nrhs));
+  dim3 grid((unsigned)((g.nnode + 255) / 256), g.dim);
+  if (g.dim == 3) (note_launch(), k_u_rhs<T, 3><<<grid, 256, 0, st>>>(g, tb, ru, sru, p, spp, alpha, bu, sbu, nrhs));
+  else (note_launch(), k_u_rhs<T, 2><<<grid, 256, 0, st>>>(g, tb, ru, sru, p, spp, alpha, bu, sbu, nrhs));
 }
 
 
@@ -890,6 +886,86 @@ void launch_dinv_mul(const T* dinv, int64_t dstride, const T* r, T* z, int64_t n
 }
 template void launch_dinv_mul<double>(const double*, int64_t, const double*, double*, int64_t, int64_t, int, cudaStream_t);
 template void launch_dinv_mul<float>(const float*, int64_t, const float*, float*, int64_t, int64_t, int, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// One Chebyshev-Jacobi step on the lumped flux-pressure Schur complement
+//   Shat_r = cm[r] Mp + tau B diag(Mq)^{-1} B^T,
+// applied as a direct stencil on the Gauss-point pressure grid: through the
+// flux DoFs on its Gauss line in direction c, a pressure point couples to the
+// pressure points of its own cell and of the neighbour cell across each face.
+// first: d = c2 Dinv b, xo = d;  else: d = c1 d + c2 Dinv (b - Shat x), xo = x + d.
+template <typename T, int DIM>
+__global__ void __launch_bounds__(256) k_schur_cheb(Grid g, TabT<T> tb, const T* __restrict__ dmq, const T* __restrict__ sb2,
+                                                    RhsCoef cm, T tau, T c1, T c2, int first, const T* __restrict__ b,
+                                                    const T* __restrict__ x, T* __restrict__ d, T* __restrict__ xo, int nrhs) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= g.Np) return;
+  const int r = blockIdx.y;
+  const int64_t np = g.Np;
+  T mp = 1;
+  for (int k = 0; k < DIM; ++k) mp *= tb.wg[k];
+  const T dinv = T(1) / (T(cm.c[r]) * mp + tau * sb2[t]);
+  const int64_t i = r * np + t;
+  if (first) {
+    T dn = c2 * dinv * b[i];
+    d[i] = dn;
+    xo[i] = dn;
+    return;
+  }
+  int co[3];
+  co[0] = (int)(t % g.ng[0]);
+  int64_t rr = t / g.ng[0];
+  co[1] = (int)(rr % g.ng[1]);
+  co[2] = (int)(rr / g.ng[1]);
+  const T* xr = x + r * np;
+  const int64_t pst[3] = {1, g.ng[0], (int64_t)g.ng[0] * g.ng[1]};
+  T acc = 0;
+#pragma unroll
+  for (int c = 0; c < DIM; ++c) {
+    int sh[3];
+    for (int k = 0; k < 3; ++k) sh[k] = (k < DIM) ? ((k == c) ? g.nu[k] : g.ng[k]) : 1;
+    T wt = 1;
+    int64_t qbase = 0, mul = 1, stride_c = 1;
+    for (int k = 0; k < 3; ++k) {
+      if (k == c) stride_c = mul;
+      else { qbase += co[k] * mul; if (k < DIM) wt *= tb.wg[k]; }
+      mul *= sh[k];
+    }
+    qbase += g.offq[c] - g.Nu;
+    const int cell = co[c] >> 1, gq = co[c] & 1;
+    const int64_t pline = t - (int64_t)co[c] * pst[c];  // pressure index of along-c coordinate 0 on this line
+    T sc = 0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const int ia = 2 * cell + a;
+      if (!q_free(g, c, ia)) continue;
+      // (B^T x) at this flux DoF: the cells sharing it along c
+      T btp = 0;
+#pragma unroll
+      for (int k = 0; k < 2; ++k) btp += tb.bd[c][a][k] * xr[pline + (int64_t)(2 * cell + k) * pst[c]];
+      if (a == 0 && cell >= 1)
+        for (int k = 0; k < 2; ++k) btp += tb.bd[c][2][k] * xr[pline + (int64_t)(2 * cell - 2 + k) * pst[c]];
+      if (a == 2 && cell + 1 < g.n[c])
+        for (int k = 0; k < 2; ++k) btp += tb.bd[c][0][k] * xr[pline + (int64_t)(2 * cell + 2 + k) * pst[c]];
+      sc += tb.bd[c][a][gq] * btp / dmq[qbase + (int64_t)ia * stride_c];
+    }
+    acc += wt * wt * sc;
+  }
+  T sx = T(cm.c[r]) * mp * xr[t] + tau * acc;
+  T dn = c2 * dinv * (b[i] - sx);
+  if (c1 != T(0)) dn += c1 * d[i];
+  d[i] = dn;
+  xo[i] = xr[t] + dn;
+}
+template <typename T>
+void launch_schur_cheb(const Grid& g, const TabT<T>& tb, const T* dmq, const T* sb2, const double* cm, double tau, double c1,
+                       double c2, int first, const T* b, const T* x, T* d, T* xo, int nrhs, cudaStream_t st) {
+  RhsCoef rc;
+  for (int r = 0; r < MAXR; ++r) rc.c[r] = (r < nrhs) ? cm[r] : 0.0;
+  dim3 grid((unsigned)((g.Np + 255) / 256), nrhs);
+  if (g.dim == 3) (note_launch(), k_schur_cheb<T, 3><<<grid, 256, 0, st>>>(g, tb, dmq, sb2, rc, T(tau), T(c1), T(c2), first, b, x, d, xo, nrhs));
+  else (note_launch(), k_schur_cheb<T, 2><<<grid, 256, 0, st>>>(g, tb, dmq, sb2, rc, T(tau), T(c1), T(c2), first, b, x, d, xo, nrhs));
+}
 #define INSTMG(T)                                                                                                   \
   template void launch_prolong_add<T>(const Grid&, const Grid&, const T*, int64_t, T*, int64_t, int, cudaStream_t); \
   template void launch_restrict<T>(const Grid&, const Grid&, const T*, int64_t, T*, int64_t, int, cudaStream_t);    \
@@ -910,6 +986,8 @@ template void launch_dinv_mul<float>(const float*, int64_t, const float*, float*
                                      int64_t, int, cudaStream_t);                                                   \
   template void launch_mask<T>(const Grid&, T*, int64_t, int, cudaStream_t);                                        \
   template void launch_mask_u<T>(const Grid&, T*, int64_t, int, cudaStream_t);                                      \
+  template void launch_schur_cheb<T>(const Grid&, const TabT<T>&, const T*, const T*, const double*, double, double, \
+                                     double, int, const T*, const T*, T*, T*, int, cudaStream_t);                  \
   template void launch_mq_line_solve<T>(const Grid&, const TabT<T>&, const T*, const T*, int64_t, T*, int64_t, double, int, \
                                         cudaStream_t);                                                              \
   template void launch_BTp<T>(const Grid&, const TabT<T>&, const T*, int64_t, const T*, int64_t, T*, int64_t, double, \

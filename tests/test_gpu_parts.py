@@ -17,10 +17,10 @@ pytestmark = pytest.mark.gpu
 CASES = [((9, 7), consolidation_bcs(2)), ((6, 5, 4), consolidation_bcs(3)), ((5, 4, 6), mixed_bcs(3))]
 
 
-def _ctx(n, bcs, K):
+def _ctx(n, bcs, K, exact=0):
     from paper_1801_04984_gb300 import binding as B
     ubc, fbc = bcs
-    return B.Context(len(n), n, dict(C2, K=K), 1, ubc, fbc)
+    return B.Context(len(n), n, dict(C2, K=K), 1, ubc, fbc, opts=dict(flux_mass_exact=exact))
 
 
 @pytest.mark.parametrize("n,bcs", CASES)
@@ -28,7 +28,7 @@ def test_flux_mass_inverse_and_schur(n, bcs):
     from paper_1801_04984_gb300 import binding as B
     rng = np.random.default_rng(21)
     K = 1e-2 * np.exp(rng.normal(0, 1.5, size=int(np.prod(n))))
-    ctx = _ctx(n, bcs, K)
+    ctx = _ctx(n, bcs, K, exact=1)
     m = Mesh(n)
     blk = SpatialBlocks(m, dict(C2, K=K))
     mask = constraint_mask(m, *bcs)
@@ -91,3 +91,27 @@ def test_elasticity_block_and_vcycle_contraction(n, bcs):
     rho = (norms[-1] / norms[0]) ** (1.0 / 6)
     assert rho < 0.35, norms
     del Aop
+
+
+@pytest.mark.parametrize("n,bcs", CASES)
+def test_lumped_schur(n, bcs):
+    """Default flux-pressure block: the Darcy mass replaced by its diagonal."""
+    from paper_1801_04984_gb300 import binding as B
+    rng = np.random.default_rng(23)
+    K = 1e-2 * np.exp(rng.normal(0, 1.5, size=int(np.prod(n))))
+    ctx = _ctx(n, bcs, K, exact=0)
+    m = Mesh(n)
+    blk = SpatialBlocks(m, dict(C2, K=K))
+    mask = constraint_mask(m, *bcs)
+    fq = mask[m.Nu:m.off_p] == 1.0
+    tau = 0.07
+    x = rng.normal(size=m.N)
+    xd = torch.tensor(x, device="cuda")
+    yd = torch.empty_like(xd)
+    ctx.apply_part(B.PART_SCHUR, tau, xd, yd)
+    Mq = blk.Mq.tocsr()[fq][:, fq]
+    Bf = blk.B.tocsr()[:, fq]
+    p = x[m.off_p:]
+    beta = C2["b"] ** 2 / C2["K_dr"]
+    ref = (C2["invM"] + beta) * (blk.Mp @ p) + tau * (Bf @ ((Bf.T @ p) / Mq.diagonal()))
+    assert np.abs(yd.cpu().numpy()[m.off_p:] - ref).max() < 1e-11 * np.abs(ref).max()
