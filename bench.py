@@ -164,6 +164,8 @@ def main():
     ap.add_argument("--slabs", type=int, default=16)
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison march")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--cheb-degree", type=int, default=0, help="elasticity smoother degree (0: library default)")
+    ap.add_argument("--schur-degree", type=int, default=0, help="Schur Chebyshev degree (0: library default)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -182,7 +184,8 @@ def main():
     n, r, slabs, T = args.n, args.r, args.slabs, 1.0
     g = layered_logk((n, n, n), layer_cells=4, std=1.5, seed=1801)
     ubc, fbc = consolidation_bcs(3)
-    ctx = B.Context(3, (n, n, n), dict(COEF, K=K0 * np.exp(g)), r, ubc, fbc)
+    ctx = B.Context(3, (n, n, n), dict(COEF, K=K0 * np.exp(g)), r, ubc, fbc,
+                    opts=dict(cheb_degree=args.cheb_degree, schur_degree=args.schur_degree))
     dev = torch.device("cuda", torch.cuda.current_device())
     f = torch.zeros(ctx.n_space, dtype=torch.float64, device=dev)
     ctx.load_preset(B.LOAD_TRACTION_TOP, 1.0, f)

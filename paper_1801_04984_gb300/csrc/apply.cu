@@ -221,6 +221,188 @@ __global__ void __launch_bounds__(U3_THREADS, ALLJ ? 2 : 1) k_apply_u3(Grid g, T
   }
 }
 
+// ---------------------------------------------------------------------------
+// FP32 3-D displacement rows, column form.  Same algorithm and staging as
+// k_apply_u3<float, true>, but every work item owns a whole line of the tile
+// in registers: a z pass item loads its 12 staged values once and produces the
+// 8 outputs of all 4 operators; a y pass item owns one pre-x target (output
+// component i, x operator) along y; an x pass item owns one output component
+// along x.  Vertex rows use 5 taps, mid rows 3; domain-boundary vertex rows
+// differ only in the centre tap (zero padding outside the domain).
+template <int OP, typename T>
+__device__ __forceinline__ void col8(const T (&tab)[4][4][5], int g0, int nn, const T* w, T* out) {
+  // w[0..11]: staged line (offset -2), out[0..7]: outputs of operator OP along the line
+#pragma unroll
+  for (int o = 0; o < 8; ++o) {
+    const int gi = g0 + o;
+    if ((o & 1) == 0) {
+      const int rt = (gi == 0) ? 2 : ((gi == nn - 1) ? 3 : 0);
+      out[o] = tab[OP][0][0] * w[o] + tab[OP][0][1] * w[o + 1] + tab[OP][rt][2] * w[o + 2] + tab[OP][0][3] * w[o + 3] +
+               tab[OP][0][4] * w[o + 4];
+    } else {
+      out[o] = tab[OP][1][1] * w[o + 1] + tab[OP][1][2] * w[o + 2] + tab[OP][1][3] * w[o + 3];
+    }
+  }
+}
+
+template <int Q, typename T>
+__device__ __forceinline__ void ypass_target(const T* __restrict__ s_zo, T* __restrict__ s_px, const T (&tab)[4][4][5], int Y0,
+                                             int ny, int lz, int lx, T cf0, T cf1, T cf2) {
+  constexpr int HH = H3 * H3, ZO = H3 * H3 * T3, PX = H3 * T3 * T3;
+  T acc[8];
+#pragma unroll
+  for (int o = 0; o < 8; ++o) acc[o] = 0;
+#pragma unroll
+  for (int t = 0; t < 21; ++t) {
+    const Term3 tm = term3(t);
+    if (tm.i * 4 + tm.xop != Q) continue;
+    const T* src = s_zo + (tm.j * 4 + tm.zop) * ZO + lz * HH + lx;
+    T w[12];
+#pragma unroll
+    for (int y = 0; y < 12; ++y) w[y] = src[y * H3];
+    T o8[8];
+    switch (tm.yop) {
+      case 0: col8<0>(tab, Y0, ny, w, o8); break;
+      case 1: col8<1>(tab, Y0, ny, w, o8); break;
+      case 2: col8<2>(tab, Y0, ny, w, o8); break;
+      default: col8<3>(tab, Y0, ny, w, o8); break;
+    }
+    const T cfv = tm.coef == 0 ? cf0 : (tm.coef == 1 ? cf1 : cf2);
+#pragma unroll
+    for (int o = 0; o < 8; ++o) acc[o] += cfv * o8[o];
+  }
+  T* dst = s_px + Q * PX + lz * (T3 * H3) + lx;
+#pragma unroll
+  for (int o = 0; o < 8; ++o) dst[o * H3] = acc[o];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(U3_THREADS, 2) k_apply_u3_col(Grid g, TabT<T> tb, SlabCoef sc, const T* __restrict__ u_in,
+                                                                 int64_t su, const T* __restrict__ p_in, int64_t sp,
+                                                                 T* __restrict__ y, int64_t sy) {
+  constexpr int HH = H3 * H3, HHH = H3 * H3 * H3;
+  constexpr int ZO = H3 * H3 * T3;
+  constexpr int PX = H3 * T3 * T3;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* s_in = reinterpret_cast<T*>(smem_raw);  // 3 * H3^3
+  T* s_zo = s_in + 3 * HHH;                  // 12 * ZO
+  T* s_px = s_zo + 12 * ZO;                  // 12 * PX
+  __shared__ T s_tab[3][4][4][5];
+  const int tid = threadIdx.x;
+  for (int i = tid; i < 3 * 4 * 4 * 5; i += U3_THREADS) (&s_tab[0][0][0][0])[i] = (&tb.q2[0][0][0][0])[i];
+  const int nx = g.nu[0], ny = g.nu[1], nz = g.nu[2];
+  const int ntz = (nz + T3 - 1) / T3;
+  const int k = blockIdx.z / ntz;
+  const int X0 = blockIdx.x * T3, Y0 = blockIdx.y * T3, Z0 = (blockIdx.z - k * ntz) * T3;
+  const T cf0 = T(2.0 * sc.mu + sc.lam), cf1 = T(sc.mu), cf2 = T(sc.lam);
+  const int64_t nn = g.nnode;
+  const T* u = u_in + k * su;
+  const int fm0 = face_mask(g, 0), fm1 = face_mask(g, 1), fm2 = face_mask(g, 2);
+  for (int i = tid; i < 3 * HHH; i += U3_THREADS) {
+    const int c = i / HHH;
+    const int rem = i - c * HHH;
+    const int lz = rem / HH, ly = (rem / H3) % H3, lx = rem % H3;
+    const int gx = X0 + lx - 2, gy = Y0 + ly - 2, gz = Z0 + lz - 2;
+    const int fm = c == 0 ? fm0 : (c == 1 ? fm1 : fm2);
+    T v = 0;
+    if ((unsigned)gx < (unsigned)nx && (unsigned)gy < (unsigned)ny && (unsigned)gz < (unsigned)nz && free_fast(fm, gx, gy, gz, nx, ny, nz))
+      v = u[c * nn + ((int64_t)gz * ny + gy) * nx + gx];
+    s_in[i] = v;
+  }
+  __syncthreads();
+  // z pass: item = (component, y, x) line along z
+  for (int it = tid; it < 3 * HH; it += U3_THREADS) {
+    const int c = it / HH, rem = it - c * HH;
+    const T* src = s_in + c * HHH + rem;
+    T w[12];
+#pragma unroll
+    for (int z = 0; z < 12; ++z) w[z] = src[z * HH];
+    T o8[8];
+    T* dst = s_zo + (c * 4) * ZO + rem;
+    col8<0>(s_tab[2], Z0, nz, w, o8);
+#pragma unroll
+    for (int o = 0; o < 8; ++o) dst[o * HH] = o8[o];
+    col8<1>(s_tab[2], Z0, nz, w, o8);
+#pragma unroll
+    for (int o = 0; o < 8; ++o) dst[ZO + o * HH] = o8[o];
+    col8<2>(s_tab[2], Z0, nz, w, o8);
+#pragma unroll
+    for (int o = 0; o < 8; ++o) dst[2 * ZO + o * HH] = o8[o];
+    col8<3>(s_tab[2], Z0, nz, w, o8);
+#pragma unroll
+    for (int o = 0; o < 8; ++o) dst[3 * ZO + o * HH] = o8[o];
+  }
+  __syncthreads();
+  // y pass: item = (pre-x target q = 4 i + xop, z, x) line along y
+  for (int it = tid; it < 12 * T3 * H3; it += U3_THREADS) {
+    const int q = it / (T3 * H3), rem = it - q * (T3 * H3);
+    const int lz = rem / H3, lx = rem - lz * H3;
+    switch (q) {
+      case 0: ypass_target<0>(s_zo, s_px, s_tab[1], Y0, ny, lz, lx, cf0, cf1, cf2); break;
+      case 1: ypass_target<1>(s_zo, s_px, s_tab[1], Y0, ny, lz, lx, cf0, cf1, cf2); break;
+      case 2: ypass_target<2>(s_zo, s_px, s_tab[1], Y0, ny, lz, lx, cf0, cf1, cf2); break;
+      case 3: ypass_target<3>(s_zo, s_px, s_tab[1], Y0, ny, lz, lx, cf0, cf1, cf2); break;
+      case 4: ypass_target<4>(s_zo, s_px, s_tab[1], Y0, ny, lz, lx, cf0, cf1, cf2); break;
+      case 5: ypass_target<5>(s_zo, s_px, s_tab[1], Y0, ny, lz, lx, cf0, cf1, cf2); break;
+      case 6: ypass_target<6>(s_zo, s_px, s_tab[1], Y0, ny, lz, lx, cf0, cf1, cf2); break;
+      case 7: ypass_target<7>(s_zo, s_px, s_tab[1], Y0, ny, lz, lx, cf0, cf1, cf2); break;
+      case 8: ypass_target<8>(s_zo, s_px, s_tab[1], Y0, ny, lz, lx, cf0, cf1, cf2); break;
+      case 9: ypass_target<9>(s_zo, s_px, s_tab[1], Y0, ny, lz, lx, cf0, cf1, cf2); break;
+      case 10: ypass_target<10>(s_zo, s_px, s_tab[1], Y0, ny, lz, lx, cf0, cf1, cf2); break;
+      default: ypass_target<11>(s_zo, s_px, s_tab[1], Y0, ny, lz, lx, cf0, cf1, cf2); break;
+    }
+  }
+  __syncthreads();
+  // x pass and output: item = (component, z, y) line along x
+  T* yk = y + k * sy;
+  for (int it = tid; it < 3 * T3 * T3; it += U3_THREADS) {
+    const int c = it / (T3 * T3), rem = it - c * (T3 * T3);
+    const int lz = rem / T3, ly = rem - lz * T3;
+    const int gy = Y0 + ly, gz = Z0 + lz;
+    if (gy >= ny || gz >= nz) continue;
+    T acc[8];
+#pragma unroll
+    for (int o = 0; o < 8; ++o) acc[o] = 0;
+    const T* src = s_px + (c * 4) * PX + (lz * T3 + ly) * H3;
+#pragma unroll
+    for (int op = 0; op < 4; ++op) {
+      T w[12];
+#pragma unroll
+      for (int x = 0; x < 12; ++x) w[x] = src[op * PX + x];
+      T o8[8];
+      switch (op) {
+        case 0: col8<0>(s_tab[0], X0, nx, w, o8); break;
+        case 1: col8<1>(s_tab[0], X0, nx, w, o8); break;
+        case 2: col8<2>(s_tab[0], X0, nx, w, o8); break;
+        default: col8<3>(s_tab[0], X0, nx, w, o8); break;
+      }
+#pragma unroll
+      for (int o = 0; o < 8; ++o) acc[o] += o8[o];
+    }
+    const int fm = c == 0 ? fm0 : (c == 1 ? fm1 : fm2);
+    const T au = T(sc.au[k]);
+#pragma unroll
+    for (int o = 0; o < 8; ++o) {
+      const int gx = X0 + o;
+      if (gx >= nx) break;
+      const int64_t node = ((int64_t)gz * ny + gy) * nx + gx;
+      T out;
+      if (free_fast(fm, gx, gy, gz, nx, ny, nz)) {
+        out = au * acc[o];
+        if (p_in) {
+          for (int l = 0; l < sc.nt; ++l) {
+            T e = T(sc.ep[k][l]);
+            if (e != T(0)) out += e * gather_Ep<T, 3>(g, tb, p_in + l * sp, c, gx, gy, gz);
+          }
+        }
+      } else {
+        out = u[c * nn + node];
+      }
+      yk[c * nn + node] = out;
+    }
+  }
+}
+
 // 2-D displacement rows: tiles of 16x16 nodes, passes y then x.
 template <typename T>
 __global__ void __launch_bounds__(256) k_apply_u2(Grid g, TabT<T> tb, SlabCoef sc, const T* __restrict__ u_in, int64_t su,
@@ -488,7 +670,8 @@ void launch_apply_u(const Grid& g, const TabT<T>& tb, const SlabCoef& sc, const 
     dim3 grid((g.nu[0] + T3 - 1) / T3, (g.nu[1] + T3 - 1) / T3, ((g.nu[2] + T3 - 1) / T3) * sc.nt);
     size_t smem = sizeof(T) * (3 * H3 * H3 * H3 + (ALLJ ? 12 : 4) * H3 * H3 * T3 + 12 * H3 * T3 * T3);
     prof_begin(st, 0);
-    (note_launch(), k_apply_u3<T, ALLJ><<<grid, U3_THREADS, smem, st>>>(g, tb, sc, u, su, p, sp, y, sy));
+    if (ALLJ) (note_launch(), k_apply_u3_col<T><<<grid, U3_THREADS, smem, st>>>(g, tb, sc, u, su, p, sp, y, sy));
+    else (note_launch(), k_apply_u3<T, false><<<grid, U3_THREADS, smem, st>>>(g, tb, sc, u, su, p, sp, y, sy));
     prof_end(st, 0);
   } else {
     dim3 grid((g.nu[0] + T2 - 1) / T2, (g.nu[1] + T2 - 1) / T2, 1);
@@ -529,6 +712,8 @@ void apply_init_attributes() {
   cudaFuncSetAttribute(k_apply_u3<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)(sizeof(double) * (3 * H3 * H3 * H3 + 4 * H3 * H3 * T3 + 12 * H3 * T3 * T3)));
   cudaFuncSetAttribute(k_apply_u3<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)(sizeof(float) * (3 * H3 * H3 * H3 + 12 * H3 * H3 * T3 + 12 * H3 * T3 * T3)));
+  cudaFuncSetAttribute(k_apply_u3_col<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)(sizeof(float) * (3 * H3 * H3 * H3 + 12 * H3 * H3 * T3 + 12 * H3 * T3 * T3)));
   done = true;
 }
