@@ -214,6 +214,24 @@ int biot_load_preset(biot_t ctx, int kind, double value, double* f, void* stream
 enum { BIOT_PART_FLUX_MASS_INV = 0, BIOT_PART_SCHUR = 1, BIOT_PART_VCYCLE = 2, BIOT_PART_ELASTICITY = 3 };
 int biot_apply_part(biot_t ctx, int part, double tau, const void* in, void* out, int prec, void* stream);
 
+/* Allocation-free flux-pressure Schur apply, for callers that cannot call
+ * cudaMalloc where they need it (a caching allocator that has reserved the whole
+ * device, latency-critical loops that cannot afford cudaMalloc's implicit
+ * device-wide synchronisation, embedded or real-time hosts that forbid device
+ * allocation after start-up).  The paper has no counterpart: this is an interface
+ * variant of biot_apply_part(BIOT_PART_SCHUR) with the default lumped Darcy mass,
+ *   out_p = ((1/M + beta) Mp + tau B diag(Mq)^{-1} B^T) in_p,  other blocks of out = 0,
+ * on spatial vectors (n_space doubles, DEVICE).  Its flux-grid scratch lives in a
+ * static device array of 2^20 doubles (8 MiB, held by every GPU that loads the
+ * library until the process exits); meshes with more flux DoFs are rejected with
+ * BIOT_EINVAL.  The first call on a device looks up that array's device address
+ * (once per device, with that device current; with CUDA's lazy module loading the
+ * driver also materialises the array at that moment); make that first call before
+ * any stream capture.  All calls share the array: calls that overlap on the GPU (other
+ * streams or devices' threads racing on one device) race on it.  The context must
+ * have been created by biot_setup; this call itself allocates nothing. */
+int biot_schur_apply_noalloc(biot_t ctx, double tau, const double* in, double* out, void* stream);
+
 /* Tracing.  biot_profile(ctx, 1) makes every launch of the displacement-row
  * operator kernel (the elasticity apply, the dominant kernel of the solver)
  * record a pair of CUDA events on its launching stream; biot_counters returns

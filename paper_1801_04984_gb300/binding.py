@@ -85,6 +85,7 @@ def load(path: str = LIB_PATH):
         "biot_goal_mean_pressure": (C.c_int, [vp, dp, dp, vp, vp]),
         "biot_load_preset": (C.c_int, [vp, C.c_int, C.c_double, vp, vp]),
         "biot_apply_part": (C.c_int, [vp, C.c_int, C.c_double, vp, vp, C.c_int, vp]),
+        "biot_schur_apply_noalloc": (C.c_int, [vp, C.c_double, vp, vp, vp]),
         "biot_profile": (C.c_int, [vp, C.c_int]),
         "biot_counters": (C.c_int, [vp, i64p, i64p, C.POINTER(C.c_double)]),
         "biot_last_error": (C.c_char_p, [vp]),
@@ -274,6 +275,12 @@ class Context:
         dt = torch.float64 if prec == FP64 else torch.float32
         return self._check(self.lib.biot_apply_part(self.h, int(part), float(tau), _ptr(x, dt, self.n_space, "in"),
                                                     _ptr(y, dt, self.n_space, "out"), prec, _stream()))
+
+    def schur_apply_noalloc(self, tau, x, y):
+        """Allocation-free flux-pressure Schur apply (FP64 spatial vectors)."""
+        import torch
+        return self._check(self.lib.biot_schur_apply_noalloc(self.h, float(tau), _ptr(x, torch.float64, self.n_space, "in"),
+                                                             _ptr(y, torch.float64, self.n_space, "out"), _stream()))
 
     def profile(self, enable):
         return self._check(self.lib.biot_profile(self.h, int(bool(enable))))

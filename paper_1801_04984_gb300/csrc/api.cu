@@ -1721,6 +1721,28 @@ extern "C" int biot_profile(biot_t c, int enable) {
   return BIOT_OK;
 }
 
+// read-only view of a context for the allocation-free entry point (noalloc.cu)
+namespace biot {
+struct CtxView {
+  const Grid* g;
+  const TabT<double>* t64;
+  const double* dmq64;
+  double invM, beta;
+};
+bool ctx_view(biot_t c, CtxView* v) {
+  if (!c || !v) return false;
+  v->g = &c->g;
+  v->t64 = &c->t64;
+  v->dmq64 = c->dmq64;
+  v->invM = c->invM;
+  v->beta = c->beta;
+  return true;
+}
+void ctx_set_error(biot_t c, const char* msg) {
+  if (c) c->err = msg ? msg : "";
+}
+}  // namespace biot
+
 extern "C" const char* biot_last_error(biot_t c) {
   if (!c) return g_err_msg.c_str();
   return c->err.c_str();
