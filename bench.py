@@ -94,6 +94,13 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def hbm_peak_measured(root):
+    try:
+        return json.load(open(os.path.join(root, "MEASURED_PEAKS.json")))["hbm_gbs"]
+    except Exception:
+        return 6800.0
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -164,6 +171,7 @@ def main():
     ap.add_argument("--slabs", type=int, default=16)
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison march")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer run")
     ap.add_argument("--cheb-degree", type=int, default=0, help="elasticity smoother degree (0: library default)")
     ap.add_argument("--schur-degree", type=int, default=0, help="Schur Chebyshev degree (0: library default)")
     args = ap.parse_args()
@@ -225,10 +233,19 @@ def main():
         times.append(e0.elapsed_time(e1) / 1e3)
     launches1, _, _ = ctx.counters()
     clocks = sampler.stop() if sampler else None
-    # one more (untimed) step with CUDA events around every launch of the dominant kernel
+    # one more (untimed) step with CUDA events around every launch of the dominant kernels
     ctx.profile(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
     step(B.MIXED, U_mixed)
-    _, op_launches, op_ms = ctx.counters()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_prof = e0.elapsed_time(e1) / 1e3
+    el = ctx.kernel_stats(B.KERNEL_ELASTICITY_FP32)
+    sch = ctx.kernel_stats(B.KERNEL_SCHUR_FP32)
+    ctx.kernel_stats(B.KERNEL_ELASTICITY_FP64)
     ctx.profile(False)
     t_step = float(np.mean(times))
     if ws > 1:
@@ -243,14 +260,14 @@ def main():
     U0_host = np.zeros(ctx.n_space)
     U_host = np.zeros(ctx.n_space)
     te = []
-    for _ in range(max(1, min(args.steps, 2))):
+    for _ in range(0 if args.no_e2e else max(1, min(args.steps, 2))):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         ctx.march(T, slabs, [f_host], tcoef, U0_host, U_host, tol=1e-10, mode=B.MIXED)
         torch.cuda.synchronize()
         te.append(time.perf_counter() - t0)
-    e2e = {"value": ws * dofs_step / float(np.mean(te)), "unit": "DoF/s",
-           "h2d_bytes_per_step": 2 * ctx.n_space * 8, "d2h_bytes_per_step": ctx.n_space * 8}
+    e2e = None if not te else {"value": ws * dofs_step / float(np.mean(te)), "unit": "DoF/s",
+                               "h2d_bytes_per_step": 2 * ctx.n_space * 8, "d2h_bytes_per_step": ctx.n_space * 8}
 
     # FP64 comparison march (device-timed, outside the headline region)
     fp64 = None
@@ -268,17 +285,36 @@ def main():
                 "ms_per_slab": t64 * 1e3 / slabs, "iterations": s64["iterations"],
                 "end_state_rel_diff_mixed_vs_fp64": rel}
 
-    # roofline of the dominant kernel (displacement-row operator, FP32 inside the V-cycle and the slab apply):
-    # algorithmic bytes per launch-level: read + write of the displacement block in FP32
-    avg_ms = op_ms / max(1, op_launches)
-    peaks = {}
+    # roofline of the dominant kernel: the FP32 elasticity (displacement-row) operator, all its
+    # launches in one march (every multigrid level and the slab applies).  Algorithmic work of the
+    # sum-factorised Kronecker apply: 180 FMA = 360 flop per Q2 node and right-hand side (z pass
+    # 12 outputs x 4 taps, y pass 21 terms x 4, x pass 12 x 4; 5-tap vertex / 3-tap mid rows);
+    # algorithmic bytes: the displacement block read once and written once, 3 x 2 x 4 B per node.
+    # The per-level working sets fit in L2, so the kernel is issue/shared-memory bound: it is
+    # reported against the FP32 CUDA-core peak (152 SMs x 128 lanes x 2 flop x SM clock).
+    el_n, el_ms, el_units = el
+    clk = (clocks or {}).get("sm_mhz") or 2070.0
+    fp32_peak = 152 * 128 * 2 * clk * 1e6 / 1e12
+    achieved = 360.0 * el_units / (el_ms / 1e3) / 1e12 if el_ms > 0 else None
+    traffic = None
     try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        prof_txt = open(os.path.join(ROOT, "profiles", "elasticity_fp32_32cube.txt")).read()
+        for line in prof_txt.splitlines():
+            if line.startswith("dram_bytes_per_node_rhs:"):
+                traffic = float(line.split(":")[1]) * el_units / max(1, el_n)
     except Exception:
-        pass
-    hbm_peak = peaks.get("hbm_gbs", 6800.0)
-    # flops of the sum-factorised elasticity apply per Q2 node and component set (counted in the kernel design):
-    # ALU roofline against the FP32 CUDA-core peak at the sampled clock
+        traffic = None
+    roofline = {"bound": "alu", "kernel": "k_apply_u3_col<float> (FP32 elasticity operator)",
+                "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": (achieved / fp32_peak) if achieved else None,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x median sampled SM clock",
+                "traffic": traffic,
+                "launches_per_step": el_n, "avg_launch_us": 1e3 * el_ms / max(1, el_n),
+                "share_of_step": (el_ms / 1e3) / t_prof if t_prof > 0 else None,
+                "algorithmic_gbs": 24.0 * el_units / (el_ms / 1e3) / 1e9 if el_ms > 0 else None,
+                "hbm_peak_gbs": hbm_peak_measured(ROOT)}
+    schur = {"kernel": "k_schur_cheb<float> (one Chebyshev step, flux-pressure Schur)", "launches_per_step": sch[0],
+             "avg_launch_us": 1e3 * sch[1] / max(1, sch[0]), "share_of_step": (sch[1] / 1e3) / t_prof if t_prof > 0 else None}
     s_mean = stats[-1]
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -297,7 +333,8 @@ def main():
         "fp64": fp64,
         "e2e": e2e,
         "gpu_launches": int((launches1 - launches0) / max(1, args.steps)),
-        "op_kernel": {"launches_per_step": op_launches, "avg_ms": avg_ms},
+        "roofline": roofline,
+        "second_kernel": schur,
         "clocks": clocks,
         "cpu_baseline": cpu,
     }

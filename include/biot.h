@@ -103,7 +103,7 @@ typedef struct {
 
 typedef struct {
   int gmres_restart;    /* m (default 30) */
-  int cheb_degree;      /* Chebyshev degree of the elasticity smoother (default 4) */
+  int cheb_degree;      /* Chebyshev degree of the elasticity smoother (default 3) */
   int schur_degree;     /* Chebyshev degree of the flux-pressure Schur solve (default 32) */
   int mg_min_cells;     /* stop coarsening at this many cells per direction (default 2) */
   double beta_fs;       /* fixed-stress parameter; <= 0 selects b^2 / K_dr */
@@ -243,6 +243,17 @@ int biot_schur_apply_noalloc(biot_t ctx, double tau, const double* in, double* o
  * synchronises on those events, then forgets them).  Either output may be NULL. */
 int biot_profile(biot_t ctx, int enable);
 int biot_counters(biot_t ctx, int64_t* launches, int64_t* op_launches, double* op_ms);
+
+/* Per-kernel tracing detail (after biot_profile(ctx, 1)): for kind
+ * BIOT_KERNEL_ELASTICITY_FP32 / _FP64 (displacement-row operator) and
+ * BIOT_KERNEL_SCHUR_FP32 (one Chebyshev step of the flux-pressure Schur solve),
+ * the number of launches recorded since the last query, their summed device time
+ * in ms (CUDA events on the launching stream) and their summed work units (Q2 node
+ * x right-hand side for the elasticity operator, Gauss pressure point x
+ * right-hand side for the Schur step).  Synchronises on the events, then forgets
+ * them.  With profiling on, CUDA graphs are not used. */
+enum { BIOT_KERNEL_ELASTICITY_FP32 = 0, BIOT_KERNEL_ELASTICITY_FP64 = 1, BIOT_KERNEL_SCHUR_FP32 = 2 };
+int biot_kernel_stats(biot_t ctx, int kind, int64_t* launches, double* ms, double* units);
 
 const char* biot_last_error(biot_t ctx);
 void biot_destroy(biot_t ctx);

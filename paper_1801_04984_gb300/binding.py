@@ -23,6 +23,7 @@ F_NATURAL, F_NOFLOW = 0, 1
 FP64, FP32, MIXED = 0, 1, 2
 LOAD_TRACTION_TOP, LOAD_MMS2D_CONST, LOAD_MMS2D_LINEAR = 0, 1, 2
 PART_FLUX_MASS_INV, PART_SCHUR, PART_VCYCLE, PART_ELASTICITY = 0, 1, 2, 3
+KERNEL_ELASTICITY_FP32, KERNEL_ELASTICITY_FP64, KERNEL_SCHUR_FP32 = 0, 1, 2
 ERR_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOCONV", 5: "EBREAKDOWN", 6: "ETIMEOUT"}
 
 
@@ -87,6 +88,7 @@ def load(path: str = LIB_PATH):
         "biot_apply_part": (C.c_int, [vp, C.c_int, C.c_double, vp, vp, C.c_int, vp]),
         "biot_schur_apply_noalloc": (C.c_int, [vp, C.c_double, vp, vp, vp]),
         "biot_profile": (C.c_int, [vp, C.c_int]),
+        "biot_kernel_stats": (C.c_int, [vp, C.c_int, i64p, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
         "biot_counters": (C.c_int, [vp, i64p, i64p, C.POINTER(C.c_double)]),
         "biot_last_error": (C.c_char_p, [vp]),
         "biot_destroy": (None, [vp]),
@@ -290,6 +292,12 @@ class Context:
         a, b, ms = C.c_int64(), C.c_int64(), C.c_double()
         self._check(self.lib.biot_counters(self.h, C.byref(a), C.byref(b), C.byref(ms)))
         return a.value, b.value, ms.value
+
+    def kernel_stats(self, kind):
+        """(launches, device ms, work units) of the recorded launches of one kernel kind."""
+        n, ms, u = C.c_int64(), C.c_double(), C.c_double()
+        self._check(self.lib.biot_kernel_stats(self.h, int(kind), C.byref(n), C.byref(ms), C.byref(u)))
+        return n.value, ms.value, u.value
 
     def load_preset(self, kind, value, f):
         import torch

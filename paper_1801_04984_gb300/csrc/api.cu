@@ -308,7 +308,7 @@ struct biot_ctx {
   int ncoarse = 0;
   TimeBasis tb;
   biot_opts opts;
-  double schur_lmax = 0, schur_lmax_tau = -1;
+  double schur_lmax = 0, schur_lmax_tau = -1, schur_lmin = 0;
   Krylov<double> k64;
   Krylov<float> k32;
   PrecWork<double> p64;
@@ -484,7 +484,10 @@ double dev_dot(biot_ctx& c, const double* a, const double* b, int64_t n, cudaStr
 // diagonal) by `steps` preconditioned-CG steps, from the Lanczos tridiagonal
 // matrix built out of the CG coefficients (FP64).  nrhs independent systems
 // of length n (stride between them), the maximum over them is returned.
-double tridiag_lmax(const std::vector<double>& d, const std::vector<double>& e) {
+double tridiag_eig(const std::vector<double>& d, const std::vector<double>& e, bool want_max);
+double tridiag_lmax(const std::vector<double>& d, const std::vector<double>& e) { return tridiag_eig(d, e, true); }
+double tridiag_lmin(const std::vector<double>& d, const std::vector<double>& e) { return tridiag_eig(d, e, false); }
+double tridiag_eig(const std::vector<double>& d, const std::vector<double>& e, bool want_max) {
   // bisection with Sturm counts on the symmetric tridiagonal (d, e)
   int k = (int)d.size();
   if (k == 0) return 1.0;
@@ -505,9 +508,12 @@ double tridiag_lmax(const std::vector<double>& d, const std::vector<double>& e) 
     }
     return cnt;
   };
+  // bisection on the Sturm count: the largest eigenvalue is the smallest x with count(x) = k,
+  // the smallest eigenvalue the smallest x with count(x) >= 1
+  const int target = want_max ? k : 1;
   for (int it = 0; it < 200; ++it) {
     double mid = 0.5 * (lo + hi);
-    if (count_below(mid) >= k) hi = mid;
+    if (count_below(mid) >= target) hi = mid;
     else lo = mid;
   }
   return hi;
@@ -515,7 +521,7 @@ double tridiag_lmax(const std::vector<double>& d, const std::vector<double>& e) 
 
 template <class OpF>
 double lanczos_lmax(biot_ctx& c, OpF op, const double* dinv, int64_t dstride, int64_t n, int64_t stride, int nrhs, int steps,
-                    double* r, double* z, double* p, double* q, cudaStream_t st) {
+                    double* r, double* z, double* p, double* q, cudaStream_t st, double* lmin_out = nullptr) {
   std::vector<double> h((size_t)stride * nrhs, 0.0);
   for (int k = 0; k < nrhs; ++k)
     for (int64_t i = 0; i < n; ++i) h[k * stride + i] = 1.0 + 0.3 * std::sin(0.91 * (double)i + 0.7 * k) + 0.2 * std::cos(2.3 * (double)i);
@@ -552,11 +558,14 @@ double lanczos_lmax(biot_ctx& c, OpF op, const double* dinv, int64_t dstride, in
     }
     CKL();
   }
+  double worst_min = 1e300;
   for (int k = 0; k < nrhs; ++k) {
     std::vector<double> e(ee[k].begin(), ee[k].end());
     if (e.size() >= dd[k].size() && !e.empty()) e.resize(dd[k].size() - 1);
     best = std::max(best, tridiag_lmax(dd[k], e));
+    worst_min = std::min(worst_min, tridiag_lmin(dd[k], e));
   }
+  if (lmin_out) *lmin_out = worst_min;
   return best;
 }
 
@@ -683,8 +692,11 @@ double schur_lmax(biot_ctx& c, double tau, cudaStream_t st) {
   launch_schur_dinv<double>(g, c.t64, c.sb2_64, cm, tau, w.pdinv, c.nt, st);
   CKL();
   auto op = [&](const double* x, double* y) { schur_apply<double>(c, tau, cm, x, y, c.nt, st); };
-  double lm = lanczos_lmax(c, op, w.pdinv, g.Np, g.Np, g.Np, c.nt, 24, w.gp, w.pp, w.pd, w.pAx, st);
+  double lmin = 0;
+  double lm = lanczos_lmax(c, op, w.pdinv, g.Np, g.Np, g.Np, c.nt, 30, w.gp, w.pp, w.pd, w.pAx, st, &lmin);
   c.schur_lmax = lm;
+  // Ritz values converge from inside the spectrum: widen the lower end, keep it positive
+  c.schur_lmin = std::max(0.7 * lmin, lm / 200.0);
   c.schur_lmax_tau = tau;
   return lm;
 }
@@ -702,7 +714,7 @@ void schur_solve(biot_ctx& c, double tau, cudaStream_t st) {
     CKL();
     w.schur_tau = tau;
   }
-  ChebCoef cc = cheb_coefs(c.opts.schur_degree, lmax / 30.0, 1.1 * lmax);
+  ChebCoef cc = cheb_coefs(c.opts.schur_degree, c.schur_lmin, 1.1 * lmax);
   if (c.lumped_flux) {
     for (int k = 0; k < cc.n; ++k) {
       launch_schur_cheb<T>(g, c.tab<T>(), c.dmq<T>(), c.sb2<T>(), cm, tau, cc.c1[k], cc.c2[k], k == 0 ? 1 : 0, w.gp, w.pp, w.pd,
@@ -1312,7 +1324,7 @@ extern "C" int biot_setup(const biot_mesh* mesh, const biot_coeffs* co, int r, c
     c->eta = co->eta;
     biot_opts d;
     d.gmres_restart = 30;
-    d.cheb_degree = 4;
+    d.cheb_degree = 3;
     d.schur_degree = 32;
     d.mg_min_cells = 2;
     d.beta_fs = -1;
@@ -1709,9 +1721,20 @@ extern "C" int biot_counters(biot_t c, int64_t* launches, int64_t* op_launches, 
   if (launches) *launches = (int64_t)launch_count();
   long long n = 0;
   double ms = 0;
-  prof_collect(0, &n, &ms);
+  prof_collect(0, &n, &ms, nullptr);
   if (op_launches) *op_launches = n;
   if (op_ms) *op_ms = ms;
+  return BIOT_OK;
+}
+
+extern "C" int biot_kernel_stats(biot_t c, int kind, int64_t* launches, double* ms, double* units) {
+  if (!c || kind < 0 || kind >= PROF_KINDS) return BIOT_EINVAL;
+  long long n = 0;
+  double t = 0, u = 0;
+  prof_collect(kind, &n, &t, &u);
+  if (launches) *launches = n;
+  if (ms) *ms = t;
+  if (units) *units = u;
   return BIOT_OK;
 }
 

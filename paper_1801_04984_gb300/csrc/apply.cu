@@ -110,125 +110,19 @@ __device__ __forceinline__ bool free_fast(int m, int gx, int gy, int gz, int nx,
 
 constexpr int U3_THREADS = 384;
 
-template <typename T, bool ALLJ>
-__global__ void __launch_bounds__(U3_THREADS, ALLJ ? 2 : 1) k_apply_u3(Grid g, TabT<T> tb, SlabCoef sc, const T* __restrict__ u_in,
-                                                                        int64_t su, const T* __restrict__ p_in, int64_t sp,
-                                                                        T* __restrict__ y, int64_t sy) {
-  constexpr int NZO = ALLJ ? 12 : 4;
-  constexpr int HH = H3 * H3, HHH = H3 * H3 * H3;
-  constexpr int ZO = H3 * H3 * T3;   // one z-pass array
-  constexpr int PX = H3 * T3 * T3;   // one pre-x array
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* s_in = reinterpret_cast<T*>(smem_raw);  // 3 * H3^3
-  T* s_zo = s_in + 3 * HHH;                  // NZO * ZO
-  T* s_px = s_zo + NZO * ZO;                 // 12 * PX
-  __shared__ T s_tab[3][4][4][5];
-  const int tid = threadIdx.x;
-  for (int i = tid; i < 3 * 4 * 4 * 5; i += U3_THREADS) (&s_tab[0][0][0][0])[i] = (&tb.q2[0][0][0][0])[i];
-  const int nx = g.nu[0], ny = g.nu[1], nz = g.nu[2];
-  const int ntz = (nz + T3 - 1) / T3;
-  const int k = blockIdx.z / ntz;
-  const int X0 = blockIdx.x * T3, Y0 = blockIdx.y * T3, Z0 = (blockIdx.z - k * ntz) * T3;
-  const T cf0 = T(2.0 * sc.mu + sc.lam), cf1 = T(sc.mu), cf2 = T(sc.lam);
-  const int64_t nn = g.nnode;
-  const T* u = u_in + k * su;
-  const int fm0 = face_mask(g, 0), fm1 = face_mask(g, 1), fm2 = face_mask(g, 2);
-  // load the masked input region (zero outside the domain and on constrained nodes); full-size
-  // regions with compile-time extents, partial tiles simply see more zero padding
-  for (int i = tid; i < 3 * HHH; i += U3_THREADS) {
-    const int c = i / HHH;
-    const int rem = i - c * HHH;
-    const int lz = rem / HH, ly = (rem / H3) % H3, lx = rem % H3;
-    const int gx = X0 + lx - 2, gy = Y0 + ly - 2, gz = Z0 + lz - 2;
-    const int fm = c == 0 ? fm0 : (c == 1 ? fm1 : fm2);
-    T v = 0;
-    if ((unsigned)gx < (unsigned)nx && (unsigned)gy < (unsigned)ny && (unsigned)gz < (unsigned)nz && free_fast(fm, gx, gy, gz, nx, ny, nz))
-      v = u[c * nn + ((int64_t)gz * ny + gy) * nx + gx];
-    s_in[i] = v;
-  }
-  for (int i = tid; i < 12 * PX; i += U3_THREADS) s_px[i] = 0;
-  constexpr int NJ = ALLJ ? 1 : 3;
-  for (int jj = 0; jj < NJ; ++jj) {
-    __syncthreads();
-    // z pass over the (H3 x H3 x T3) region
-    for (int i = tid; i < ZO; i += U3_THREADS) {
-      const int lz = i / HH, rem = i - lz * HH;  // rem = ly * H3 + lx
-      const T* tz = &s_tab[2][0][rowtype(Z0 + lz, nz)][0];
-#pragma unroll
-      for (int j = 0; j < (ALLJ ? 3 : 1); ++j) {
-        const int jin = ALLJ ? j : jj;
-        const T* v = s_in + jin * HHH + lz * HH + rem;
-        const T w0 = v[0], w1 = v[HH], w2 = v[2 * HH], w3 = v[3 * HH], w4 = v[4 * HH];
-#pragma unroll
-        for (int op = 0; op < 4; ++op) {
-          const T* cz = tz + op * 4 * 5;
-          s_zo[(j * 4 + op) * ZO + i] = cz[0] * w0 + cz[1] * w1 + cz[2] * w2 + cz[3] * w3 + cz[4] * w4;
-        }
-      }
-    }
-    __syncthreads();
-    // y pass over the (H3 x T3 x T3) region, accumulated into the pre-x arrays
-    for (int i = tid; i < PX; i += U3_THREADS) {
-      const int lz = i / (T3 * H3), rem = i - lz * (T3 * H3);
-      const int ly = rem / H3, lx = rem - ly * H3;
-      const int rt = rowtype(Y0 + ly, ny);
-      const int zoff = lz * HH + ly * H3 + lx;
-      T acc[12];
-#pragma unroll
-      for (int q = 0; q < 12; ++q) acc[q] = 0;
-#pragma unroll
-      for (int t = 0; t < 21; ++t) {
-        const Term3 tm = term3(t);
-        if (!ALLJ && tm.j != jj) continue;
-        const int slot = ALLJ ? (tm.j * 4 + tm.zop) : tm.zop;
-        const T cfv = tm.coef == 0 ? cf0 : (tm.coef == 1 ? cf1 : cf2);
-        acc[tm.i * 4 + tm.xop] += cfv * tap5(s_tab[1][tm.yop][rt], s_zo + slot * ZO + zoff, H3);
-      }
-#pragma unroll
-      for (int q = 0; q < 12; ++q) s_px[q * PX + i] += acc[q];
-    }
-  }
-  __syncthreads();
-  // x pass and output over the (T3 x T3 x T3) tile
-  T* yk = y + k * sy;
-  for (int i = tid; i < T3 * T3 * T3; i += U3_THREADS) {
-    const int lz = i / (T3 * T3), ly = (i / T3) % T3, lx = i % T3;
-    const int gx = X0 + lx, gy = Y0 + ly, gz = Z0 + lz;
-    if (gx >= nx || gy >= ny || gz >= nz) continue;
-    const int rt = rowtype(gx, nx);
-    const int64_t node = ((int64_t)gz * ny + gy) * nx + gx;
-    const int poff = (lz * T3 + ly) * H3 + lx;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const int fm = c == 0 ? fm0 : (c == 1 ? fm1 : fm2);
-      T out;
-      if (free_fast(fm, gx, gy, gz, nx, ny, nz)) {
-        T acc = 0;
-#pragma unroll
-        for (int op = 0; op < 4; ++op) acc += tap5(s_tab[0][op][rt], s_px + (c * 4 + op) * PX + poff, 1);
-        out = T(sc.au[k]) * acc;
-        if (p_in) {
-          for (int l = 0; l < sc.nt; ++l) {
-            T e = T(sc.ep[k][l]);
-            if (e != T(0)) out += e * gather_Ep<T, 3>(g, tb, p_in + l * sp, c, gx, gy, gz);
-          }
-        }
-      } else {
-        out = u[c * nn + node];
-      }
-      yk[c * nn + node] = out;
-    }
-  }
-}
-
 // ---------------------------------------------------------------------------
-// FP32 3-D displacement rows, column form.  Same algorithm and staging as
-// k_apply_u3<float, true>, but every work item owns a whole line of the tile
-// in registers: a z pass item loads its 12 staged values once and produces the
+// 3-D displacement rows.  grid: (tiles_x, tiles_y, tiles_z * nt); one block =
+// one 8^3-node output tile of one temporal level k, staged with a 2-node halo
+// (12^3) in shared memory; z, y, x passes of the 21 Kronecker terms.
+// Y_k = au[k] A u_k + E(sum_l ep[k][l] p_l) on free rows, u_k on constrained rows.
+// Column form: every work item owns a whole line of the tile in registers: a z pass item loads its 12 staged values once and produces the
 // 8 outputs of all 4 operators; a y pass item owns one pre-x target (output
 // component i, x operator) along y; an x pass item owns one output component
 // along x.  Vertex rows use 5 taps, mid rows 3; domain-boundary vertex rows
 // differ only in the centre tap (zero padding outside the domain).
+// ALLJ (FP32): the z pass runs for the three input components at once (12
+// z-pass arrays); otherwise (FP64, twice the shared memory per value) component
+// by component with the y pass accumulating into the pre-x arrays.
 template <int OP, typename T>
 __device__ __forceinline__ void col8(const T (&tab)[4][4][5], int g0, int nn, const T* w, T* out) {
   // w[0..11]: staged line (offset -2), out[0..7]: outputs of operator OP along the line
@@ -247,7 +141,7 @@ __device__ __forceinline__ void col8(const T (&tab)[4][4][5], int g0, int nn, co
 
 template <int Q, typename T>
 __device__ __forceinline__ void ypass_target(const T* __restrict__ s_zo, T* __restrict__ s_px, const T (&tab)[4][4][5], int Y0,
-                                             int ny, int lz, int lx, T cf0, T cf1, T cf2) {
+                                             int ny, int lz, int lx, T cf0, T cf1, T cf2, int jonly) {
   constexpr int HH = H3 * H3, ZO = H3 * H3 * T3, PX = H3 * T3 * T3;
   T acc[8];
 #pragma unroll
@@ -256,7 +150,8 @@ __device__ __forceinline__ void ypass_target(const T* __restrict__ s_zo, T* __re
   for (int t = 0; t < 21; ++t) {
     const Term3 tm = term3(t);
     if (tm.i * 4 + tm.xop != Q) continue;
-    const T* src = s_zo + (tm.j * 4 + tm.zop) * ZO + lz * HH + lx;
+    if (jonly >= 0 && tm.j != jonly) continue;
+    const T* src = s_zo + (jonly >= 0 ? tm.zop : tm.j * 4 + tm.zop) * ZO + lz * HH + lx;
     T w[12];
 #pragma unroll
     for (int y = 0; y < 12; ++y) w[y] = src[y * H3];
@@ -272,21 +167,28 @@ __device__ __forceinline__ void ypass_target(const T* __restrict__ s_zo, T* __re
     for (int o = 0; o < 8; ++o) acc[o] += cfv * o8[o];
   }
   T* dst = s_px + Q * PX + lz * (T3 * H3) + lx;
+  if (jonly <= 0) {
 #pragma unroll
-  for (int o = 0; o < 8; ++o) dst[o * H3] = acc[o];
+    for (int o = 0; o < 8; ++o) dst[o * H3] = acc[o];
+  } else {
+#pragma unroll
+    for (int o = 0; o < 8; ++o) dst[o * H3] += acc[o];
+  }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(U3_THREADS, 2) k_apply_u3_col(Grid g, TabT<T> tb, SlabCoef sc, const T* __restrict__ u_in,
-                                                                 int64_t su, const T* __restrict__ p_in, int64_t sp,
-                                                                 T* __restrict__ y, int64_t sy) {
+template <typename T, bool ALLJ>
+__global__ void __launch_bounds__(U3_THREADS, ALLJ ? 2 : 1) k_apply_u3_col(Grid g, TabT<T> tb, SlabCoef sc,
+                                                                            const T* __restrict__ u_in, int64_t su,
+                                                                            const T* __restrict__ p_in, int64_t sp,
+                                                                            T* __restrict__ y, int64_t sy) {
   constexpr int HH = H3 * H3, HHH = H3 * H3 * H3;
   constexpr int ZO = H3 * H3 * T3;
   constexpr int PX = H3 * T3 * T3;
+  constexpr int NZO = ALLJ ? 12 : 4;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* s_in = reinterpret_cast<T*>(smem_raw);  // 3 * H3^3
-  T* s_zo = s_in + 3 * HHH;                  // 12 * ZO
-  T* s_px = s_zo + 12 * ZO;                  // 12 * PX
+  T* s_zo = s_in + 3 * HHH;                  // NZO * ZO
+  T* s_px = s_zo + NZO * ZO;                 // 12 * PX
   __shared__ T s_tab[3][4][4][5];
   const int tid = threadIdx.x;
   for (int i = tid; i < 3 * 4 * 4 * 5; i += U3_THREADS) (&s_tab[0][0][0][0])[i] = (&tb.q2[0][0][0][0])[i];
@@ -298,58 +200,76 @@ __global__ void __launch_bounds__(U3_THREADS, 2) k_apply_u3_col(Grid g, TabT<T> 
   const int64_t nn = g.nnode;
   const T* u = u_in + k * su;
   const int fm0 = face_mask(g, 0), fm1 = face_mask(g, 1), fm2 = face_mask(g, 2);
-  for (int i = tid; i < 3 * HHH; i += U3_THREADS) {
-    const int c = i / HHH;
-    const int rem = i - c * HHH;
-    const int lz = rem / HH, ly = (rem / H3) % H3, lx = rem % H3;
-    const int gx = X0 + lx - 2, gy = Y0 + ly - 2, gz = Z0 + lz - 2;
-    const int fm = c == 0 ? fm0 : (c == 1 ? fm1 : fm2);
+  // staging: several independent loads in flight per thread (the loads hit L2)
+  constexpr int NLD = (3 * HHH + U3_THREADS - 1) / U3_THREADS;
+  T vals[NLD];
+#pragma unroll
+  for (int s8 = 0; s8 < NLD; ++s8) {
+    const int i = tid + s8 * U3_THREADS;
     T v = 0;
-    if ((unsigned)gx < (unsigned)nx && (unsigned)gy < (unsigned)ny && (unsigned)gz < (unsigned)nz && free_fast(fm, gx, gy, gz, nx, ny, nz))
-      v = u[c * nn + ((int64_t)gz * ny + gy) * nx + gx];
-    s_in[i] = v;
+    if (i < 3 * HHH) {
+      const int c = i / HHH;
+      const int rem = i - c * HHH;
+      const int lz = rem / HH, ly = (rem / H3) % H3, lx = rem % H3;
+      const int gx = X0 + lx - 2, gy = Y0 + ly - 2, gz = Z0 + lz - 2;
+      const int fm = c == 0 ? fm0 : (c == 1 ? fm1 : fm2);
+      if ((unsigned)gx < (unsigned)nx && (unsigned)gy < (unsigned)ny && (unsigned)gz < (unsigned)nz &&
+          free_fast(fm, gx, gy, gz, nx, ny, nz))
+        v = __ldg(u + c * nn + ((int64_t)gz * ny + gy) * nx + gx);
+    }
+    vals[s8] = v;
+  }
+#pragma unroll
+  for (int s8 = 0; s8 < NLD; ++s8) {
+    const int i = tid + s8 * U3_THREADS;
+    if (i < 3 * HHH) s_in[i] = vals[s8];
   }
   __syncthreads();
-  // z pass: item = (component, y, x) line along z
-  for (int it = tid; it < 3 * HH; it += U3_THREADS) {
-    const int c = it / HH, rem = it - c * HH;
-    const T* src = s_in + c * HHH + rem;
-    T w[12];
+  constexpr int NJ = ALLJ ? 1 : 3;
+  for (int jj = 0; jj < NJ; ++jj) {
+    if (jj > 0) __syncthreads();
+    // z pass: item = (component, y, x) line along z
+    for (int it = tid; it < (ALLJ ? 3 : 1) * HH; it += U3_THREADS) {
+      const int c = ALLJ ? it / HH : jj, rem = ALLJ ? it - (it / HH) * HH : it;
+      const T* src = s_in + c * HHH + rem;
+      T w[12];
 #pragma unroll
-    for (int z = 0; z < 12; ++z) w[z] = src[z * HH];
-    T o8[8];
-    T* dst = s_zo + (c * 4) * ZO + rem;
-    col8<0>(s_tab[2], Z0, nz, w, o8);
+      for (int z = 0; z < 12; ++z) w[z] = src[z * HH];
+      T o8[8];
+      T* dst = s_zo + (ALLJ ? c * 4 : 0) * ZO + rem;
+      col8<0>(s_tab[2], Z0, nz, w, o8);
 #pragma unroll
-    for (int o = 0; o < 8; ++o) dst[o * HH] = o8[o];
-    col8<1>(s_tab[2], Z0, nz, w, o8);
+      for (int o = 0; o < 8; ++o) dst[o * HH] = o8[o];
+      col8<1>(s_tab[2], Z0, nz, w, o8);
 #pragma unroll
-    for (int o = 0; o < 8; ++o) dst[ZO + o * HH] = o8[o];
-    col8<2>(s_tab[2], Z0, nz, w, o8);
+      for (int o = 0; o < 8; ++o) dst[ZO + o * HH] = o8[o];
+      col8<2>(s_tab[2], Z0, nz, w, o8);
 #pragma unroll
-    for (int o = 0; o < 8; ++o) dst[2 * ZO + o * HH] = o8[o];
-    col8<3>(s_tab[2], Z0, nz, w, o8);
+      for (int o = 0; o < 8; ++o) dst[2 * ZO + o * HH] = o8[o];
+      col8<3>(s_tab[2], Z0, nz, w, o8);
 #pragma unroll
-    for (int o = 0; o < 8; ++o) dst[3 * ZO + o * HH] = o8[o];
-  }
-  __syncthreads();
-  // y pass: item = (pre-x target q = 4 i + xop, z, x) line along y
-  for (int it = tid; it < 12 * T3 * H3; it += U3_THREADS) {
-    const int q = it / (T3 * H3), rem = it - q * (T3 * H3);
-    const int lz = rem / H3, lx = rem - lz * H3;
-    switch (q) {
-      case 0: ypass_target<0>(s_zo, s_px, s_tab[1], Y0, ny, lz, lx, cf0, cf1, cf2); break;
-      case 1: ypass_target<1>(s_zo, s_px, s_tab[1], Y0, ny, lz, lx, cf0, cf1, cf2); break;
-      case 2: ypass_target<2>(s_zo, s_px, s_tab[1], Y0, ny, lz, lx, cf0, cf1, cf2); break;
-      case 3: ypass_target<3>(s_zo, s_px, s_tab[1], Y0, ny, lz, lx, cf0, cf1, cf2); break;
-      case 4: ypass_target<4>(s_zo, s_px, s_tab[1], Y0, ny, lz, lx, cf0, cf1, cf2); break;
-      case 5: ypass_target<5>(s_zo, s_px, s_tab[1], Y0, ny, lz, lx, cf0, cf1, cf2); break;
-      case 6: ypass_target<6>(s_zo, s_px, s_tab[1], Y0, ny, lz, lx, cf0, cf1, cf2); break;
-      case 7: ypass_target<7>(s_zo, s_px, s_tab[1], Y0, ny, lz, lx, cf0, cf1, cf2); break;
-      case 8: ypass_target<8>(s_zo, s_px, s_tab[1], Y0, ny, lz, lx, cf0, cf1, cf2); break;
-      case 9: ypass_target<9>(s_zo, s_px, s_tab[1], Y0, ny, lz, lx, cf0, cf1, cf2); break;
-      case 10: ypass_target<10>(s_zo, s_px, s_tab[1], Y0, ny, lz, lx, cf0, cf1, cf2); break;
-      default: ypass_target<11>(s_zo, s_px, s_tab[1], Y0, ny, lz, lx, cf0, cf1, cf2); break;
+      for (int o = 0; o < 8; ++o) dst[3 * ZO + o * HH] = o8[o];
+    }
+    __syncthreads();
+    // y pass: item = (pre-x target q = 4 i + xop, z, x) line along y
+    const int jo = ALLJ ? -1 : jj;
+    for (int it = tid; it < 12 * T3 * H3; it += U3_THREADS) {
+      const int q = it / (T3 * H3), rem = it - q * (T3 * H3);
+      const int lz = rem / H3, lx = rem - lz * H3;
+      switch (q) {
+        case 0: ypass_target<0>(s_zo, s_px, s_tab[1], Y0, ny, lz, lx, cf0, cf1, cf2, jo); break;
+        case 1: ypass_target<1>(s_zo, s_px, s_tab[1], Y0, ny, lz, lx, cf0, cf1, cf2, jo); break;
+        case 2: ypass_target<2>(s_zo, s_px, s_tab[1], Y0, ny, lz, lx, cf0, cf1, cf2, jo); break;
+        case 3: ypass_target<3>(s_zo, s_px, s_tab[1], Y0, ny, lz, lx, cf0, cf1, cf2, jo); break;
+        case 4: ypass_target<4>(s_zo, s_px, s_tab[1], Y0, ny, lz, lx, cf0, cf1, cf2, jo); break;
+        case 5: ypass_target<5>(s_zo, s_px, s_tab[1], Y0, ny, lz, lx, cf0, cf1, cf2, jo); break;
+        case 6: ypass_target<6>(s_zo, s_px, s_tab[1], Y0, ny, lz, lx, cf0, cf1, cf2, jo); break;
+        case 7: ypass_target<7>(s_zo, s_px, s_tab[1], Y0, ny, lz, lx, cf0, cf1, cf2, jo); break;
+        case 8: ypass_target<8>(s_zo, s_px, s_tab[1], Y0, ny, lz, lx, cf0, cf1, cf2, jo); break;
+        case 9: ypass_target<9>(s_zo, s_px, s_tab[1], Y0, ny, lz, lx, cf0, cf1, cf2, jo); break;
+        case 10: ypass_target<10>(s_zo, s_px, s_tab[1], Y0, ny, lz, lx, cf0, cf1, cf2, jo); break;
+        default: ypass_target<11>(s_zo, s_px, s_tab[1], Y0, ny, lz, lx, cf0, cf1, cf2, jo); break;
+      }
     }
   }
   __syncthreads();
@@ -669,15 +589,16 @@ void launch_apply_u(const Grid& g, const TabT<T>& tb, const SlabCoef& sc, const 
     constexpr bool ALLJ = sizeof(T) == 4;
     dim3 grid((g.nu[0] + T3 - 1) / T3, (g.nu[1] + T3 - 1) / T3, ((g.nu[2] + T3 - 1) / T3) * sc.nt);
     size_t smem = sizeof(T) * (3 * H3 * H3 * H3 + (ALLJ ? 12 : 4) * H3 * H3 * T3 + 12 * H3 * T3 * T3);
-    prof_begin(st, 0);
-    if (ALLJ) (note_launch(), k_apply_u3_col<T><<<grid, U3_THREADS, smem, st>>>(g, tb, sc, u, su, p, sp, y, sy));
-    else (note_launch(), k_apply_u3<T, false><<<grid, U3_THREADS, smem, st>>>(g, tb, sc, u, su, p, sp, y, sy));
-    prof_end(st, 0);
+    const int kind = sizeof(T) == 4 ? 0 : 1;
+    prof_begin(st, kind, (double)g.nnode * sc.nt);
+    (note_launch(), k_apply_u3_col<T, ALLJ><<<grid, U3_THREADS, smem, st>>>(g, tb, sc, u, su, p, sp, y, sy));
+    prof_end(st, kind);
   } else {
     dim3 grid((g.nu[0] + T2 - 1) / T2, (g.nu[1] + T2 - 1) / T2, 1);
-    prof_begin(st, 0);
+    const int kind = sizeof(T) == 4 ? 0 : 1;
+    prof_begin(st, kind, (double)g.nnode * sc.nt);
     (note_launch(), k_apply_u2<T><<<grid, 256, 0, st>>>(g, tb, sc, u, su, p, sp, y, sy));
-    prof_end(st, 0);
+    prof_end(st, kind);
   }
 }
 
@@ -709,12 +630,10 @@ void launch_diag_A(const Grid& g, const TabT<T>& tb, double lam, double mu, T* d
 void apply_init_attributes() {
   static bool done = false;
   if (done) return;
-  cudaFuncSetAttribute(k_apply_u3<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaFuncSetAttribute(k_apply_u3_col<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)(sizeof(float) * (3 * H3 * H3 * H3 + 12 * H3 * H3 * T3 + 12 * H3 * T3 * T3)));
+  cudaFuncSetAttribute(k_apply_u3_col<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)(sizeof(double) * (3 * H3 * H3 * H3 + 4 * H3 * H3 * T3 + 12 * H3 * T3 * T3)));
-  cudaFuncSetAttribute(k_apply_u3<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)(sizeof(float) * (3 * H3 * H3 * H3 + 12 * H3 * H3 * T3 + 12 * H3 * T3 * T3)));
-  cudaFuncSetAttribute(k_apply_u3_col<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)(sizeof(float) * (3 * H3 * H3 * H3 + 12 * H3 * H3 * T3 + 12 * H3 * T3 * T3)));
   done = true;
 }
 

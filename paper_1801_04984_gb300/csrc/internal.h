@@ -8,15 +8,18 @@
 namespace biot {
 
 // ---- tracing (prof.cu) ------------------------------------------------------
-constexpr int PROF_KINDS = 4;  // 0 displacement-row operator, 1 flux rows, 2 pressure rows, 3 Krylov vector kernels
+// 0 FP32 elasticity (displacement-row) operator, 1 FP64 elasticity operator, 2 FP32 Schur
+// Chebyshev step, 3 spare; units = the kernel's work units (node x right-hand side for the
+// elasticity operator, pressure point x right-hand side for the Schur step)
+constexpr int PROF_KINDS = 4;
 void note_launch();
 void note_launches(long long k);  // graph replays: add the kernels of the graph
 long long launch_count();
 void prof_enable(bool on);
 bool prof_enabled();
-void prof_begin(cudaStream_t st, int kind);
+void prof_begin(cudaStream_t st, int kind, double units);
 void prof_end(cudaStream_t st, int kind);
-void prof_collect(int kind, long long* n, double* ms);
+void prof_collect(int kind, long long* n, double* ms, double* units);
 
 // ---- slab operator pieces (apply.cu) --------------------------------------
 template <typename T>

@@ -963,8 +963,10 @@ void launch_schur_cheb(const Grid& g, const TabT<T>& tb, const T* dmq, const T* 
   RhsCoef rc;
   for (int r = 0; r < MAXR; ++r) rc.c[r] = (r < nrhs) ? cm[r] : 0.0;
   dim3 grid((unsigned)((g.Np + 255) / 256), nrhs);
+  if (sizeof(T) == 4) prof_begin(st, 2, (double)g.Np * nrhs);
   if (g.dim == 3) (note_launch(), k_schur_cheb<T, 3><<<grid, 256, 0, st>>>(g, tb, dmq, sb2, rc, T(tau), T(c1), T(c2), first, b, x, d, xo, nrhs));
   else (note_launch(), k_schur_cheb<T, 2><<<grid, 256, 0, st>>>(g, tb, dmq, sb2, rc, T(tau), T(c1), T(c2), first, b, x, d, xo, nrhs));
+  if (sizeof(T) == 4) prof_end(st, 2);
 }
 #define INSTMG(T)                                                                                                   \
   template void launch_prolong_add<T>(const Grid&, const Grid&, const T*, int64_t, T*, int64_t, int, cudaStream_t); \

@@ -14,6 +14,7 @@ static std::mutex g_mu;
 struct EvPair {
   cudaEvent_t a, b;
   int kind;
+  double units;
 };
 static std::vector<EvPair> g_open;   // recorded, not yet collected
 static std::vector<EvPair> g_free;   // reusable
@@ -25,7 +26,7 @@ long long launch_count() { return g_launches.load(); }
 void prof_enable(bool on) { g_prof.store(on); }
 bool prof_enabled() { return g_prof.load(); }
 
-void prof_begin(cudaStream_t st, int kind) {
+void prof_begin(cudaStream_t st, int kind, double units) {
   if (!g_prof.load()) return;
   std::lock_guard<std::mutex> lk(g_mu);
   EvPair e;
@@ -37,6 +38,7 @@ void prof_begin(cudaStream_t st, int kind) {
     cudaEventCreate(&e.b);
   }
   e.kind = kind;
+  e.units = units;
   cudaEventRecord(e.a, st);
   g_cur[kind] = e;
 }
@@ -50,10 +52,10 @@ void prof_end(cudaStream_t st, int kind) {
 }
 
 // sums the recorded launches of `kind` (synchronising on their events) and clears them
-void prof_collect(int kind, long long* n, double* ms) {
+void prof_collect(int kind, long long* n, double* ms, double* units) {
   std::lock_guard<std::mutex> lk(g_mu);
   long long cnt = 0;
-  double tot = 0;
+  double tot = 0, un = 0;
   std::vector<EvPair> keep;
   for (EvPair& e : g_open) {
     if (e.kind != kind) {
@@ -64,12 +66,14 @@ void prof_collect(int kind, long long* n, double* ms) {
     float t = 0;
     cudaEventElapsedTime(&t, e.a, e.b);
     tot += t;
+    un += e.units;
     ++cnt;
     g_free.push_back(e);
   }
   g_open.swap(keep);
   if (n) *n = cnt;
   if (ms) *ms = tot;
+  if (units) *units = un;
 }
 
 }  // namespace biot
