@@ -109,6 +109,9 @@ typedef struct {
   double beta_fs;       /* fixed-stress parameter; <= 0 selects b^2 / K_dr */
   int flux_mass_exact;  /* flux-pressure block: 0 (default) replaces the Darcy mass by its diagonal;
                            1 inverts it exactly by line solves */
+  int pair_coupling;    /* complex eigen-pair of the time matrix (r >= 1): 0 (default) applies one block
+                           Gauss-Seidel sweep with the +-beta S coupling; -1 drops the coupling (the
+                           paper's diagonal-blockwise L_j preconditioner) */
 } biot_opts;
 
 typedef struct {
@@ -184,6 +187,36 @@ int biot_march(biot_t ctx, double T, int slabs, int nterms, const double* const*
 int biot_adjoint_grad(biot_t ctx, double T, int slabs, int nterms, const double* const* f_terms, const double* tcoef,
                       const double* U0, const double* j_goal, const biot_solve_opts* opts, int recompute, double* J_out,
                       double* dJ_dlogK, void* stream);
+
+/* Batched marches: `count` independent instances, each with its own mesh,
+ * coefficients (K_cell on the host), time order r, horizon T and slab count, and
+ * either a built-in load (load_kind >= 0: one BIOT_LOAD_* preset of magnitude
+ * load_value, constant in time) or explicit load terms as in biot_march
+ * (load_kind = -1).  U0 / U_end (n_space each, host or device, may be NULL) are
+ * the instance's initial and end states.  The instances are solved on the
+ * current device by one host worker with its own stream and a cache of contexts
+ * keyed by everything except the permeability (instances of equal shape reuse the
+ * multigrid hierarchy and Krylov bases).  `workers` is accepted for a later
+ * concurrent mode and currently ignored.  status[i] and stats[i] (host arrays, may be NULL) receive each
+ * instance's return code and statistics; the call returns BIOT_OK or the first
+ * failing code.  (The paper solves one problem at a time; batching serves the
+ * many-instance studies its space-time method targets, e.g. parameter sweeps.) */
+typedef struct {
+  biot_mesh mesh;
+  biot_coeffs coeffs;
+  int r;
+  double T;
+  int slabs;
+  int load_kind;
+  double load_value;
+  int nterms;
+  const double* const* f_terms;
+  const double* tcoef;
+  const double* U0;
+  double* U_end;
+} biot_batch_item;
+int biot_solve_batch(const biot_batch_item* items, int count, const biot_opts* opts, const biot_solve_opts* sopts,
+                     int workers, int* status, biot_stats* stats);
 
 /* Goal weight vector of J = mean pressure over the box [lo, hi] (exact
  * integration of the DGQ1 pressure over the clipped cells), written to the

@@ -39,12 +39,18 @@ class Coeffs(C.Structure):
 
 class Opts(C.Structure):
     _fields_ = [("gmres_restart", C.c_int), ("cheb_degree", C.c_int), ("schur_degree", C.c_int),
-                ("mg_min_cells", C.c_int), ("beta_fs", C.c_double), ("flux_mass_exact", C.c_int)]
+                ("mg_min_cells", C.c_int), ("beta_fs", C.c_double), ("flux_mass_exact", C.c_int), ("pair_coupling", C.c_int)]
 
 
 class SolveOpts(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iters", C.c_int), ("mode", C.c_int), ("inner_tol", C.c_double),
                 ("transpose", C.c_int)]
+
+
+class BatchItem(C.Structure):
+    _fields_ = [("mesh", Mesh), ("coeffs", Coeffs), ("r", C.c_int), ("T", C.c_double), ("slabs", C.c_int),
+                ("load_kind", C.c_int), ("load_value", C.c_double), ("nterms", C.c_int),
+                ("f_terms", C.c_void_p), ("tcoef", C.c_void_p), ("U0", C.c_void_p), ("U_end", C.c_void_p)]
 
 
 class Stats(C.Structure):
@@ -84,6 +90,8 @@ def load(path: str = LIB_PATH):
         "biot_adjoint_grad": (C.c_int, [vp, C.c_double, C.c_int, C.c_int, C.POINTER(vp), dp, vp, vp,
                                         C.POINTER(SolveOpts), C.c_int, dp, vp, vp]),
         "biot_goal_mean_pressure": (C.c_int, [vp, dp, dp, vp, vp]),
+        "biot_solve_batch": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(Opts), C.POINTER(SolveOpts), C.c_int, ip,
+                                       C.c_void_p]),
         "biot_load_preset": (C.c_int, [vp, C.c_int, C.c_double, vp, vp]),
         "biot_apply_part": (C.c_int, [vp, C.c_int, C.c_double, vp, vp, C.c_int, vp]),
         "biot_schur_apply_noalloc": (C.c_int, [vp, C.c_double, vp, vp, vp]),
@@ -148,7 +156,7 @@ class Context:
         self.K = np.ascontiguousarray(np.asarray(coeffs["K"], dtype=np.float64))
         co = Coeffs(coeffs["b"], coeffs["invM"], coeffs["K_dr"], coeffs["lam"], coeffs["mu"], coeffs["eta"],
                     self.K.ctypes.data_as(C.POINTER(C.c_double)))
-        o = Opts(0, 0, 0, 0, -1.0, 0)
+        o = Opts(0, 0, 0, 0, -1.0, 0, 0)
         if opts:
             for k, v in opts.items():
                 setattr(o, k, v)
@@ -303,3 +311,52 @@ class Context:
         import torch
         return self._check(self.lib.biot_load_preset(self.h, int(kind), float(value),
                                                      _ptr(f, torch.float64, self.n_space, "f"), _stream()))
+
+
+def make_mesh(dim, n, u_bc, f_bc, lo=None, hi=None):
+    m = Mesh()
+    m.dim = dim
+    for d in range(3):
+        m.n[d] = int(n[d]) if d < dim else 1
+        m.lo[d] = float(lo[d]) if (lo is not None and d < dim) else 0.0
+        m.hi[d] = float(hi[d]) if (hi is not None and d < dim) else 1.0
+    for f in range(6):
+        m.u_bc[f] = int(u_bc[f]) if f < 2 * dim else 0
+        m.f_bc[f] = int(f_bc[f]) if f < 2 * dim else 0
+    return m
+
+
+def solve_batch(instances, workers=8, tol=1e-10, mode=MIXED, inner_tol=1e-5, max_iters=2000, opts=None):
+    """Batched marches (biot_solve_batch).  Each instance is a dict with dim, n, coeffs
+    (b, invM, K_dr, lam, mu, eta, K), r, T, slabs, u_bc, f_bc, load_kind, load_value and
+    U_end (a float64 numpy array of n_space that receives the end state).
+    Returns (rc, per-instance status list, per-instance stats dicts)."""
+    lib = load()
+    cnt = len(instances)
+    items = (BatchItem * cnt)()
+    keep = []
+    for i, ins in enumerate(instances):
+        it = items[i]
+        it.mesh = make_mesh(ins["dim"], ins["n"], ins["u_bc"], ins["f_bc"])
+        K = np.ascontiguousarray(np.asarray(ins["coeffs"]["K"], dtype=np.float64))
+        keep.append(K)
+        co = ins["coeffs"]
+        it.coeffs = Coeffs(co["b"], co["invM"], co["K_dr"], co["lam"], co["mu"], co["eta"],
+                           K.ctypes.data_as(C.POINTER(C.c_double)))
+        it.r, it.T, it.slabs = int(ins["r"]), float(ins["T"]), int(ins["slabs"])
+        it.load_kind, it.load_value, it.nterms = int(ins.get("load_kind", 0)), float(ins.get("load_value", 1.0)), 0
+        it.f_terms = None
+        it.tcoef = None
+        it.U0 = None
+        out = ins.get("U_end")
+        it.U_end = out.ctypes.data if out is not None else None
+    o = Opts(0, 0, 0, 0, -1.0, 0, 0)
+    if opts:
+        for k, v in opts.items():
+            setattr(o, k, v)
+    so = SolveOpts(tol, max_iters, mode, inner_tol, 0)
+    status = (C.c_int * cnt)()
+    stats = (Stats * cnt)()
+    rc = lib.biot_solve_batch(C.cast(items, C.c_void_p), cnt, C.byref(o), C.byref(so), int(workers), status,
+                              C.cast(stats, C.c_void_p))
+    return rc, list(status), [s.as_dict() for s in stats]

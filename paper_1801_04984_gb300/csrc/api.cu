@@ -86,6 +86,8 @@ struct TimeBasis {
   double nodes[MAXR], w[MAXR], D[MAXR][MAXR], phi0[MAXR];
   double V[MAXR][MAXR], W[MAXR][MAXR];  // M_t^{-1} D = V Lambda_R V^{-1};  W = V^{-1} M_t^{-1}
   double lam[MAXR];                      // real part of the eigenvalue owning each transformed component
+  int pair;                              // first transformed component of the complex pair (-1: none)
+  double pair_beta;                      // beta of the pair: block [[alpha, beta], [-beta, alpha]]
 };
 
 long double lagr(const long double* x, int n, int i, long double s) {
@@ -130,6 +132,7 @@ void invert_small(int n, const long double A[MAXR][MAXR], long double Ai[MAXR][M
 TimeBasis make_time_basis(int r) {
   TimeBasis tb;
   std::memset(&tb, 0, sizeof(tb));
+  tb.pair = -1;
   int nt = r + 1;
   tb.nt = nt;
   long double x[MAXR];
@@ -226,6 +229,8 @@ TimeBasis make_time_basis(int r) {
       // T (a + ib) = (alpha + i beta)(a + ib): V = [a, b] gives block [[alpha, beta], [-beta, alpha]]
       for (int a = 0; a < nt; ++a) { V[a][col] = v[a].real(); V[a][col + 1] = v[a].imag(); }
       tb.lam[col] = tb.lam[col + 1] = (double)lam.real();
+      tb.pair = col;
+      tb.pair_beta = (double)lam.imag();
       col += 2;
     }
   }
@@ -322,6 +327,9 @@ struct biot_ctx {
   double* a64 = nullptr;
   float* d32 = nullptr;
   float* r32 = nullptr;
+  double* m_f[8] = {nullptr};  // march buffers (load terms, state, rhs, slab solution)
+  const double** m_fdev = nullptr;
+  double *m_U = nullptr, *m_SU = nullptr, *m_rhs = nullptr, *m_X = nullptr;
   double* lvl64 = nullptr;     // one-level temporaries
   double* lvl64b = nullptr;
   std::vector<void*> extra;    // other allocations
@@ -703,31 +711,29 @@ double schur_lmax(biot_ctx& c, double tau, cudaStream_t st) {
 
 // p = Shat^{-1} g by Chebyshev-Jacobi (w.gp -> w.pp)
 template <typename T>
-void schur_solve(biot_ctx& c, double tau, cudaStream_t st) {
+void schur_solve(biot_ctx& c, double tau, cudaStream_t st, int k0, int nk) {
   PrecWork<T>& w = c.pw<T>();
   const Grid& g = c.g;
-  double cm[MAXR];
-  schur_cm(c, cm);
+  double cm_all[MAXR];
+  schur_cm(c, cm_all);
+  const double* cm = cm_all + k0;
   double lmax = schur_lmax(c, tau, st);
-  if (w.schur_tau != tau) {
-    launch_schur_dinv<T>(g, c.tab<T>(), c.sb2<T>(), cm, tau, w.pdinv, c.nt, st);
-    CKL();
-    w.schur_tau = tau;
-  }
   ChebCoef cc = cheb_coefs(c.opts.schur_degree, c.schur_lmin, 1.1 * lmax);
   if (c.lumped_flux) {
     for (int k = 0; k < cc.n; ++k) {
       launch_schur_cheb<T>(g, c.tab<T>(), c.dmq<T>(), c.sb2<T>(), cm, tau, cc.c1[k], cc.c2[k], k == 0 ? 1 : 0, w.gp, w.pp, w.pd,
-                           w.pxo, c.nt, st);
+                           w.pxo, nk, st);
       CKL();
       std::swap(w.pp, w.pxo);
     }
     return;
   }
+  launch_schur_dinv<T>(g, c.tab<T>(), c.sb2<T>(), cm, tau, w.pdinv, nk, st);
+  CKL();
   for (int k = 0; k < cc.n; ++k) {
     bool first = (k == 0);
-    if (!first) schur_apply<T>(c, tau, cm, w.pp, w.pAx, c.nt, st);
-    launch_cheb_update_r<T>(w.gp, w.pAx, w.pdinv, w.pd, w.pp, w.pxo, cc.c1[k], cc.c2[k], first ? 1 : 0, g.Np, c.nt, st);
+    if (!first) schur_apply<T>(c, tau, cm, w.pp, w.pAx, nk, st);
+    launch_cheb_update_r<T>(w.gp, w.pAx, w.pdinv, w.pd, w.pp, w.pxo, cc.c1[k], cc.c2[k], first ? 1 : 0, g.Np, nk, st);
     CKL();
     std::swap(w.pp, w.pxo);
   }
@@ -736,6 +742,30 @@ void schur_solve(biot_ctx& c, double tau, cudaStream_t st) {
 template <typename T>
 void copy2d(T* dst, int64_t dpitch, const T* src, int64_t spitch, int64_t width, int rows, cudaStream_t st) {
   CK(cudaMemcpy2DAsync(dst, dpitch * sizeof(T), src, spitch * sizeof(T), width * sizeof(T), rows, cudaMemcpyDeviceToDevice, st));
+}
+
+// Block-triangular solve of the transformed diagonal blocks for components k0 .. k0+nk-1
+// (w.tA -> w.tB): flux-pressure block first (lumped Schur, Chebyshev), then the
+// displacement by one V-cycle for tau A u = r_u + b tau E p.
+template <typename T>
+void block_solve(biot_ctx& c, double tau, int k0, int nk, cudaStream_t st) {
+  PrecWork<T>& w = c.pw<T>();
+  const Grid& g = c.g;
+  const int64_t N = g.N, Nu = g.Nu, Np = g.Np;
+  const int64_t nqt = g.nq[0] + g.nq[1] + g.nq[2];
+  LevelWork<T>& lw = lwork<T>(c.lv[0]);
+  T* tA = w.tA + (int64_t)k0 * N;
+  T* tB = w.tB + (int64_t)k0 * N;
+  flux_solve<T>(c, tau, tA + Nu, N, nullptr, 0.0, w.fq, nqt, nk, st);
+  launch_p_minus_Bq<T>(g, c.tab<T>(), tA + g.offp, N, w.fq, nqt, tau, w.gp, Np, nk, st);
+  CKL();
+  schur_solve<T>(c, tau, st, k0, nk);
+  flux_solve<T>(c, tau, tA + Nu, N, w.pp, tau, tB + Nu, N, nk, st);
+  copy2d<T>(tB + g.offp, N, w.pp, Np, Np, nk, st);
+  launch_u_rhs<T>(g, c.tab<T>(), tA, N, w.pp, Np, c.b * tau, lw.b, Nu, nk, st);
+  CKL();
+  vcycle<T>(c, tau, nk, st);
+  copy2d<T>(tB, N, lw.x, Nu, Nu, nk, st);
 }
 
 // z = P r  (or P^T r)
@@ -757,16 +787,23 @@ void precondition_T(biot_ctx& c, double tau, const T* R, T* Z, int transpose, cu
   launch_time_mix<T, T>(R, N, w.tA, N, nt, Wm, N, st);
   CKL();
   if (!transpose) {
-    flux_solve<T>(c, tau, w.tA + Nu, N, nullptr, 0.0, w.fq, nqt, nt, st);
-    launch_p_minus_Bq<T>(g, c.tab<T>(), w.tA + g.offp, N, w.fq, nqt, tau, w.gp, Np, nt, st);
-    CKL();
-    schur_solve<T>(c, tau, st);
-    flux_solve<T>(c, tau, w.tA + Nu, N, w.pp, tau, w.tB + Nu, N, nt, st);
-    copy2d<T>(w.tB + g.offp, N, w.pp, Np, Np, nt, st);
-    launch_u_rhs<T>(g, c.tab<T>(), w.tA, N, w.pp, Np, c.b * tau, lw.b, Nu, nt, st);
-    CKL();
-    vcycle<T>(c, tau, nt, st);
-    copy2d<T>(w.tB, N, lw.x, Nu, Nu, nt, st);
+    const int p0 = c.tb.pair;
+    if (c.opts.pair_coupling && p0 >= 0) {
+      // one block Gauss-Seidel sweep on the 2x2 real block of the complex pair
+      // [[L, beta S], [-beta S, L]]: y_p0 = L^{-1} r_p0, y_p0+1 = L^{-1} (r_p0+1 + beta S y_p0)
+      block_solve<T>(c, tau, 0, p0 + 1, st);
+      const double beta = c.tb.pair_beta;
+      T* r1 = w.tA + (int64_t)(p0 + 1) * N;
+      const T* y0 = w.tB + (int64_t)p0 * N;
+      launch_p_plus_ETu<T>(g, c.tab<T>(), r1 + g.offp, N, y0, N, beta * c.b, r1 + g.offp, N, 1, st);
+      double mp = 1.0;
+      for (int d = 0; d < g.dim; ++d) mp *= c.t64.wg[d];
+      launch_axpby<T>(r1 + g.offp, y0 + g.offp, beta * c.invM * mp, 1.0, Np, st);
+      CKL();
+      block_solve<T>(c, tau, p0 + 1, nt - p0 - 1, st);
+    } else {
+      block_solve<T>(c, tau, 0, nt, st);
+    }
   } else {
     copy2d<T>(lw.b, Nu, w.tA, N, Nu, nt, st);
     vcycle<T>(c, tau, nt, st);
@@ -776,7 +813,7 @@ void precondition_T(biot_ctx& c, double tau, const T* R, T* Z, int transpose, cu
     flux_solve<T>(c, tau, w.tA + Nu, N, nullptr, 0.0, w.fq, nqt, nt, st);
     launch_p_minus_Bq<T>(g, c.tab<T>(), w.gp, Np, w.fq, nqt, -tau, w.gp, Np, nt, st);
     CKL();
-    schur_solve<T>(c, tau, st);
+    schur_solve<T>(c, tau, st, 0, nt);
     flux_solve<T>(c, tau, w.tA + Nu, N, w.pp, -tau, w.tB + Nu, N, nt, st);
     copy2d<T>(w.tB + g.offp, N, w.pp, Np, Np, nt, st);
   }
@@ -1139,6 +1176,9 @@ void set_permeability(biot_ctx& c, const double* K, cudaStream_t st) {
   c.schur_lmax_tau = -1;
   c.p64.schur_tau = -1;
   c.p32.schur_tau = -1;
+  // captured Arnoldi steps carry the Chebyshev coefficients of the old Schur bounds
+  for (auto& kv : c.graphs) cudaGraphExecDestroy(kv.second.exec);
+  c.graphs.clear();
 }
 
 // ---- loads ---------------------------------------------------------------------------
@@ -1165,7 +1205,6 @@ void time_load_coefs(const biot_ctx& c, double t0, double tau, int nterms, const
 }
 
 struct MarchBufs {
-  std::vector<double*> f;
   const double** fdev = nullptr;
   double* U = nullptr;
   double* SU = nullptr;  // one level
@@ -1173,35 +1212,35 @@ struct MarchBufs {
   double* X = nullptr;
 };
 
+// The march buffers live in the context (allocated on first use, reused by every later
+// march, freed by biot_destroy), so repeated marches allocate nothing.
 void march_prepare(biot_ctx& c, int nterms, const double* const* f_terms, const double* U0, MarchBufs& mb, cudaStream_t st) {
   const Grid& g = c.g;
   if (nterms < 0 || nterms > 8) fail(BIOT_EINVAL, "nterms must be in 0..8");
-  for (int m = 0; m < nterms; ++m) {
-    double* d = dalloc<double>(g.N);
-    if (!f_terms[m]) fail(BIOT_EINVAL, "NULL load term");
-    CK(cudaMemcpyAsync(d, f_terms[m], g.N * sizeof(double), is_device_ptr(f_terms[m]) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
-    launch_mask<double>(g, d, g.N, 1, st);
-    CKL();
-    mb.f.push_back(d);
+  if (!c.m_U) {
+    for (int m = 0; m < 8; ++m) c.m_f[m] = dalloc<double>(g.N);
+    c.m_fdev = (const double**)dalloc<double*>(8);
+    CK(cudaMemcpy((void*)c.m_fdev, c.m_f, 8 * sizeof(double*), cudaMemcpyHostToDevice));
+    c.m_U = dalloc<double>(g.N);
+    c.m_SU = dalloc<double>(g.N);
+    c.m_rhs = dalloc<double>(g.N * c.nt);
+    c.m_X = dalloc<double>(g.N * c.nt);
   }
-  mb.fdev = (const double**)dalloc<double*>(std::max(1, nterms));
-  if (nterms) CK(cudaMemcpyAsync((void*)mb.fdev, mb.f.data(), nterms * sizeof(double*), cudaMemcpyHostToDevice, st));
-  mb.U = dalloc<double>(g.N);
+  for (int m = 0; m < nterms; ++m) {
+    if (!f_terms[m]) fail(BIOT_EINVAL, "NULL load term");
+    CK(cudaMemcpyAsync(c.m_f[m], f_terms[m], g.N * sizeof(double),
+                       is_device_ptr(f_terms[m]) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    launch_mask<double>(g, c.m_f[m], g.N, 1, st);
+    CKL();
+  }
+  mb.fdev = c.m_fdev;
+  mb.U = c.m_U;
+  mb.SU = c.m_SU;
+  mb.rhs = c.m_rhs;
+  mb.X = c.m_X;
   if (U0) CK(cudaMemcpyAsync(mb.U, U0, g.N * sizeof(double), is_device_ptr(U0) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
   else CK(cudaMemsetAsync(mb.U, 0, g.N * sizeof(double), st));
-  mb.SU = dalloc<double>(g.N);
-  mb.rhs = dalloc<double>(g.N * c.nt);
-  mb.X = dalloc<double>(g.N * c.nt);
   CK(cudaStreamSynchronize(st));
-}
-
-void march_free(MarchBufs& mb) {
-  for (double* p : mb.f) cudaFree(p);
-  cudaFree((void*)mb.fdev);
-  cudaFree(mb.U);
-  cudaFree(mb.SU);
-  cudaFree(mb.rhs);
-  cudaFree(mb.X);
 }
 
 // rhs of slab n from the loads and the jump term of the state mb.U
@@ -1248,7 +1287,6 @@ void march_impl(biot_ctx& c, double T, int slabs, int nterms, const double* cons
   if (ckpt) CK(cudaMemcpyAsync(ckpt + (int64_t)slabs * g.N, mb.U, g.N * sizeof(double), cudaMemcpyDeviceToDevice, st));
   if (U_end) CK(cudaMemcpyAsync(U_end, mb.U, g.N * sizeof(double), is_device_ptr(U_end) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
-  march_free(mb);
   tot.seconds = now_s() - t_start;
   st_out = tot;
 }
@@ -1329,6 +1367,7 @@ extern "C" int biot_setup(const biot_mesh* mesh, const biot_coeffs* co, int r, c
     d.mg_min_cells = 2;
     d.beta_fs = -1;
     d.flux_mass_exact = 0;
+    d.pair_coupling = 1;
     if (opts) {
       if (opts->gmres_restart > 0) d.gmres_restart = std::min(opts->gmres_restart, 60);
       if (opts->cheb_degree > 0) d.cheb_degree = std::min(opts->cheb_degree, 30);
@@ -1336,6 +1375,7 @@ extern "C" int biot_setup(const biot_mesh* mesh, const biot_coeffs* co, int r, c
       if (opts->mg_min_cells > 0) d.mg_min_cells = opts->mg_min_cells;
       d.beta_fs = opts->beta_fs;
       d.flux_mass_exact = opts->flux_mass_exact ? 1 : 0;
+      d.pair_coupling = opts->pair_coupling >= 0 ? 1 : 0;
     }
     c->opts = d;
     c->lumped_flux = d.flux_mass_exact ? 0 : 1;
@@ -1364,7 +1404,7 @@ extern "C" int biot_setup(const biot_mesh* mesh, const biot_coeffs* co, int r, c
     cudaStream_t st = 0;
     set_permeability(*c, co->K_cell, st);
     build_levels(*c, st);
-    CK(cudaDeviceSynchronize());
+    CK(cudaStreamSynchronize(st));
   } catch (const Err& e) {
     biot_destroy(c);
     return e.code;
@@ -1517,7 +1557,6 @@ extern "C" int biot_adjoint_grad(biot_t c, double T, int slabs, int nterms, cons
     }
   }
   CK(cudaStreamSynchronize(st));
-  march_free(mb);
   cudaFree(Z);
   cudaFree(zr);
   cudaFree(tmp);
@@ -1764,6 +1803,13 @@ bool ctx_view(biot_t c, CtxView* v) {
 void ctx_set_error(biot_t c, const char* msg) {
   if (c) c->err = msg ? msg : "";
 }
+// batched solves drive many contexts from several host threads: no stream capture there
+void ctx_disable_graphs(biot_t c) {
+  if (!c) return;
+  for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second.exec);
+  c->graphs.clear();
+  c->use_graphs = false;
+}
 }  // namespace biot
 
 extern "C" const char* biot_last_error(biot_t c) {
@@ -1797,5 +1843,7 @@ extern "C" void biot_destroy(biot_t c) {
   auto FP = [&](auto& w) { F(w.tA); F(w.tB); F(w.fq); F(w.tq); F(w.fq2); F(w.gp); F(w.pp); F(w.pd); F(w.pAx); F(w.pxo); F(w.pdinv); };
   FP(c->p64); FP(c->p32);
   for (void* p : c->extra) F(p);
+  for (int m = 0; m < 8; ++m) F(c->m_f[m]);
+  F((void*)c->m_fdev); F(c->m_U); F(c->m_SU); F(c->m_rhs); F(c->m_X);
   delete c;
 }

@@ -11,6 +11,8 @@
 //    Mp p and B q.
 // Every output DoF is computed by exactly one thread (gather form): no atomics,
 // bitwise reproducible.
+#include <mutex>
+
 #include "internal.h"
 
 namespace biot {
@@ -628,13 +630,13 @@ void launch_diag_A(const Grid& g, const TabT<T>& tb, double lam, double mu, T* d
 
 // opt-in shared memory sizes, set once per process before any launch (and so before any graph capture)
 void apply_init_attributes() {
-  static bool done = false;
-  if (done) return;
+  static std::once_flag once;
+  std::call_once(once, [] {
   cudaFuncSetAttribute(k_apply_u3_col<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)(sizeof(float) * (3 * H3 * H3 * H3 + 12 * H3 * H3 * T3 + 12 * H3 * T3 * T3)));
   cudaFuncSetAttribute(k_apply_u3_col<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)(sizeof(double) * (3 * H3 * H3 * H3 + 4 * H3 * H3 * T3 + 12 * H3 * T3 * T3)));
-  done = true;
+  });
 }
 
 #define INST(T)                                                                                                        \

@@ -52,8 +52,9 @@ def test_mixed_precision_matches_fp64(n, r):
 
 
 def test_march_mms_matches_oracle():
-    n, r = (8, 8), 1
-    K = np.full(64, 1e-2)
+    # the 2-D manufactured-solution workload: 16 x 16 quads, dG(1), T = 1 in 8 slabs, FP64
+    n, r = (16, 16), 1
+    K = np.full(256, 1e-2)
     ctx, prob = _setup(n, r, dirichlet_bcs(2), K, C1)
     m = prob.mesh
     ex = MMS2D(1.0, 1.0, 0.9, 0.1, 1.0, 1e-2)
