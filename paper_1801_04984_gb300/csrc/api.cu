@@ -277,6 +277,7 @@ struct PrecWork {
   T *tA = nullptr, *tB = nullptr;  // slab
   T *fq = nullptr, *tq = nullptr, *fq2 = nullptr;  // nt * Nq
   T *gp = nullptr, *pp = nullptr, *pd = nullptr, *pAx = nullptr, *pxo = nullptr, *pdinv = nullptr;  // nt * Np
+  T* scoef = nullptr;  // 16 * Np: lumped Schur stencil for schur_tau
   double schur_tau = -1.0;
 };
 
@@ -443,6 +444,7 @@ void ensure_prec(biot_ctx& c) {
   w.pAx = dalloc<T>(nt * g.Np);
   w.pxo = dalloc<T>(nt * g.Np);
   w.pdinv = dalloc<T>(nt * g.Np);
+  w.scoef = dalloc<T>(16 * g.Np);
   for (Level& L : c.lv) {
     LevelWork<T>& lw = lwork<T>(L);
     int64_t n = (int64_t)nt * L.g.Nu;
@@ -720,9 +722,16 @@ void schur_solve(biot_ctx& c, double tau, cudaStream_t st, int k0, int nk) {
   double lmax = schur_lmax(c, tau, st);
   ChebCoef cc = cheb_coefs(c.opts.schur_degree, c.schur_lmin, 1.1 * lmax);
   if (c.lumped_flux) {
+    if (w.schur_tau != tau) {  // stencil and diagonal of this tau (prec_prepare normally did this)
+      launch_schur_dinv<T>(g, c.tab<T>(), c.sb2<T>(), cm_all, tau, w.pdinv, c.nt, st);
+      launch_schur_stencil<T>(g, c.tab<T>(), c.dmq<T>(), tau, w.scoef, st);
+      CKL();
+      w.schur_tau = tau;
+    }
+    const T* dinv = w.pdinv + (int64_t)k0 * g.Np;
     for (int k = 0; k < cc.n; ++k) {
-      launch_schur_cheb<T>(g, c.tab<T>(), c.dmq<T>(), c.sb2<T>(), cm, tau, cc.c1[k], cc.c2[k], k == 0 ? 1 : 0, w.gp, w.pp, w.pd,
-                           w.pxo, nk, st);
+      launch_schur_cheb_st<T>(g, c.tab<T>(), w.scoef, dinv, cm, cc.c1[k], cc.c2[k], k == 0 ? 1 : 0, w.gp, w.pp, w.pd, w.pxo, nk,
+                              st);
       CKL();
       std::swap(w.pp, w.pxo);
     }
@@ -855,6 +864,7 @@ void prec_prepare(biot_ctx& c, double tau, cudaStream_t st) {
     double cm[MAXR];
     schur_cm(c, cm);
     launch_schur_dinv<T>(c.g, c.tab<T>(), c.sb2<T>(), cm, tau, w.pdinv, c.nt, st);
+    launch_schur_stencil<T>(c.g, c.tab<T>(), c.dmq<T>(), tau, w.scoef, st);
     CKL();
     w.schur_tau = tau;
   }
@@ -1840,7 +1850,7 @@ extern "C" void biot_destroy(biot_t c) {
   if (c->ev_in) cudaEventDestroy(c->ev_in);
   if (c->ev_out) cudaEventDestroy(c->ev_out);
   if (c->ws) cudaStreamDestroy(c->ws);
-  auto FP = [&](auto& w) { F(w.tA); F(w.tB); F(w.fq); F(w.tq); F(w.fq2); F(w.gp); F(w.pp); F(w.pd); F(w.pAx); F(w.pxo); F(w.pdinv); };
+  auto FP = [&](auto& w) { F(w.tA); F(w.tB); F(w.fq); F(w.tq); F(w.fq2); F(w.gp); F(w.pp); F(w.pd); F(w.pAx); F(w.pxo); F(w.pdinv); F(w.scoef); };
   FP(c->p64); FP(c->p32);
   for (void* p : c->extra) F(p);
   for (int m = 0; m < 8; ++m) F(c->m_f[m]);

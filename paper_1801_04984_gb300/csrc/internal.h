@@ -125,10 +125,13 @@ void launch_cheb_update_r(const T* b, const T* Ax, const T* dinv, T* d, const T*
                           int64_t n, int nrhs, cudaStream_t st);
 template <typename TX, typename TD>
 void launch_add_scaled(TX* x, const TD* d, double s, int64_t n, cudaStream_t st);
-// one fused Chebyshev-Jacobi step on the lumped flux-pressure Schur complement (pressure arrays, stride Np)
+// precomputed lumped flux-pressure Schur stencil (16 coefficients per pressure point) and one
+// fused Chebyshev-Jacobi step using it (pressure arrays, stride Np)
 template <typename T>
-void launch_schur_cheb(const Grid& g, const TabT<T>& tb, const T* dmq, const T* sb2, const double* cm, double tau, double c1,
-                       double c2, int first, const T* b, const T* x, T* d, T* xo, int nrhs, cudaStream_t st);
+void launch_schur_stencil(const Grid& g, const TabT<T>& tb, const T* dmq, double tau, T* coef, cudaStream_t st);
+template <typename T>
+void launch_schur_cheb_st(const Grid& g, const TabT<T>& tb, const T* coef, const T* dinv, const double* cm, double c1, double c2,
+                          int first, const T* b, const T* x, T* d, T* xo, int nrhs, cudaStream_t st);
 template <typename T>
 void launch_dinv_mul(const T* dinv, int64_t dstride, const T* r, T* z, int64_t n, int64_t stride, int nrhs, cudaStream_t st);
 // exact (s Mq)^{-1} by line solves (flux-block arrays); constrained entries untouched

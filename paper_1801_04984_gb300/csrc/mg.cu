@@ -888,84 +888,127 @@ template void launch_dinv_mul<double>(const double*, int64_t, const double*, dou
 template void launch_dinv_mul<float>(const float*, int64_t, const float*, float*, int64_t, int64_t, int, cudaStream_t);
 
 // ---------------------------------------------------------------------------
-// One Chebyshev-Jacobi step on the lumped flux-pressure Schur complement
-//   Shat_r = cm[r] Mp + tau B diag(Mq)^{-1} B^T,
-// applied as a direct stencil on the Gauss-point pressure grid: through the
-// flux DoFs on its Gauss line in direction c, a pressure point couples to the
-// pressure points of its own cell and of the neighbour cell across each face.
-// first: d = c2 Dinv b, xo = d;  else: d = c1 d + c2 Dinv (b - Shat x), xo = x + d.
+// Precomputed stencil of tau B diag(Mq)^{-1} B^T on the Gauss-point pressure grid:
+// per point 16 coefficients [self, partner along x, y, z, then for x, y, z the
+// two points of the lower and of the upper neighbour cell on the same line]
+// (structure of arrays, coef[k * Np + t]; 2-D packs the 11 slots self, x and y
+// partner, x lower and upper (2 each), y lower and upper (2 each) the same way).
+// One Chebyshev-Jacobi step then costs no division and little index arithmetic.
 template <typename T, int DIM>
-__global__ void __launch_bounds__(256) k_schur_cheb(Grid g, TabT<T> tb, const T* __restrict__ dmq, const T* __restrict__ sb2,
-                                                    RhsCoef cm, T tau, T c1, T c2, int first, const T* __restrict__ b,
-                                                    const T* __restrict__ x, T* __restrict__ d, T* __restrict__ xo, int nrhs) {
+__global__ void k_schur_stencil(Grid g, TabT<T> tb, const T* __restrict__ dmq, double tau, T* __restrict__ coef) {
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= g.Np) return;
-  const int r = blockIdx.y;
   const int64_t np = g.Np;
-  T mp = 1;
-  for (int k = 0; k < DIM; ++k) mp *= tb.wg[k];
-  const T dinv = T(1) / (T(cm.c[r]) * mp + tau * sb2[t]);
-  const int64_t i = r * np + t;
-  if (first) {
-    T dn = c2 * dinv * b[i];
-    d[i] = dn;
-    xo[i] = dn;
-    return;
-  }
   int co[3];
   co[0] = (int)(t % g.ng[0]);
   int64_t rr = t / g.ng[0];
   co[1] = (int)(rr % g.ng[1]);
   co[2] = (int)(rr / g.ng[1]);
-  const T* xr = x + r * np;
-  const int64_t pst[3] = {1, g.ng[0], (int64_t)g.ng[0] * g.ng[1]};
-  T acc = 0;
-#pragma unroll
+  double self = 0, part[3] = {0, 0, 0}, lo[3][2] = {{0, 0}, {0, 0}, {0, 0}}, hi[3][2] = {{0, 0}, {0, 0}, {0, 0}};
   for (int c = 0; c < DIM; ++c) {
     int sh[3];
     for (int k = 0; k < 3; ++k) sh[k] = (k < DIM) ? ((k == c) ? g.nu[k] : g.ng[k]) : 1;
-    T wt = 1;
+    double wt = 1;
     int64_t qbase = 0, mul = 1, stride_c = 1;
     for (int k = 0; k < 3; ++k) {
       if (k == c) stride_c = mul;
-      else { qbase += co[k] * mul; if (k < DIM) wt *= tb.wg[k]; }
+      else { qbase += co[k] * mul; if (k < DIM) wt *= (double)tb.wg[k]; }
       mul *= sh[k];
     }
     qbase += g.offq[c] - g.Nu;
     const int cell = co[c] >> 1, gq = co[c] & 1;
-    const int64_t pline = t - (int64_t)co[c] * pst[c];  // pressure index of along-c coordinate 0 on this line
-    T sc = 0;
-#pragma unroll
     for (int a = 0; a < 3; ++a) {
       const int ia = 2 * cell + a;
       if (!q_free(g, c, ia)) continue;
-      // (B^T x) at this flux DoF: the cells sharing it along c
-      T btp = 0;
-#pragma unroll
-      for (int k = 0; k < 2; ++k) btp += tb.bd[c][a][k] * xr[pline + (int64_t)(2 * cell + k) * pst[c]];
+      const double w = tau * wt * wt * (double)tb.bd[c][a][gq] / (double)dmq[qbase + (int64_t)ia * stride_c];
+      // this flux DoF touches the own cell's two points (local a) ...
+      for (int k = 0; k < 2; ++k) {
+        const double v = w * (double)tb.bd[c][a][k];
+        if (k == gq) self += v;
+        else part[c] += v;
+      }
+      // ... and, on a face, the neighbour cell's two points (local 2 - a)
       if (a == 0 && cell >= 1)
-        for (int k = 0; k < 2; ++k) btp += tb.bd[c][2][k] * xr[pline + (int64_t)(2 * cell - 2 + k) * pst[c]];
+        for (int k = 0; k < 2; ++k) lo[c][k] += w * (double)tb.bd[c][2][k];
       if (a == 2 && cell + 1 < g.n[c])
-        for (int k = 0; k < 2; ++k) btp += tb.bd[c][0][k] * xr[pline + (int64_t)(2 * cell + 2 + k) * pst[c]];
-      sc += tb.bd[c][a][gq] * btp / dmq[qbase + (int64_t)ia * stride_c];
+        for (int k = 0; k < 2; ++k) hi[c][k] += w * (double)tb.bd[c][0][k];
     }
-    acc += wt * wt * sc;
   }
-  T sx = T(cm.c[r]) * mp * xr[t] + tau * acc;
-  T dn = c2 * dinv * (b[i] - sx);
+  coef[t] = (T)self;
+  for (int c = 0; c < DIM; ++c) coef[(1 + c) * np + t] = (T)part[c];
+  for (int c = 0; c < DIM; ++c)
+    for (int k = 0; k < 2; ++k) {
+      coef[(1 + DIM + 4 * c + k) * np + t] = (T)lo[c][k];
+      coef[(1 + DIM + 4 * c + 2 + k) * np + t] = (T)hi[c][k];
+    }
+}
+
+// Chebyshev-Jacobi step on Shat_r = cm[r] Mp + tau B diag(Mq)^{-1} B^T with the
+// precomputed stencil; dinv per rhs (stride Np).
+template <typename T, int DIM>
+__global__ void __launch_bounds__(256) k_schur_cheb_st(Grid g, const T* __restrict__ coef, const T* __restrict__ dinv, RhsCoef cm,
+                                                       T mp, T c1, T c2, int first, const T* __restrict__ b,
+                                                       const T* __restrict__ x, T* __restrict__ d, T* __restrict__ xo) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= g.Np) return;
+  const int r = blockIdx.y;
+  const int64_t np = g.Np;
+  const int64_t i = r * np + t;
+  const T di = dinv[i];
+  if (first) {
+    const T dn = c2 * di * b[i];
+    d[i] = dn;
+    xo[i] = dn;
+    return;
+  }
+  const int ng0 = g.ng[0], ng1 = g.ng[1];
+  const int c0 = (int)(t % ng0);
+  const int64_t rr = t / ng0;
+  const int c1i = (int)(rr % ng1);
+  const int c2i = (int)(rr / ng1);
+  const int co[3] = {c0, c1i, c2i};
+  const int64_t pst[3] = {1, ng0, (int64_t)ng0 * ng1};
+  const T* xr = x + r * np;
+  const T xs = xr[t];
+  T acc = (T(cm.c[r]) * mp + coef[t]) * xs;
+#pragma unroll
+  for (int c = 0; c < DIM; ++c) {
+    const int cc = co[c];
+    const int64_t base = t - (int64_t)cc * pst[c];  // along-c coordinate 0 of this line
+    acc += coef[(1 + c) * np + t] * xr[base + (int64_t)(cc ^ 1) * pst[c]];
+    const int e2 = cc & ~1;  // 2 * cell
+    if (e2 >= 2) {
+      acc += coef[(1 + DIM + 4 * c) * np + t] * xr[base + (int64_t)(e2 - 2) * pst[c]];
+      acc += coef[(1 + DIM + 4 * c + 1) * np + t] * xr[base + (int64_t)(e2 - 1) * pst[c]];
+    }
+    if (e2 + 2 < g.ng[c]) {
+      acc += coef[(1 + DIM + 4 * c + 2) * np + t] * xr[base + (int64_t)(e2 + 2) * pst[c]];
+      acc += coef[(1 + DIM + 4 * c + 3) * np + t] * xr[base + (int64_t)(e2 + 3) * pst[c]];
+    }
+  }
+  T dn = c2 * di * (b[i] - acc);
   if (c1 != T(0)) dn += c1 * d[i];
   d[i] = dn;
-  xo[i] = xr[t] + dn;
+  xo[i] = xs + dn;
+}
+
+template <typename T>
+void launch_schur_stencil(const Grid& g, const TabT<T>& tb, const T* dmq, double tau, T* coef, cudaStream_t st) {
+  int blocks = (int)((g.Np + 255) / 256);
+  if (g.dim == 3) (note_launch(), k_schur_stencil<T, 3><<<blocks, 256, 0, st>>>(g, tb, dmq, tau, coef));
+  else (note_launch(), k_schur_stencil<T, 2><<<blocks, 256, 0, st>>>(g, tb, dmq, tau, coef));
 }
 template <typename T>
-void launch_schur_cheb(const Grid& g, const TabT<T>& tb, const T* dmq, const T* sb2, const double* cm, double tau, double c1,
-                       double c2, int first, const T* b, const T* x, T* d, T* xo, int nrhs, cudaStream_t st) {
+void launch_schur_cheb_st(const Grid& g, const TabT<T>& tb, const T* coef, const T* dinv, const double* cm, double c1, double c2,
+                          int first, const T* b, const T* x, T* d, T* xo, int nrhs, cudaStream_t st) {
   RhsCoef rc;
   for (int r = 0; r < MAXR; ++r) rc.c[r] = (r < nrhs) ? cm[r] : 0.0;
+  double mp = 1.0;
+  for (int k = 0; k < g.dim; ++k) mp *= (double)tb.wg[k];
   dim3 grid((unsigned)((g.Np + 255) / 256), nrhs);
   if (sizeof(T) == 4) prof_begin(st, 2, (double)g.Np * nrhs);
-  if (g.dim == 3) (note_launch(), k_schur_cheb<T, 3><<<grid, 256, 0, st>>>(g, tb, dmq, sb2, rc, T(tau), T(c1), T(c2), first, b, x, d, xo, nrhs));
-  else (note_launch(), k_schur_cheb<T, 2><<<grid, 256, 0, st>>>(g, tb, dmq, sb2, rc, T(tau), T(c1), T(c2), first, b, x, d, xo, nrhs));
+  if (g.dim == 3) (note_launch(), k_schur_cheb_st<T, 3><<<grid, 256, 0, st>>>(g, coef, dinv, rc, T(mp), T(c1), T(c2), first, b, x, d, xo));
+  else (note_launch(), k_schur_cheb_st<T, 2><<<grid, 256, 0, st>>>(g, coef, dinv, rc, T(mp), T(c1), T(c2), first, b, x, d, xo));
   if (sizeof(T) == 4) prof_end(st, 2);
 }
 #define INSTMG(T)                                                                                                   \
@@ -988,8 +1031,9 @@ void launch_schur_cheb(const Grid& g, const TabT<T>& tb, const T* dmq, const T* 
                                      int64_t, int, cudaStream_t);                                                   \
   template void launch_mask<T>(const Grid&, T*, int64_t, int, cudaStream_t);                                        \
   template void launch_mask_u<T>(const Grid&, T*, int64_t, int, cudaStream_t);                                      \
-  template void launch_schur_cheb<T>(const Grid&, const TabT<T>&, const T*, const T*, const double*, double, double, \
-                                     double, int, const T*, const T*, T*, T*, int, cudaStream_t);                  \
+  template void launch_schur_stencil<T>(const Grid&, const TabT<T>&, const T*, double, T*, cudaStream_t);          \
+  template void launch_schur_cheb_st<T>(const Grid&, const TabT<T>&, const T*, const T*, const double*, double, double, \
+                                        int, const T*, const T*, T*, T*, int, cudaStream_t);                        \
   template void launch_mq_line_solve<T>(const Grid&, const TabT<T>&, const T*, const T*, int64_t, T*, int64_t, double, int, \
                                         cudaStream_t);                                                              \
   template void launch_BTp<T>(const Grid&, const TabT<T>&, const T*, int64_t, const T*, int64_t, T*, int64_t, double, \
