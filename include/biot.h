@@ -103,8 +103,8 @@ typedef struct {
 
 typedef struct {
   int gmres_restart;    /* m (default 30) */
-  int cheb_degree;      /* Chebyshev degree of the elasticity smoother (default 3) */
-  int schur_degree;     /* Chebyshev degree of the flux-pressure Schur solve (default 32) */
+  int cheb_degree;      /* Chebyshev degree of the elasticity smoother (default 3, at most 128) */
+  int schur_degree;     /* Chebyshev degree of the flux-pressure Schur solve (default 32, at most 128) */
   int mg_min_cells;     /* stop coarsening at this many cells per direction (default 2) */
   double beta_fs;       /* fixed-stress parameter; <= 0 selects b^2 / K_dr */
   int flux_mass_exact;  /* flux-pressure block: 0 (default) replaces the Darcy mass by its diagonal;

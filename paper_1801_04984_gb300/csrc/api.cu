@@ -580,9 +580,10 @@ double lanczos_lmax(biot_ctx& c, OpF op, const double* dinv, int64_t dstride, in
 }
 
 // ---- Chebyshev smoothing -----------------------------------------------------
+constexpr int MAX_CHEB = 128;
 struct ChebCoef {
   int n;
-  double c1[32], c2[32];
+  double c1[MAX_CHEB], c2[MAX_CHEB];
 };
 ChebCoef cheb_coefs(int degree, double lmin, double lmax) {
   ChebCoef cc;
@@ -591,7 +592,7 @@ ChebCoef cheb_coefs(int degree, double lmin, double lmax) {
   double rho_old = 1.0 / sigma;
   cc.c1[0] = 0.0;
   cc.c2[0] = 1.0 / theta;
-  for (int k = 1; k < degree && k < 32; ++k) {
+  for (int k = 1; k < degree && k < MAX_CHEB; ++k) {
     double rho = 1.0 / (2.0 * sigma - rho_old);
     cc.c1[k] = rho * rho_old;
     cc.c2[k] = 2.0 * rho / delta;
@@ -1380,8 +1381,8 @@ extern "C" int biot_setup(const biot_mesh* mesh, const biot_coeffs* co, int r, c
     d.pair_coupling = 1;
     if (opts) {
       if (opts->gmres_restart > 0) d.gmres_restart = std::min(opts->gmres_restart, 60);
-      if (opts->cheb_degree > 0) d.cheb_degree = std::min(opts->cheb_degree, 30);
-      if (opts->schur_degree > 0) d.schur_degree = std::min(opts->schur_degree, 30);
+      if (opts->cheb_degree > 0) d.cheb_degree = std::min(opts->cheb_degree, MAX_CHEB);
+      if (opts->schur_degree > 0) d.schur_degree = std::min(opts->schur_degree, MAX_CHEB);
       if (opts->mg_min_cells > 0) d.mg_min_cells = opts->mg_min_cells;
       d.beta_fs = opts->beta_fs;
       d.flux_mass_exact = opts->flux_mass_exact ? 1 : 0;

@@ -4,8 +4,8 @@
 //  * apply_u : displacement rows.  The elasticity block is applied by global sum
 //    factorisation: A = sum of 21 (3-D) / 8 (2-D) Kronecker products of banded
 //    1-D Q2 matrices, evaluated tile by tile in shared memory in three passes
-//    (z, then y, then x).  The E p coupling is gathered from the neighbouring
-//    cells' Gauss-point pressures.
+//    (z, then y, then x).  The E p coupling is added by a second per-node
+//    kernel, sum-factorised over the node's block of Gauss-point pressures.
 //  * apply_q : flux rows, Darcy mass with the cellwise eta/K_c and B^T p.
 //  * apply_p : pressure rows, E^T u (storage of the volumetric strain),
 //    Mp p and B q.
@@ -51,51 +51,7 @@ __device__ inline T tap5(const T* c, const T* v, int stride) {
   return c[0] * v[0] + c[1] * v[stride] + c[2] * v[2 * stride] + c[3] * v[3 * stride] + c[4] * v[4 * stride];
 }
 
-// E p gathered at Q2 node (ix,iy,iz), component c, for one pressure level.
-template <typename T, int DIM>
-__device__ inline T gather_Ep(const Grid& g, const TabT<T>& tb, const T* __restrict__ p, int c, int ix, int iy, int iz) {
-  int idx[3] = {ix, iy, iz};
-  int pi[3][4];
-  T pc[3][4];
-  int cnt[3];
-  for (int d = 0; d < 3; ++d) {
-    int k = 0;
-    if (d < DIM) {
-      int m = idx[d];
-      const T(*tab)[2] = (d == c) ? tb.bd[d] : tb.bv[d];
-      if (m & 1) {
-        int j = m >> 1;
-        for (int q = 0; q < 2; ++q) { pi[d][k] = 2 * j + q; pc[d][k] = tab[1][q]; ++k; }
-      } else {
-        int j = m >> 1;
-        if (j >= 1) for (int q = 0; q < 2; ++q) { pi[d][k] = 2 * (j - 1) + q; pc[d][k] = tab[2][q]; ++k; }
-        if (j < g.n[d]) for (int q = 0; q < 2; ++q) { pi[d][k] = 2 * j + q; pc[d][k] = tab[0][q]; ++k; }
-      }
-    } else {
-      pi[d][0] = 0; pc[d][0] = T(1); k = 1;
-    }
-    cnt[d] = k;
-  }
-  T acc = 0;
-  for (int a = 0; a < cnt[2]; ++a)
-    for (int b = 0; b < cnt[1]; ++b) {
-      T cab = pc[2][a] * pc[1][b];
-      const T* row = p + ((int64_t)pi[2][a] * g.ng[1] + pi[1][b]) * g.ng[0];
-      T s = 0;
-      for (int e = 0; e < cnt[0]; ++e) s += pc[0][e] * row[pi[0][e]];
-      acc += cab * s;
-    }
-  return acc;
-}
-
 // ---------------------------------------------------------------------------
-// 3-D displacement rows.  grid: (tiles_x, tiles_y, tiles_z * nt); 256 threads;
-// one block = one 8^3-node output tile of one temporal level k.
-// u_in: nt levels of [u_0|u_1|u_2] at stride su; p_in (may be null): nt levels at stride sp;
-// y: nt levels at stride sy.  Y_k = au[k] A u_k + E(sum_l ep[k][l] p_l) on free rows, u_k on constrained rows.
-// ALLJ: the z pass runs for all three input components at once (3 barriers per
-// tile; needs 12 z-pass arrays in shared memory, used for FP32), otherwise
-// component by component (4 arrays, used for FP64 where shared memory is 2x).
 // bit (2*dir + side) set when that face constrains component c
 __device__ inline int face_mask(const Grid& g, int c) {
   int m = 0;
@@ -110,13 +66,121 @@ __device__ __forceinline__ bool free_fast(int m, int gx, int gy, int gz, int nx,
            ((m & 16) && gz == 0) || ((m & 32) && gz == nz - 1));
 }
 
+// 1-D taps of the E coupling along direction d for Q2 node index m: the Gauss-point
+// pressures of the (up to two) cells sharing the node, starting at pressure index
+// s0; cv: value weights (bv), cd: derivative weights (bd).  Missing cells get zero
+// weights and an in-range index.
+template <typename T>
+__device__ __forceinline__ void ep_taps(const TabT<T>& tb, int d, int m, int ncell, int& s0, T (&cv)[4], T (&cd)[4]) {
+  const int j = m >> 1;
+  if (m & 1) {  // mid node: own cell only, local node 1
+    s0 = 2 * j;
+    cv[0] = tb.bv[d][1][0]; cv[1] = tb.bv[d][1][1]; cv[2] = T(0); cv[3] = T(0);
+    cd[0] = tb.bd[d][1][0]; cd[1] = tb.bd[d][1][1]; cd[2] = T(0); cd[3] = T(0);
+  } else {      // vertex: cell j-1 (local node 2) in the first slots if it exists, then cell j (local node 0)
+    const bool lo = j >= 1, hi = j < ncell;
+    s0 = lo ? 2 * j - 2 : 0;
+    cv[0] = lo ? tb.bv[d][2][0] : (hi ? tb.bv[d][0][0] : T(0));
+    cv[1] = lo ? tb.bv[d][2][1] : (hi ? tb.bv[d][0][1] : T(0));
+    cv[2] = (lo && hi) ? tb.bv[d][0][0] : T(0);
+    cv[3] = (lo && hi) ? tb.bv[d][0][1] : T(0);
+    cd[0] = lo ? tb.bd[d][2][0] : (hi ? tb.bd[d][0][0] : T(0));
+    cd[1] = lo ? tb.bd[d][2][1] : (hi ? tb.bd[d][0][1] : T(0));
+    cd[2] = (lo && hi) ? tb.bd[d][0][0] : T(0);
+    cd[3] = (lo && hi) ? tb.bd[d][0][1] : T(0);
+  }
+}
+
+// Y_k += E (sum_l ep[k][l] p_l) on the free displacement rows (§Monolithic
+// Approach: the -b E p block of A_s and its time mixing), one thread per Q2 node
+// for all components and temporal levels.  E_c is the tensor product over the
+// directions of the derivative taps (direction c) and the value taps (the others),
+// evaluated by sum factorisation over the node's 4^d block of Gauss-point pressures.
+template <typename T, int DIM>
+__global__ void __launch_bounds__(256) k_add_Ep(Grid g, TabT<T> tb, SlabCoef sc, const T* __restrict__ p_in, int64_t sp,
+                                                T* __restrict__ y, int64_t sy) {
+  const int64_t node = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (node >= g.nnode) return;
+  const int ix = (int)(node % g.nu[0]);
+  const int64_t rr = node / g.nu[0];
+  const int iy = (int)(rr % g.nu[1]);
+  const int iz = DIM == 3 ? (int)(rr / g.nu[1]) : 0;
+  int sx, sy0, sz = 0;
+  T vx[4], dx[4], vy[4], dy[4], vz[4], dz[4];
+  ep_taps<T>(tb, 0, ix, g.n[0], sx, vx, dx);
+  ep_taps<T>(tb, 1, iy, g.n[1], sy0, vy, dy);
+  if (DIM == 3) ep_taps<T>(tb, 2, iz, g.n[2], sz, vz, dz);
+  // 4-wide windows; taps past the end of the pressure grid carry zero weight and
+  // read a clamped (in-range) index
+  int ox[4], oy[4], oz[4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    ox[e] = min(sx + e, g.ng[0] - 1);
+    oy[e] = min(sy0 + e, g.ng[1] - 1);
+    oz[e] = DIM == 3 ? min(sz + e, g.ng[2] - 1) : 0;
+  }
+  constexpr int NZ = DIM == 3 ? 4 : 1;
+  T ec[MAXR][DIM];
+#pragma unroll
+  for (int l = 0; l < MAXR; ++l) {
+    if (l < sc.nt) {
+      const T* p = p_in + l * sp;
+      T a0 = 0, a1 = 0, a2 = 0;
+#pragma unroll
+      for (int c2 = 0; c2 < NZ; ++c2) {
+        T b0 = 0, b1 = 0, b2 = 0;  // y-contracted partial sums for the three components
+#pragma unroll
+        for (int c1 = 0; c1 < 4; ++c1) {
+          const T* row = p + ((int64_t)oz[c2] * g.ng[1] + oy[c1]) * g.ng[0];
+          T sv = 0, sd = 0;
+#pragma unroll
+          for (int c0 = 0; c0 < 4; ++c0) {
+            const T pv = __ldg(row + ox[c0]);
+            sv += vx[c0] * pv;
+            sd += dx[c0] * pv;
+          }
+          b0 += vy[c1] * sd;  // comp 0: derivative in x
+          b1 += dy[c1] * sv;  // comp 1: derivative in y
+          b2 += vy[c1] * sv;  // comp 2: values in x and y
+        }
+        if (DIM == 3) {
+          a0 += vz[c2] * b0;
+          a1 += vz[c2] * b1;
+          a2 += dz[c2] * b2;  // comp 2: derivative in z
+        } else {
+          a0 += b0;
+          a1 += b1;
+        }
+      }
+      ec[l][0] = a0;
+      ec[l][1] = a1;
+      if (DIM == 3) ec[l][DIM - 1] = a2;
+    }
+  }
+  const int64_t nn = g.nnode;
+#pragma unroll
+  for (int c = 0; c < DIM; ++c) {
+    if (!free_fast(face_mask(g, c), ix, iy, iz, g.nu[0], g.nu[1], g.nu[2])) continue;
+#pragma unroll
+    for (int k = 0; k < MAXR; ++k) {
+      if (k >= sc.nt) continue;
+      T s = 0;
+#pragma unroll
+      for (int l = 0; l < MAXR; ++l)
+        if (l < sc.nt) s += T(sc.ep[k][l]) * ec[l][c];
+      y[k * sy + c * nn + node] += s;
+    }
+  }
+}
+
 constexpr int U3_THREADS = 384;
 
 // ---------------------------------------------------------------------------
 // 3-D displacement rows.  grid: (tiles_x, tiles_y, tiles_z * nt); one block =
 // one 8^3-node output tile of one temporal level k, staged with a 2-node halo
 // (12^3) in shared memory; z, y, x passes of the 21 Kronecker terms.
-// Y_k = au[k] A u_k + E(sum_l ep[k][l] p_l) on free rows, u_k on constrained rows.
+// Y_k = au[k] A u_k on free rows, u_k on constrained rows (u_in: nt levels of
+// [u_0|u_1|u_2] at stride su, y at stride sy; the E p term is added by k_add_Ep).
 // Column form: every work item owns a whole line of the tile in registers: a z pass item loads its 12 staged values once and produces the
 // 8 outputs of all 4 operators; a y pass item owns one pre-x target (output
 // component i, x operator) along y; an x pass item owns one output component
@@ -181,7 +245,6 @@ __device__ __forceinline__ void ypass_target(const T* __restrict__ s_zo, T* __re
 template <typename T, bool ALLJ>
 __global__ void __launch_bounds__(U3_THREADS, ALLJ ? 2 : 1) k_apply_u3_col(Grid g, TabT<T> tb, SlabCoef sc,
                                                                             const T* __restrict__ u_in, int64_t su,
-                                                                            const T* __restrict__ p_in, int64_t sp,
                                                                             T* __restrict__ y, int64_t sy) {
   constexpr int HH = H3 * H3, HHH = H3 * H3 * H3;
   constexpr int ZO = H3 * H3 * T3;
@@ -311,12 +374,6 @@ __global__ void __launch_bounds__(U3_THREADS, ALLJ ? 2 : 1) k_apply_u3_col(Grid 
       T out;
       if (free_fast(fm, gx, gy, gz, nx, ny, nz)) {
         out = au * acc[o];
-        if (p_in) {
-          for (int l = 0; l < sc.nt; ++l) {
-            T e = T(sc.ep[k][l]);
-            if (e != T(0)) out += e * gather_Ep<T, 3>(g, tb, p_in + l * sp, c, gx, gy, gz);
-          }
-        }
       } else {
         out = u[c * nn + node];
       }
@@ -328,7 +385,7 @@ __global__ void __launch_bounds__(U3_THREADS, ALLJ ? 2 : 1) k_apply_u3_col(Grid 
 // 2-D displacement rows: tiles of 16x16 nodes, passes y then x.
 template <typename T>
 __global__ void __launch_bounds__(256) k_apply_u2(Grid g, TabT<T> tb, SlabCoef sc, const T* __restrict__ u_in, int64_t su,
-                                                  const T* __restrict__ p_in, int64_t sp, T* __restrict__ y, int64_t sy) {
+                                                  T* __restrict__ y, int64_t sy) {
   __shared__ T s_in[2][H2 * H2];
   __shared__ T s_px[8][T2 * H2];
   __shared__ T s_tab[2][4][4][5];
@@ -383,12 +440,6 @@ __global__ void __launch_bounds__(256) k_apply_u2(Grid g, TabT<T> tb, SlabCoef s
 #pragma unroll
           for (int op = 0; op < 4; ++op) acc += tap5(s_tab[0][op][rt], &s_px[c * 4 + op][ly * H2 + lx], 1);
           out = T(sc.au[k]) * acc;
-          if (p_in) {
-            for (int l = 0; l < sc.nt; ++l) {
-              T e = T(sc.ep[k][l]);
-              if (e != T(0)) out += e * gather_Ep<T, 2>(g, tb, p_in + l * sp, c, gx, gy, 0);
-            }
-          }
         } else {
           out = u_in[k * su + c * nn + node];
         }
@@ -593,14 +644,24 @@ void launch_apply_u(const Grid& g, const TabT<T>& tb, const SlabCoef& sc, const 
     size_t smem = sizeof(T) * (3 * H3 * H3 * H3 + (ALLJ ? 12 : 4) * H3 * H3 * T3 + 12 * H3 * T3 * T3);
     const int kind = sizeof(T) == 4 ? 0 : 1;
     prof_begin(st, kind, (double)g.nnode * sc.nt);
-    (note_launch(), k_apply_u3_col<T, ALLJ><<<grid, U3_THREADS, smem, st>>>(g, tb, sc, u, su, p, sp, y, sy));
+    (note_launch(), k_apply_u3_col<T, ALLJ><<<grid, U3_THREADS, smem, st>>>(g, tb, sc, u, su, y, sy));
     prof_end(st, kind);
   } else {
     dim3 grid((g.nu[0] + T2 - 1) / T2, (g.nu[1] + T2 - 1) / T2, 1);
     const int kind = sizeof(T) == 4 ? 0 : 1;
     prof_begin(st, kind, (double)g.nnode * sc.nt);
-    (note_launch(), k_apply_u2<T><<<grid, 256, 0, st>>>(g, tb, sc, u, su, p, sp, y, sy));
+    (note_launch(), k_apply_u2<T><<<grid, 256, 0, st>>>(g, tb, sc, u, su, y, sy));
     prof_end(st, kind);
+  }
+  if (p) {
+    bool any = false;
+    for (int k = 0; k < sc.nt; ++k)
+      for (int l = 0; l < sc.nt; ++l) any = any || sc.ep[k][l] != 0.0;
+    if (any) {
+      const int blocks = (int)((g.nnode + 255) / 256);
+      if (g.dim == 3) (note_launch(), k_add_Ep<T, 3><<<blocks, 256, 0, st>>>(g, tb, sc, p, sp, y, sy));
+      else (note_launch(), k_add_Ep<T, 2><<<blocks, 256, 0, st>>>(g, tb, sc, p, sp, y, sy));
+    }
   }
 }
 
