@@ -13,6 +13,7 @@
 // bitwise reproducible.
 #include <mutex>
 
+#include "coupling.cuh"
 #include "internal.h"
 
 namespace biot {
@@ -52,50 +53,10 @@ __device__ inline T tap5(const T* c, const T* v, int stride) {
 }
 
 // ---------------------------------------------------------------------------
-// bit (2*dir + side) set when that face constrains component c
-__device__ inline int face_mask(const Grid& g, int c) {
-  int m = 0;
-  for (int f = 0; f < 2 * g.dim; ++f) {
-    int b = g.ubc[f];
-    if (b == U_DIRICHLET || (b == U_ROLLER && c == f / 2)) m |= 1 << f;
-  }
-  return m;
-}
-__device__ __forceinline__ bool free_fast(int m, int gx, int gy, int gz, int nx, int ny, int nz) {
-  return !(((m & 1) && gx == 0) || ((m & 2) && gx == nx - 1) || ((m & 4) && gy == 0) || ((m & 8) && gy == ny - 1) ||
-           ((m & 16) && gz == 0) || ((m & 32) && gz == nz - 1));
-}
-
-// 1-D taps of the E coupling along direction d for Q2 node index m: the Gauss-point
-// pressures of the (up to two) cells sharing the node, starting at pressure index
-// s0; cv: value weights (bv), cd: derivative weights (bd).  Missing cells get zero
-// weights and an in-range index.
-template <typename T>
-__device__ __forceinline__ void ep_taps(const TabT<T>& tb, int d, int m, int ncell, int& s0, T (&cv)[4], T (&cd)[4]) {
-  const int j = m >> 1;
-  if (m & 1) {  // mid node: own cell only, local node 1
-    s0 = 2 * j;
-    cv[0] = tb.bv[d][1][0]; cv[1] = tb.bv[d][1][1]; cv[2] = T(0); cv[3] = T(0);
-    cd[0] = tb.bd[d][1][0]; cd[1] = tb.bd[d][1][1]; cd[2] = T(0); cd[3] = T(0);
-  } else {      // vertex: cell j-1 (local node 2) in the first slots if it exists, then cell j (local node 0)
-    const bool lo = j >= 1, hi = j < ncell;
-    s0 = lo ? 2 * j - 2 : 0;
-    cv[0] = lo ? tb.bv[d][2][0] : (hi ? tb.bv[d][0][0] : T(0));
-    cv[1] = lo ? tb.bv[d][2][1] : (hi ? tb.bv[d][0][1] : T(0));
-    cv[2] = (lo && hi) ? tb.bv[d][0][0] : T(0);
-    cv[3] = (lo && hi) ? tb.bv[d][0][1] : T(0);
-    cd[0] = lo ? tb.bd[d][2][0] : (hi ? tb.bd[d][0][0] : T(0));
-    cd[1] = lo ? tb.bd[d][2][1] : (hi ? tb.bd[d][0][1] : T(0));
-    cd[2] = (lo && hi) ? tb.bd[d][0][0] : T(0);
-    cd[3] = (lo && hi) ? tb.bd[d][0][1] : T(0);
-  }
-}
-
 // Y_k += E (sum_l ep[k][l] p_l) on the free displacement rows (§Monolithic
 // Approach: the -b E p block of A_s and its time mixing), one thread per Q2 node
-// for all components and temporal levels.  E_c is the tensor product over the
-// directions of the derivative taps (direction c) and the value taps (the others),
-// evaluated by sum factorisation over the node's 4^d block of Gauss-point pressures.
+// for all components and temporal levels, sum-factorised over the node's block of
+// Gauss-point pressures.
 template <typename T, int DIM>
 __global__ void __launch_bounds__(256) k_add_Ep(Grid g, TabT<T> tb, SlabCoef sc, const T* __restrict__ p_in, int64_t sp,
                                                 T* __restrict__ y, int64_t sy) {
@@ -105,71 +66,30 @@ __global__ void __launch_bounds__(256) k_add_Ep(Grid g, TabT<T> tb, SlabCoef sc,
   const int64_t rr = node / g.nu[0];
   const int iy = (int)(rr % g.nu[1]);
   const int iz = DIM == 3 ? (int)(rr / g.nu[1]) : 0;
-  int sx, sy0, sz = 0;
-  T vx[4], dx[4], vy[4], dy[4], vz[4], dz[4];
-  ep_taps<T>(tb, 0, ix, g.n[0], sx, vx, dx);
-  ep_taps<T>(tb, 1, iy, g.n[1], sy0, vy, dy);
-  if (DIM == 3) ep_taps<T>(tb, 2, iz, g.n[2], sz, vz, dz);
-  // 4-wide windows; taps past the end of the pressure grid carry zero weight and
-  // read a clamped (in-range) index
-  int ox[4], oy[4], oz[4];
+  const EpNode<T, DIM> en(g, tb, ix, iy, iz);
+  T s[MAXR][DIM];  // s[k][c] = sum_l ep[k][l] (E_c p_l)
 #pragma unroll
-  for (int e = 0; e < 4; ++e) {
-    ox[e] = min(sx + e, g.ng[0] - 1);
-    oy[e] = min(sy0 + e, g.ng[1] - 1);
-    oz[e] = DIM == 3 ? min(sz + e, g.ng[2] - 1) : 0;
-  }
-  constexpr int NZ = DIM == 3 ? 4 : 1;
-  T ec[MAXR][DIM];
+  for (int k = 0; k < MAXR; ++k)
 #pragma unroll
-  for (int l = 0; l < MAXR; ++l) {
-    if (l < sc.nt) {
-      const T* p = p_in + l * sp;
-      T a0 = 0, a1 = 0, a2 = 0;
+    for (int c = 0; c < DIM; ++c) s[k][c] = T(0);
+#pragma unroll 1
+  for (int l = 0; l < sc.nt; ++l) {
+    T e[DIM];
+    en.eval(g, p_in + l * sp, e);
 #pragma unroll
-      for (int c2 = 0; c2 < NZ; ++c2) {
-        T b0 = 0, b1 = 0, b2 = 0;  // y-contracted partial sums for the three components
+    for (int k = 0; k < MAXR; ++k) {
+      const T w = T(l == 0 ? sc.ep[k][0] : (l == 1 ? sc.ep[k][1] : sc.ep[k][2]));
 #pragma unroll
-        for (int c1 = 0; c1 < 4; ++c1) {
-          const T* row = p + ((int64_t)oz[c2] * g.ng[1] + oy[c1]) * g.ng[0];
-          T sv = 0, sd = 0;
-#pragma unroll
-          for (int c0 = 0; c0 < 4; ++c0) {
-            const T pv = __ldg(row + ox[c0]);
-            sv += vx[c0] * pv;
-            sd += dx[c0] * pv;
-          }
-          b0 += vy[c1] * sd;  // comp 0: derivative in x
-          b1 += dy[c1] * sv;  // comp 1: derivative in y
-          b2 += vy[c1] * sv;  // comp 2: values in x and y
-        }
-        if (DIM == 3) {
-          a0 += vz[c2] * b0;
-          a1 += vz[c2] * b1;
-          a2 += dz[c2] * b2;  // comp 2: derivative in z
-        } else {
-          a0 += b0;
-          a1 += b1;
-        }
-      }
-      ec[l][0] = a0;
-      ec[l][1] = a1;
-      if (DIM == 3) ec[l][DIM - 1] = a2;
+      for (int c = 0; c < DIM; ++c) s[k][c] += w * e[c];
     }
   }
   const int64_t nn = g.nnode;
 #pragma unroll
   for (int c = 0; c < DIM; ++c) {
-    if (!free_fast(face_mask(g, c), ix, iy, iz, g.nu[0], g.nu[1], g.nu[2])) continue;
+    if (!u_free_mask(u_face_mask(g, c), ix, iy, iz, g.nu[0], g.nu[1], g.nu[2])) continue;
 #pragma unroll
-    for (int k = 0; k < MAXR; ++k) {
-      if (k >= sc.nt) continue;
-      T s = 0;
-#pragma unroll
-      for (int l = 0; l < MAXR; ++l)
-        if (l < sc.nt) s += T(sc.ep[k][l]) * ec[l][c];
-      y[k * sy + c * nn + node] += s;
-    }
+    for (int k = 0; k < MAXR; ++k)
+      if (k < sc.nt) y[k * sy + c * nn + node] += s[k][c];
   }
 }
 
@@ -264,7 +184,7 @@ __global__ void __launch_bounds__(U3_THREADS, ALLJ ? 2 : 1) k_apply_u3_col(Grid 
   const T cf0 = T(2.0 * sc.mu + sc.lam), cf1 = T(sc.mu), cf2 = T(sc.lam);
   const int64_t nn = g.nnode;
   const T* u = u_in + k * su;
-  const int fm0 = face_mask(g, 0), fm1 = face_mask(g, 1), fm2 = face_mask(g, 2);
+  const int fm0 = u_face_mask(g, 0), fm1 = u_face_mask(g, 1), fm2 = u_face_mask(g, 2);
   // staging: several independent loads in flight per thread (the loads hit L2)
   constexpr int NLD = (3 * HHH + U3_THREADS - 1) / U3_THREADS;
   T vals[NLD];
@@ -279,7 +199,7 @@ __global__ void __launch_bounds__(U3_THREADS, ALLJ ? 2 : 1) k_apply_u3_col(Grid 
       const int gx = X0 + lx - 2, gy = Y0 + ly - 2, gz = Z0 + lz - 2;
       const int fm = c == 0 ? fm0 : (c == 1 ? fm1 : fm2);
       if ((unsigned)gx < (unsigned)nx && (unsigned)gy < (unsigned)ny && (unsigned)gz < (unsigned)nz &&
-          free_fast(fm, gx, gy, gz, nx, ny, nz))
+          u_free_mask(fm, gx, gy, gz, nx, ny, nz))
         v = __ldg(u + c * nn + ((int64_t)gz * ny + gy) * nx + gx);
     }
     vals[s8] = v;
@@ -372,7 +292,7 @@ __global__ void __launch_bounds__(U3_THREADS, ALLJ ? 2 : 1) k_apply_u3_col(Grid 
       if (gx >= nx) break;
       const int64_t node = ((int64_t)gz * ny + gy) * nx + gx;
       T out;
-      if (free_fast(fm, gx, gy, gz, nx, ny, nz)) {
+      if (u_free_mask(fm, gx, gy, gz, nx, ny, nz)) {
         out = au * acc[o];
       } else {
         out = u[c * nn + node];
@@ -529,7 +449,7 @@ __global__ void k_apply_q(Grid g, TabT<T> tb, SlabCoef sc, const T* __restrict__
 // ---------------------------------------------------------------------------
 // pressure rows: one thread per Gauss-point pressure DoF.
 template <typename T, int DIM>
-__global__ void k_apply_p(Grid g, TabT<T> tb, SlabCoef sc, const T* __restrict__ x, int64_t sx, T* __restrict__ y, int64_t sy) {
+__global__ void __launch_bounds__(256) k_apply_p(Grid g, TabT<T> tb, SlabCoef sc, const T* __restrict__ x, int64_t sx, T* __restrict__ y, int64_t sy) {
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= g.Np) return;
   int co[3];
@@ -542,40 +462,10 @@ __global__ void k_apply_p(Grid g, TabT<T> tb, SlabCoef sc, const T* __restrict__
   T mp = T(1);
   for (int d = 0; d < DIM; ++d) mp *= tb.wg[d];
   T eu[MAXR], bq[MAXR], pv[MAXR];
-  // the cell's Q2 node block and the per-component face masks, shared by all levels
-  int fm[3];
-  for (int c = 0; c < DIM; ++c) fm[c] = face_mask(g, c);
-  T f[DIM][3][3];  // f[c][d][a]: 1-D factor of E^T for component c along direction d
-#pragma unroll
-  for (int c = 0; c < DIM; ++c)
-#pragma unroll
-    for (int d = 0; d < 3; ++d)
-#pragma unroll
-      for (int a = 0; a < 3; ++a)
-        f[c][d][a] = (d < DIM) ? ((d == c) ? tb.bd[d][a][gq[d]] : tb.bv[d][a][gq[d]]) : (a == 0 ? T(1) : T(0));
-  const int nx = g.nu[0], ny = g.nu[1], nz = g.nu[2];
+  const EtPoint<T, DIM> et(g, tb, co);
   for (int l = 0; l < sc.nt; ++l) {
     const T* xl = x + l * sx;
-    // E^T u: the cell's 3^DIM nodes, all components
-    T acc = 0;
-#pragma unroll
-    for (int c = 0; c < DIM; ++c) {
-      constexpr int AZ = (DIM == 3) ? 3 : 1;
-#pragma unroll
-      for (int az = 0; az < AZ; ++az)
-#pragma unroll
-        for (int ay = 0; ay < 3; ++ay) {
-          const int iz = 2 * cell[2] + az, iy = 2 * cell[1] + ay;
-          const T* row = xl + c * g.nnode + ((int64_t)iz * ny + iy) * nx;
-          T s = 0;
-#pragma unroll
-          for (int ax = 0; ax < 3; ++ax) {
-            const int ix = 2 * cell[0] + ax;
-            if (free_fast(fm[c], ix, iy, iz, nx, ny, nz)) s += f[c][0][ax] * row[ix];
-          }
-          acc += f[c][2][az] * f[c][1][ay] * s;
-        }
-    }
+    const T acc = et.eval(g, xl);  // E^T u: the cell's 3^DIM nodes, all components
     eu[l] = acc;
     // B q: for each component c the 3 DoFs along c on this Gauss line
     T bacc = 0;

@@ -1,0 +1,166 @@
+// Device helpers for the displacement-pressure coupling E_{ij} = (phi^p_j, div v_i)
+// of §Monolithic Approach (the -b E p block of A_s and the b E^T u storage term),
+// evaluated pointwise and sum-factorised on the uniform Cartesian mesh:
+//
+//  * E_c = tensor product over the directions of 1-D Q2-node x Gauss-point
+//    factors, the derivative factor (bd) along c and the value factor (bv)
+//    along the others.
+//  * A Q2 node sees the Gauss-point pressures of the (up to 2^d) cells sharing
+//    it: a 4-wide window per direction at a vertex, 2 at a mid node.
+//  * A Gauss point sees the 3^d Q2 nodes of its own cell.
+//
+// Everything stays in registers: fixed-size windows with zero weights on the
+// missing taps (and an in-range index), no runtime-indexed local arrays.
+#pragma once
+#include "common.cuh"
+#include "tables.h"
+
+namespace biot {
+
+// Face bit (2*dir + side) set when that face constrains displacement component c.
+__device__ __forceinline__ int u_face_mask(const Grid& g, int c) {
+  int m = 0;
+  for (int f = 0; f < 2 * g.dim; ++f) {
+    const int b = g.ubc[f];
+    if (b == U_DIRICHLET || (b == U_ROLLER && c == f / 2)) m |= 1 << f;
+  }
+  return m;
+}
+__device__ __forceinline__ bool u_free_mask(int m, int gx, int gy, int gz, int nx, int ny, int nz) {
+  return !(((m & 1) && gx == 0) || ((m & 2) && gx == nx - 1) || ((m & 4) && gy == 0) || ((m & 8) && gy == ny - 1) ||
+           ((m & 16) && gz == 0) || ((m & 32) && gz == nz - 1));
+}
+
+// 1-D window of the E coupling along direction d for Q2 node index m: the
+// Gauss-point pressures starting at s0 (4 slots), with value weights cv and
+// derivative weights cd; slots of a missing cell carry zero weight.
+template <typename T>
+__device__ __forceinline__ void ep_window(const TabT<T>& tb, int d, int m, int ncell, int& s0, T (&cv)[4], T (&cd)[4]) {
+  const int j = m >> 1;
+  if (m & 1) {  // mid node: own cell only, local node 1
+    s0 = 2 * j;
+    cv[0] = tb.bv[d][1][0]; cv[1] = tb.bv[d][1][1]; cv[2] = T(0); cv[3] = T(0);
+    cd[0] = tb.bd[d][1][0]; cd[1] = tb.bd[d][1][1]; cd[2] = T(0); cd[3] = T(0);
+  } else {      // vertex: cell j-1 (local node 2) first if it exists, then cell j (local node 0)
+    const bool lo = j >= 1, hi = j < ncell;
+    s0 = lo ? 2 * j - 2 : 0;
+    cv[0] = lo ? tb.bv[d][2][0] : (hi ? tb.bv[d][0][0] : T(0));
+    cv[1] = lo ? tb.bv[d][2][1] : (hi ? tb.bv[d][0][1] : T(0));
+    cv[2] = (lo && hi) ? tb.bv[d][0][0] : T(0);
+    cv[3] = (lo && hi) ? tb.bv[d][0][1] : T(0);
+    cd[0] = lo ? tb.bd[d][2][0] : (hi ? tb.bd[d][0][0] : T(0));
+    cd[1] = lo ? tb.bd[d][2][1] : (hi ? tb.bd[d][0][1] : T(0));
+    cd[2] = (lo && hi) ? tb.bd[d][0][0] : T(0);
+    cd[3] = (lo && hi) ? tb.bd[d][0][1] : T(0);
+  }
+}
+
+// The windows of one Q2 node in all directions.
+template <typename T, int DIM>
+struct EpNode {
+  int ox[4], oy[4], oz[4];  // clamped pressure-grid coordinates of the window slots
+  T vx[4], dx[4], vy[4], dy[4], vz[4], dz[4];
+
+  __device__ __forceinline__ EpNode(const Grid& g, const TabT<T>& tb, int ix, int iy, int iz) {
+    int sx, sy, sz = 0;
+    ep_window<T>(tb, 0, ix, g.n[0], sx, vx, dx);
+    ep_window<T>(tb, 1, iy, g.n[1], sy, vy, dy);
+    if (DIM == 3) ep_window<T>(tb, 2, iz, g.n[2], sz, vz, dz);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      ox[e] = min(sx + e, g.ng[0] - 1);
+      oy[e] = min(sy + e, g.ng[1] - 1);
+      oz[e] = DIM == 3 ? min(sz + e, g.ng[2] - 1) : 0;
+    }
+  }
+
+  // out[c] = (E_c p) at this node for one pressure level p (Gauss-point grid, x fastest)
+  __device__ __forceinline__ void eval(const Grid& g, const T* __restrict__ p, T (&out)[DIM]) const {
+    constexpr int NZ = DIM == 3 ? 4 : 1;
+    T a0 = 0, a1 = 0, a2 = 0;
+#pragma unroll
+    for (int c2 = 0; c2 < NZ; ++c2) {
+      T b0 = 0, b1 = 0, b2 = 0;  // y-contracted partial sums
+#pragma unroll
+      for (int c1 = 0; c1 < 4; ++c1) {
+        const T* row = p + ((int64_t)oz[c2] * g.ng[1] + oy[c1]) * g.ng[0];
+        T sv = 0, sd = 0;
+#pragma unroll
+        for (int c0 = 0; c0 < 4; ++c0) {
+          const T pv = __ldg(row + ox[c0]);
+          sv += vx[c0] * pv;
+          sd += dx[c0] * pv;
+        }
+        b0 += vy[c1] * sd;  // component 0: derivative along x
+        b1 += dy[c1] * sv;  // component 1: derivative along y
+        b2 += vy[c1] * sv;  // component 2: values along x and y
+      }
+      if (DIM == 3) {
+        a0 += vz[c2] * b0;
+        a1 += vz[c2] * b1;
+        a2 += dz[c2] * b2;  // component 2: derivative along z
+      } else {
+        a0 += b0;
+        a1 += b1;
+      }
+    }
+    out[0] = a0;
+    out[1] = a1;
+    if (DIM == 3) out[DIM - 1] = a2;
+  }
+};
+
+// E^T at one Gauss point: the 1-D factors f[c][d][a] of component c along
+// direction d for the cell's local node a, and the cell's node block.
+template <typename T, int DIM>
+struct EtPoint {
+  int cell[3];
+  T f[DIM][3][3];
+  int fm[3];
+
+  __device__ __forceinline__ EtPoint(const Grid& g, const TabT<T>& tb, const int (&co)[3]) {
+    int gq[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      cell[d] = (d < DIM) ? co[d] >> 1 : 0;
+      gq[d] = (d < DIM) ? (co[d] & 1) : 0;
+    }
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) {
+      fm[c] = u_face_mask(g, c);
+#pragma unroll
+      for (int d = 0; d < 3; ++d)
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+          f[c][d][a] = (d < DIM) ? ((d == c) ? tb.bd[d][a][gq[d]] : tb.bv[d][a][gq[d]]) : (a == 0 ? T(1) : T(0));
+    }
+  }
+
+  // (E^T u) at this point for one displacement level u ([u_0|u_1|u_2], stride nnode);
+  // constrained displacement entries count as zero
+  __device__ __forceinline__ T eval(const Grid& g, const T* __restrict__ u) const {
+    const int nx = g.nu[0], ny = g.nu[1], nz = g.nu[2];
+    constexpr int AZ = (DIM == 3) ? 3 : 1;
+    T acc = 0;
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) {
+#pragma unroll
+      for (int az = 0; az < AZ; ++az)
+#pragma unroll
+        for (int ay = 0; ay < 3; ++ay) {
+          const int iz = 2 * cell[2] + az, iy = 2 * cell[1] + ay;
+          const T* row = u + c * g.nnode + ((int64_t)iz * ny + iy) * nx;
+          T s = 0;
+#pragma unroll
+          for (int ax = 0; ax < 3; ++ax) {
+            const int ix = 2 * cell[0] + ax;
+            if (u_free_mask(fm[c], ix, iy, iz, nx, ny, nz)) s += f[c][0][ax] * __ldg(row + ix);
+          }
+          acc += f[c][2][az] * f[c][1][ay] * s;
+        }
+    }
+    return acc;
+  }
+};
+
+}  // namespace biot

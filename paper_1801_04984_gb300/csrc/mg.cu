@@ -9,6 +9,7 @@
 // block first, with the displacement coupling lam b E^T (tau A)^{-1} b tau E
 // replaced by lam (b^2/K_dr) Mp, then the displacement from
 // tau A u = r_u + b tau E p.
+#include "coupling.cuh"
 #include "internal.h"
 
 namespace biot {
@@ -388,50 +389,29 @@ __global__ void k_q_final(Grid g, TabT<T> tb, const T* __restrict__ rq, int64_t 
 }
 
 // bu = ru + alpha * E p on free displacement DoFs, ru on constrained
+// bu = ru + alpha E p on free displacement rows, ru on constrained rows; one
+// thread per Q2 node, all components (sum-factorised E, see coupling.cuh)
 template <typename T, int DIM>
-__global__ void k_u_rhs(Grid g, TabT<T> tb, const T* __restrict__ ru, int64_t sru, const T* __restrict__ p, int64_t spp,
-                        double alpha, T* __restrict__ bu, int64_t sbu, int nrhs) {
-  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(256) k_u_rhs(Grid g, TabT<T> tb, const T* __restrict__ ru, int64_t sru,
+                                               const T* __restrict__ p, int64_t spp, double alpha, T* __restrict__ bu,
+                                               int64_t sbu, int nrhs) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= g.nnode) return;
-  int ix = (int)(t % g.nu[0]);
-  int64_t rr = t / g.nu[0];
-  int iy = (int)(rr % g.nu[1]);
-  int iz = (int)(rr / g.nu[1]);
-  int idx[3] = {ix, iy, iz};
-  {
-    const int c = blockIdx.y;
-    bool fr = u_free(g, c, ix, iy, iz);
-    // taps of E along each direction
-    int pi[3][4], cnt[3];
-    T pc[3][4];
-    for (int d = 0; d < 3; ++d) {
-      int k = 0;
-      if (d < DIM) {
-        int m = idx[d];
-        const T(*tab)[2] = (d == c) ? tb.bd[d] : tb.bv[d];
-        if (m & 1) { for (int q = 0; q < 2; ++q) { pi[d][k] = m - 1 + q; pc[d][k] = tab[1][q]; ++k; } }
-        else {
-          int j = m >> 1;
-          if (j >= 1) for (int q = 0; q < 2; ++q) { pi[d][k] = 2 * (j - 1) + q; pc[d][k] = tab[2][q]; ++k; }
-          if (j < g.n[d]) for (int q = 0; q < 2; ++q) { pi[d][k] = 2 * j + q; pc[d][k] = tab[0][q]; ++k; }
-        }
-      } else { pi[d][0] = 0; pc[d][0] = T(1); k = 1; }
-      cnt[d] = k;
-    }
-    for (int r = 0; r < nrhs; ++r) {
+  const int ix = (int)(t % g.nu[0]);
+  const int64_t rr = t / g.nu[0];
+  const int iy = (int)(rr % g.nu[1]);
+  const int iz = DIM == 3 ? (int)(rr / g.nu[1]) : 0;
+  const EpNode<T, DIM> en(g, tb, ix, iy, iz);
+  bool fr[DIM];
+#pragma unroll
+  for (int c = 0; c < DIM; ++c) fr[c] = u_free_mask(u_face_mask(g, c), ix, iy, iz, g.nu[0], g.nu[1], g.nu[2]);
+  for (int r = 0; r < nrhs; ++r) {
+    T ep[DIM];
+    en.eval(g, p + r * spp, ep);
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) {
       T v = ru[r * sru + c * g.nnode + t];
-      if (fr) {
-        const T* pr = p + r * spp;
-        T acc = 0;
-        for (int a = 0; a < cnt[2]; ++a)
-          for (int b = 0; b < cnt[1]; ++b) {
-            const T* row = pr + ((int64_t)pi[2][a] * g.ng[1] + pi[1][b]) * g.ng[0];
-            T s = 0;
-            for (int e = 0; e < cnt[0]; ++e) s += pc[0][e] * row[pi[0][e]];
-            acc += pc[2][a] * pc[1][b] * s;
-          }
-        v += T(alpha) * acc;
-      }
+      if (fr[c]) v += T(alpha) * ep[c];
       bu[r * sbu + c * g.nnode + t] = v;
     }
   }
@@ -491,48 +471,27 @@ void launch_q_final(const Grid& g, const TabT<T>& tb, const T* rq, int64_t srq, 
 template <typename T>
 void launch_u_rhs(const Grid& g, const TabT<T>& tb, const T* ru, int64_t sru, const T* p, int64_t spp, double alpha, T* bu,
                   int64_t sbu, int nrhs, cudaStream_t st) {
-  dim3 grid((unsigned)((g.nnode + 255) / 256), g.dim);
+  const unsigned grid = (unsigned)((g.nnode + 255) / 256);
   if (g.dim == 3) (note_launch(), k_u_rhs<T, 3><<<grid, 256, 0, st>>>(g, tb, ru, sru, p, spp, alpha, bu, sbu, nrhs));
   else (note_launch(), k_u_rhs<T, 2><<<grid, 256, 0, st>>>(g, tb, ru, sru, p, spp, alpha, bu, sbu, nrhs));
 }
 
 
 // out_p = rp + alpha E^T u at a pressure DoF (u masked)
+// out = rp + alpha E^T u per pressure Gauss point (constrained displacements count as zero)
 template <typename T, int DIM>
-__global__ void k_p_plus_ETu(Grid g, TabT<T> tb, const T* __restrict__ rp, int64_t srp, const T* __restrict__ u, int64_t su,
-                             double alpha, T* __restrict__ out, int64_t so, int nrhs) {
-  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(256) k_p_plus_ETu(Grid g, TabT<T> tb, const T* __restrict__ rp, int64_t srp,
+                                                    const T* __restrict__ u, int64_t su, double alpha, T* __restrict__ out,
+                                                    int64_t so, int nrhs) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= g.Np) return;
   int co[3];
   co[0] = (int)(t % g.ng[0]);
-  int64_t rr = t / g.ng[0];
+  const int64_t rr = t / g.ng[0];
   co[1] = (int)(rr % g.ng[1]);
   co[2] = (int)(rr / g.ng[1]);
-  int cell[3], gq[3];
-  for (int d = 0; d < 3; ++d) { cell[d] = (d < DIM) ? co[d] >> 1 : 0; gq[d] = (d < DIM) ? (co[d] & 1) : 0; }
-  for (int r = 0; r < nrhs; ++r) {
-    const T* ur = u + r * su;
-    T acc = 0;
-    for (int c = 0; c < DIM; ++c) {
-      T f[3][3];
-      for (int d = 0; d < 3; ++d)
-        for (int a = 0; a < 3; ++a)
-          f[d][a] = (d < DIM) ? ((d == c) ? tb.bd[d][a][gq[d]] : tb.bv[d][a][gq[d]]) : (a == 0 ? T(1) : T(0));
-      const int az_n = (DIM == 3) ? 3 : 1;
-      for (int az = 0; az < az_n; ++az)
-        for (int ay = 0; ay < 3; ++ay) {
-          int iz = 2 * cell[2] + az, iy = 2 * cell[1] + ay;
-          const T* row = ur + c * g.nnode + ((int64_t)iz * g.nu[1] + iy) * g.nu[0];
-          T s = 0;
-          for (int ax = 0; ax < 3; ++ax) {
-            int ix = 2 * cell[0] + ax;
-            if (u_free(g, c, ix, iy, iz)) s += f[0][ax] * row[ix];
-          }
-          acc += f[2][az] * f[1][ay] * s;
-        }
-    }
-    out[r * so + t] = rp[r * srp + t] + T(alpha) * acc;
-  }
+  const EtPoint<T, DIM> et(g, tb, co);
+  for (int r = 0; r < nrhs; ++r) out[r * so + t] = rp[r * srp + t] + T(alpha) * et.eval(g, u + r * su);
 }
 template <typename T>
 void launch_p_plus_ETu(const Grid& g, const TabT<T>& tb, const T* rp, int64_t srp, const T* u, int64_t su, double alpha, T* out,
