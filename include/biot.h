@@ -138,7 +138,22 @@ typedef struct {
  * lambda < 0, eta <= 0, any K_cell <= 0 or non-finite; ENOMEM; ECUDA. */
 int biot_setup(const biot_mesh* mesh, const biot_coeffs* coeffs, int r, const biot_opts* opts, biot_t* out);
 
-/* Sizes: DoFs per temporal level and per slab, number of cells. */
+/* Batched context: nb independent instances of the same mesh, coefficients
+ * and time order that differ only in their permeability fields (coeffs->K_cell:
+ * HOST array of nb * n_cells values, instance-major) and their loads.  Every
+ * kernel of the apply, preconditioner and solver covers all instances in one
+ * launch (the instance is part of the launch grid) and every Krylov scalar is
+ * kept per instance.  Vector layout of a batched slab vector: level-major,
+ * the spatial vector of temporal level k of instance b starts at
+ * (k * nb + b) * n_space (biot_sizes reports per-instance sizes).
+ * biot_apply_slab and biot_precondition accept batched vectors; solves run in
+ * BIOT_MIXED mode through biot_march_batch.  Requires the lumped Darcy mass
+ * (opts->flux_mass_exact = 0).  Errors as biot_setup, EINVAL for nb outside
+ * 1..4096.  (The paper solves one problem at a time; this serves many-instance
+ * studies such as permeability sweeps.) */
+int biot_setup_batch(const biot_mesh* mesh, const biot_coeffs* coeffs, int r, const biot_opts* opts, int nb, biot_t* out);
+
+/* Sizes: DoFs per temporal level and per slab, number of cells (per instance). */
 int biot_sizes(biot_t ctx, int64_t* n_space, int64_t* n_slab, int64_t* n_cells);
 
 /* Replace the cellwise permeability (HOST array, n_cells, > 0). */
@@ -177,6 +192,22 @@ int biot_march(biot_t ctx, double T, int slabs, int nterms, const double* const*
                const double* U0, double* U_end, double* X_all, const biot_solve_opts* opts, int* iters_per_slab,
                biot_stats* stats, void* stream);
 
+/* Marches every instance of a batched context (biot_setup_batch) over the same
+ * `slabs` slabs of (0, T] (paper §Discretisation in Time), all instances in
+ * lockstep: one batched right-hand side, one batched mixed-precision solve per
+ * slab.  f_terms holds nb * nterms pointers (instance b's term m at
+ * f_terms[b * nterms + m], n_space each, HOST or DEVICE); the time profiles
+ * tcoef (4 * nterms, HOST) are shared.  U0 (nb pointers, or NULL for zero
+ * initial states; entries may be NULL) and U_end (nb pointers) are per-instance
+ * states of n_space entries, HOST or DEVICE.  iters, stats and status (HOST,
+ * nb entries each, may be NULL) receive each instance's total Krylov
+ * iterations, statistics and return code; the call returns BIOT_OK or the
+ * first failing code.  Only BIOT_MIXED solves (opts->mode) are batched; a
+ * context with nb = 1 marches as biot_march. */
+int biot_march_batch(biot_t ctx, double T, int slabs, int nterms, const double* const* f_terms, const double* tcoef,
+                     const double* const* U0, double* const* U_end, const biot_solve_opts* opts, int* iters,
+                     biot_stats* stats, int* status, void* stream);
+
 /* Adjoint gradient of J = j^T U(T^-) with respect to the cellwise
  * log-permeability g_c (K_c = K0 exp(g_c)): the dual problem marched backwards
  * over slabs with the transposed slab operator, the forward slab solutions
@@ -193,13 +224,17 @@ int biot_adjoint_grad(biot_t ctx, double T, int slabs, int nterms, const double*
  * either a built-in load (load_kind >= 0: one BIOT_LOAD_* preset of magnitude
  * load_value, constant in time) or explicit load terms as in biot_march
  * (load_kind = -1).  U0 / U_end (n_space each, host or device, may be NULL) are
- * the instance's initial and end states.  The instances are solved on the
- * current device by one host worker with its own stream and a cache of contexts
- * keyed by everything except the permeability (instances of equal shape reuse the
- * multigrid hierarchy and Krylov bases).  `workers` is accepted for a later
- * concurrent mode and currently ignored.  status[i] and stats[i] (host arrays, may be NULL) receive each
- * instance's return code and statistics; the call returns BIOT_OK or the first
- * failing code.  (The paper solves one problem at a time; batching serves the
+ * the instance's initial and end states.  Instances that share everything but
+ * the permeability and the load (mesh, boundary codes, coefficients, r, T,
+ * slabs, time profiles) form a group; with sopts->mode = BIOT_MIXED every group
+ * of two or more is solved as one batched context (biot_setup_batch /
+ * biot_march_batch: all its instances in every launch), at most `workers`
+ * instances per context (<= 0: 64).  Other instances (FP64 mode, groups of one,
+ * the 2-D manufactured presets, whose load depends on the instance's
+ * permeability) are marched one by one with a context cache keyed by shape.
+ * status[i] and stats[i] (host arrays, may be NULL) receive each instance's
+ * return code and statistics; the call returns BIOT_OK or the first failing
+ * code.  (The paper solves one problem at a time; batching serves the
  * many-instance studies its space-time method targets, e.g. parameter sweeps.) */
 typedef struct {
   biot_mesh mesh;

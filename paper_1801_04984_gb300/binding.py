@@ -80,6 +80,10 @@ def load(path: str = LIB_PATH):
     vp, dp, ip, i64p = C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int), C.POINTER(C.c_int64)
     sig = {
         "biot_setup": (C.c_int, [C.POINTER(Mesh), C.POINTER(Coeffs), C.c_int, C.POINTER(Opts), C.POINTER(vp)]),
+        "biot_setup_batch": (C.c_int, [C.POINTER(Mesh), C.POINTER(Coeffs), C.c_int, C.POINTER(Opts), C.c_int,
+                                       C.POINTER(vp)]),
+        "biot_march_batch": (C.c_int, [vp, C.c_double, C.c_int, C.c_int, C.POINTER(vp), dp, C.POINTER(vp), C.POINTER(vp),
+                                       C.POINTER(SolveOpts), ip, C.c_void_p, ip, vp]),
         "biot_sizes": (C.c_int, [vp, i64p, i64p, i64p]),
         "biot_set_permeability": (C.c_int, [vp, dp]),
         "biot_apply_slab": (C.c_int, [vp, C.c_double, vp, vp, C.c_int, C.c_int, vp]),
@@ -140,9 +144,12 @@ def _solve_opts(tol=1e-10, max_iters=2000, mode=FP64, inner_tol=1e-5, transpose=
 
 
 class Context:
-    """One mesh + coefficient set + time order r on the current CUDA device."""
+    """One mesh + coefficient set + time order r on the current CUDA device.  With nb > 1
+    (biot_setup_batch) the context holds nb instances that differ only in their
+    permeability (coeffs["K"]: nb * n_cells values, instance-major) and in their loads;
+    its slab vectors are level-major (level k of instance b at (k * nb + b) * n_space)."""
 
-    def __init__(self, dim, n, coeffs: dict, r: int, u_bc, f_bc, lo=None, hi=None, opts: dict | None = None):
+    def __init__(self, dim, n, coeffs: dict, r: int, u_bc, f_bc, lo=None, hi=None, opts: dict | None = None, nb: int = 1):
         lib = load()
         m = Mesh()
         m.dim = dim
@@ -161,15 +168,21 @@ class Context:
             for k, v in opts.items():
                 setattr(o, k, v)
         h = C.c_void_p()
-        rc = lib.biot_setup(C.byref(m), C.byref(co), int(r), C.byref(o), C.byref(h))
+        if nb == 1:
+            rc = lib.biot_setup(C.byref(m), C.byref(co), int(r), C.byref(o), C.byref(h))
+        else:
+            rc = lib.biot_setup_batch(C.byref(m), C.byref(co), int(r), C.byref(o), int(nb), C.byref(h))
         if rc != OK:
             raise BiotError(rc, lib.biot_last_error(None).decode())
         self.h = h
         self.lib = lib
+        self.nb = int(nb)
         self.dim, self.r, self.nt = dim, r, r + 1
         ns, nsl, nc = C.c_int64(), C.c_int64(), C.c_int64()
         lib.biot_sizes(h, C.byref(ns), C.byref(nsl), C.byref(nc))
+        # per-instance sizes; a batched slab vector holds nb of them (n_slab_all)
         self.n_space, self.n_slab, self.n_cells = ns.value, nsl.value, nc.value
+        self.n_slab_all = self.n_slab * self.nb
 
     def _check(self, rc, allow=()):
         if rc != OK and rc not in allow:
@@ -197,15 +210,15 @@ class Context:
         import torch
         prec = FP64 if x.dtype == torch.float64 else FP32
         dt = torch.float64 if prec == FP64 else torch.float32
-        return self._check(self.lib.biot_apply_slab(self.h, float(tau), _ptr(x, dt, self.n_slab, "x"),
-                                                    _ptr(y, dt, self.n_slab, "y"), prec, int(transpose), _stream()))
+        return self._check(self.lib.biot_apply_slab(self.h, float(tau), _ptr(x, dt, self.n_slab_all, "x"),
+                                                    _ptr(y, dt, self.n_slab_all, "y"), prec, int(transpose), _stream()))
 
     def precondition(self, tau, r, z, transpose=False):
         import torch
         prec = FP64 if r.dtype == torch.float64 else FP32
         dt = torch.float64 if prec == FP64 else torch.float32
-        return self._check(self.lib.biot_precondition(self.h, float(tau), _ptr(r, dt, self.n_slab, "r"),
-                                                      _ptr(z, dt, self.n_slab, "z"), prec, int(transpose), _stream()))
+        return self._check(self.lib.biot_precondition(self.h, float(tau), _ptr(r, dt, self.n_slab_all, "r"),
+                                                      _ptr(z, dt, self.n_slab_all, "z"), prec, int(transpose), _stream()))
 
     def solve_slab(self, tau, rhs, x, tol=1e-10, max_iters=2000, mode=FP64, inner_tol=1e-5, transpose=False,
                    allow_noconv=False):
@@ -256,6 +269,43 @@ class Context:
         d = st.as_dict()
         d["iters_per_slab"] = list(its)
         return d
+
+    def march_batch(self, T, slabs, f_terms, tcoef, U0, U_end, tol=1e-10, max_iters=2000, inner_tol=1e-5):
+        """Batched march (biot_march_batch, BIOT_MIXED).  f_terms: one list of load terms per
+        instance (same count for all; torch CUDA tensors or numpy arrays of n_space);
+        U0: None or one state per instance; U_end: one output per instance (torch CUDA tensor
+        or float64 numpy array).  Returns (rc, status list, stats dicts)."""
+        nb = self.nb
+        assert len(f_terms) == nb and len(U_end) == nb
+        nterms = len(f_terms[0])
+        flat = [f for terms in f_terms for f in terms]
+        assert len(flat) == nb * nterms
+        arr = (C.c_void_p * max(1, nb * nterms))()
+        keep = []
+
+        def anyptr(t, name):
+            if t is None:
+                return None
+            if isinstance(t, np.ndarray):
+                assert t.dtype == np.float64 and t.flags.c_contiguous and t.size == self.n_space, name
+                keep.append(t)
+                return t.ctypes.data
+            keep.append(t)
+            return _ptr(t, None, self.n_space, name).value
+        for i, f in enumerate(flat):
+            if isinstance(f, np.ndarray):
+                f = np.ascontiguousarray(f, dtype=np.float64)
+            arr[i] = anyptr(f, "f_term")
+        tc = np.ascontiguousarray(np.asarray(tcoef, dtype=np.float64).reshape(-1)) if nterms else np.zeros(4)
+        u0 = (C.c_void_p * nb)(*[anyptr(u, "U0") for u in U0]) if U0 is not None else None
+        ue = (C.c_void_p * nb)(*[anyptr(u, "U_end") for u in U_end])
+        o = _solve_opts(tol, max_iters, MIXED, inner_tol, 0)
+        its = (C.c_int * nb)()
+        stats = (Stats * nb)()
+        status = (C.c_int * nb)()
+        rc = self.lib.biot_march_batch(self.h, float(T), int(slabs), nterms, arr, tc.ctypes.data_as(C.POINTER(C.c_double)),
+                                       u0, ue, C.byref(o), its, C.cast(stats, C.c_void_p), status, _stream())
+        return rc, list(status), [s.as_dict() for s in stats]
 
     def adjoint_grad(self, T, slabs, f_terms, tcoef, U0, j_goal, dJ, tol=1e-10, max_iters=2000, mode=FP64,
                      inner_tol=1e-5, recompute=True):
@@ -326,10 +376,11 @@ def make_mesh(dim, n, u_bc, f_bc, lo=None, hi=None):
     return m
 
 
-def solve_batch(instances, workers=8, tol=1e-10, mode=MIXED, inner_tol=1e-5, max_iters=2000, opts=None):
+def solve_batch(instances, workers=0, tol=1e-10, mode=MIXED, inner_tol=1e-5, max_iters=2000, opts=None):
     """Batched marches (biot_solve_batch).  Each instance is a dict with dim, n, coeffs
     (b, invM, K_dr, lam, mu, eta, K), r, T, slabs, u_bc, f_bc, load_kind, load_value and
-    U_end (a float64 numpy array of n_space that receives the end state).
+    U_end (a float64 numpy array of n_space that receives the end state).  `workers`:
+    at most this many instances per batched context (0: the library default).
     Returns (rc, per-instance status list, per-instance stats dicts)."""
     lib = load()
     cnt = len(instances)

@@ -293,8 +293,14 @@ struct GraphEntry {
   long long kernels;  // kernel nodes in the graph (for the launch counter)
 };
 
+// per-instance scalar block of the Krylov reductions in hdev / hhost (instance b at b * HS):
+// [0, 64) first Gram-Schmidt dots, [64, 128) second, 128 ||w||^2, 129 1/||w||, [160, 224) the
+// least-squares coefficients y
+constexpr int HS = 256;
+
 struct biot_ctx {
   Grid g;
+  int nb = 1;                  // independent instances batched in this context (level-major vectors)
   int lumped_flux = 1;
   bool use_graphs = true;
   std::map<GraphKey, GraphEntry> graphs;
@@ -321,8 +327,12 @@ struct biot_ctx {
   PrecWork<float> p32;
   void** ptrbuf = nullptr;     // device array of vector pointers for small reductions
   void** hptr = nullptr;       // pinned staging for ptrbuf
-  double* hdev = nullptr;      // device scalars for the Krylov reductions
+  double* hdev = nullptr;      // device scalars for the Krylov reductions (HS per instance)
   double* hhost = nullptr;     // pinned mirror
+  double* bdev = nullptr;      // per-column scalars of batched kernels (4 * nt * nb + 64)
+  double* bhost = nullptr;     // pinned mirror
+  std::vector<int> it_b, ref_b, rc_b;   // batched solve: per-instance statistics of the last call
+  std::vector<double> res_b;
   double* partial = nullptr;   // reduction partials
   double* r64 = nullptr;       // FP64 slab temporaries (refinement / march)
   double* a64 = nullptr;
@@ -331,11 +341,16 @@ struct biot_ctx {
   double* m_f[8] = {nullptr};  // march buffers (load terms, state, rhs, slab solution)
   const double** m_fdev = nullptr;
   double *m_U = nullptr, *m_SU = nullptr, *m_rhs = nullptr, *m_X = nullptr;
+  double* bm_f = nullptr;      // batched march buffers: load terms [b][m][N], state [b][N],
+  const double** bm_fdev = nullptr;  // per-instance term tables (8 each), jump term, rhs and
+  double *bm_U = nullptr, *bm_SU = nullptr, *bm_rhs = nullptr, *bm_X = nullptr;  // solution [k][b][N]
+  int bm_terms = 0;
   double* lvl64 = nullptr;     // one-level temporaries
   double* lvl64b = nullptr;
   std::vector<void*> extra;    // other allocations
   std::string err;
 
+  int64_t lvN() const { return g.N * nb; }  // stride between temporal levels of a slab vector
   template <typename T> Krylov<T>& kry();
   template <typename T> PrecWork<T>& pw();
   template <typename T> const TabT<T>& tab() const;
@@ -400,6 +415,17 @@ SlabCoef slab_coef(const biot_ctx& c, double tau, int transpose) {
   return s;
 }
 
+// segments of a (batched) slab vector: instance b, level k at (k * nb + b) * N
+Seg slab_seg(const biot_ctx& c) {
+  Seg sg;
+  sg.nb = c.nb;
+  sg.nt = c.nt;
+  sg.len = c.g.N;
+  sg.istride = c.g.N;
+  sg.lstride = c.g.N * c.nb;
+  return sg;
+}
+
 template <typename T>
 void apply_slab_T(biot_ctx& c, double tau, const T* x, T* y, int transpose, cudaStream_t st) {
   SlabCoef sc = slab_coef(c, tau, transpose);
@@ -417,10 +443,12 @@ template <typename T>
 void apply_A(const Level& L, double lam, double mu, double tau, const T* x, T* y, int nrhs, cudaStream_t st) {
   SlabCoef sc;
   std::memset(&sc, 0, sizeof(sc));
-  sc.nt = nrhs;
+  sc.nt = 1;
   sc.lam = lam;
   sc.mu = mu;
-  for (int k = 0; k < nrhs; ++k) sc.au[k] = tau;
+  sc.au[0] = tau;
+  sc.ucols = nrhs;  // every column (temporal level x batched instance) takes tau A
+  sc.udiv = nrhs;
   launch_apply_u<T>(L.g, ltab<T>(L), sc, x, L.g.Nu, nullptr, 0, y, L.g.Nu, st);
   CKL();
 }
@@ -431,7 +459,7 @@ void ensure_prec(biot_ctx& c) {
   PrecWork<T>& w = c.pw<T>();
   if (w.tA) return;
   const Grid& g = c.g;
-  const int nt = c.nt;
+  const int nt = c.nt * c.nb;  // columns: temporal levels x instances
   int64_t nqt = g.nq[0] + g.nq[1] + g.nq[2];
   w.tA = dalloc<T>(nt * g.N);
   w.tB = dalloc<T>(nt * g.N);
@@ -444,7 +472,7 @@ void ensure_prec(biot_ctx& c) {
   w.pAx = dalloc<T>(nt * g.Np);
   w.pxo = dalloc<T>(nt * g.Np);
   w.pdinv = dalloc<T>(nt * g.Np);
-  w.scoef = dalloc<T>(16 * g.Np);
+  w.scoef = dalloc<T>(16 * g.Np * c.nb);
   for (Level& L : c.lv) {
     LevelWork<T>& lw = lwork<T>(L);
     int64_t n = (int64_t)nt * L.g.Nu;
@@ -466,14 +494,16 @@ void ensure_krylov(biot_ctx& c, int m) {
   if (K.tmp) cudaFree(K.tmp);
   K.V.clear();
   K.Z.clear();
-  const int64_t n = c.g.N * c.nt;
+  const int64_t n = c.g.N * c.nt * c.nb;
   for (int i = 0; i <= m; ++i) K.V.push_back(dalloc<T>(n));
   for (int i = 0; i < m; ++i) K.Z.push_back(dalloc<T>(n));
   K.tmp = dalloc<T>(n);
   K.dV = (const T**)dalloc<T*>(2 * m + 1);
   std::vector<T*> ptrs(K.V.begin(), K.V.end());
   ptrs.insert(ptrs.end(), K.Z.begin(), K.Z.end());
+  // pageable copy on the legacy stream: wait for it, the solver's streams do not order after it
   CK(cudaMemcpy((void*)K.dV, ptrs.data(), ptrs.size() * sizeof(T*), cudaMemcpyHostToDevice));
+  CK(cudaDeviceSynchronize());
   K.m = m;
 }
 
@@ -531,43 +561,80 @@ double tridiag_eig(const std::vector<double>& d, const std::vector<double>& e, b
 
 template <class OpF>
 double lanczos_lmax(biot_ctx& c, OpF op, const double* dinv, int64_t dstride, int64_t n, int64_t stride, int nrhs, int steps,
-                    double* r, double* z, double* p, double* q, cudaStream_t st, double* lmin_out = nullptr) {
+                    double* r, double* z, double* p, double* q, cudaStream_t st, double* lmin_out = nullptr, int per_level = 1) {
+  // start vector of rhs k depends on its temporal level k / per_level only, so every batched
+  // instance starts from the vector a single context would use
   std::vector<double> h((size_t)stride * nrhs, 0.0);
   for (int k = 0; k < nrhs; ++k)
-    for (int64_t i = 0; i < n; ++i) h[k * stride + i] = 1.0 + 0.3 * std::sin(0.91 * (double)i + 0.7 * k) + 0.2 * std::cos(2.3 * (double)i);
+    for (int64_t i = 0; i < n; ++i)
+      h[k * stride + i] = 1.0 + 0.3 * std::sin(0.91 * (double)i + 0.7 * (k / per_level)) + 0.2 * std::cos(2.3 * (double)i);
   CK(cudaMemcpyAsync(r, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice, st));
   // z = Dinv r, p = z (rows with Dinv = 0, the constrained ones, never enter the Krylov space)
   launch_dinv_mul<double>(dinv, dstride, r, z, n, stride, nrhs, st);
   CK(cudaMemcpyAsync(p, z, (size_t)stride * nrhs * sizeof(double), cudaMemcpyDeviceToDevice, st));
   CKL();
+  // every rhs at once: segmented dots (one result per rhs) and per-rhs axpbys with
+  // coefficient columns staged through pinned memory (each staging write follows a
+  // stream synchronisation, so no copy still reads it)
+  Seg sg;
+  sg.nb = nrhs;
+  sg.nt = 1;
+  sg.len = n;
+  sg.istride = stride;
+  sg.lstride = 0;
+  double* out = c.bdev;                 // nrhs dots
+  double* ca = c.bdev + nrhs;           // coefficient columns
+  double* cb = c.bdev + 2 * nrhs;
+  double* one = c.bdev + 3 * nrhs;
+  c.hptr[8] = (void*)r;
+  c.hptr[9] = (void*)p;
+  CK(cudaMemcpyAsync(c.ptrbuf + 8, c.hptr + 8, 2 * sizeof(void*), cudaMemcpyHostToDevice, st));
+  const double* const* vr = reinterpret_cast<const double* const*>(c.ptrbuf + 8);
+  const double* const* vp = reinterpret_cast<const double* const*>(c.ptrbuf + 9);
+  auto dots = [&](const double* const* V, const double* w, std::vector<double>& res) {
+    launch_seg_multidot<double>(V, 1, w, sg, c.partial, out, 1, st);
+    CKL();
+    CK(cudaMemcpyAsync(c.bhost, out, nrhs * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    res.assign(c.bhost, c.bhost + nrhs);
+  };
   double best = 0.0;
-  std::vector<double> rz(nrhs), alpha_prev(nrhs, 0.0), beta_prev(nrhs, 0.0);
+  std::vector<double> rz, pq, rzn, alpha_prev(nrhs, 0.0), beta_prev(nrhs, 0.0);
   std::vector<std::vector<double>> dd(nrhs), ee(nrhs);
-  for (int k = 0; k < nrhs; ++k) rz[k] = dev_dot(c, r + k * stride, z + k * stride, n, st);
+  dots(vr, z, rz);
+  for (int k = 0; k < nrhs; ++k) c.bhost[3 * nrhs + k] = 1.0;
   for (int it = 0; it < steps; ++it) {
     op(p, q);
+    dots(vp, q, pq);
     bool stop = false;
-    for (int k = 0; k < nrhs; ++k) {
-      double pq = dev_dot(c, p + k * stride, q + k * stride, n, st);
-      if (!(pq > 0) || !(rz[k] > 0)) { stop = true; continue; }
-      double alpha = rz[k] / pq;
-      dd[k].push_back(1.0 / alpha + (it > 0 ? beta_prev[k] / alpha_prev[k] : 0.0));
-      launch_axpby<double>(r + k * stride, q + k * stride, -alpha, 1.0, n, st);
-      alpha_prev[k] = alpha;
-    }
+    for (int k = 0; k < nrhs; ++k)
+      if (!(pq[k] > 0) || !(rz[k] > 0)) stop = true;
     if (stop) break;
+    for (int k = 0; k < nrhs; ++k) {
+      const double alpha = rz[k] / pq[k];
+      dd[k].push_back(1.0 / alpha + (it > 0 ? beta_prev[k] / alpha_prev[k] : 0.0));
+      alpha_prev[k] = alpha;
+      c.bhost[nrhs + k] = -alpha;
+      c.bhost[3 * nrhs + k] = 1.0;
+    }
+    CK(cudaMemcpyAsync(ca, c.bhost + nrhs, nrhs * sizeof(double), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(one, c.bhost + 3 * nrhs, nrhs * sizeof(double), cudaMemcpyHostToDevice, st));
+    launch_seg_axpby<double>(r, q, ca, one, sg, st);  // r -= alpha q
     launch_dinv_mul<double>(dinv, dstride, r, z, n, stride, nrhs, st);
     CKL();
+    dots(vr, z, rzn);
     for (int k = 0; k < nrhs; ++k) {
-      double rzn = dev_dot(c, r + k * stride, z + k * stride, n, st);
-      double beta = rzn / rz[k];
+      const double beta = rzn[k] / rz[k];
       ee[k].push_back(std::sqrt(std::max(beta, 0.0)) / alpha_prev[k]);
       beta_prev[k] = beta;
-      rz[k] = rzn;
-      launch_axpby<double>(p + k * stride, z + k * stride, 1.0, beta, n, st);  // p = z + beta p
+      rz[k] = rzn[k];
+      c.bhost[2 * nrhs + k] = beta;
     }
+    CK(cudaMemcpyAsync(cb, c.bhost + 2 * nrhs, nrhs * sizeof(double), cudaMemcpyHostToDevice, st));
+    launch_seg_axpby<double>(p, z, one, cb, sg, st);  // p = z + beta p
     CKL();
   }
+  CK(cudaStreamSynchronize(st));
   double worst_min = 1e300;
   for (int k = 0; k < nrhs; ++k) {
     std::vector<double> e(ee[k].begin(), ee[k].end());
@@ -700,16 +767,31 @@ double schur_lmax(biot_ctx& c, double tau, cudaStream_t st) {
   const Grid& g = c.g;
   double cm[MAXR];
   schur_cm(c, cm);
-  launch_schur_dinv<double>(g, c.t64, c.sb2_64, cm, tau, w.pdinv, c.nt, st);
+  const int cols = c.nt * c.nb;  // every temporal level of every batched instance
+  launch_schur_dinv<double>(g, c.t64, c.sb2_64, cm, tau, w.pdinv, cols, st);
   CKL();
-  auto op = [&](const double* x, double* y) { schur_apply<double>(c, tau, cm, x, y, c.nt, st); };
+  auto op = [&](const double* x, double* y) { schur_apply<double>(c, tau, cm, x, y, cols, st); };
   double lmin = 0;
-  double lm = lanczos_lmax(c, op, w.pdinv, g.Np, g.Np, g.Np, c.nt, 30, w.gp, w.pp, w.pd, w.pAx, st, &lmin);
+  double lm = lanczos_lmax(c, op, w.pdinv, g.Np, g.Np, g.Np, cols, 30, w.gp, w.pp, w.pd, w.pAx, st, &lmin, c.nb);
   c.schur_lmax = lm;
   // Ritz values converge from inside the spectrum: widen the lower end, keep it positive
   c.schur_lmin = std::max(0.7 * lmin, lm / 200.0);
   c.schur_lmax_tau = tau;
   return lm;
+}
+
+// Jacobi diagonal of every column and the lumped Schur stencil of every instance for this tau
+template <typename T>
+void schur_prepare(biot_ctx& c, double tau, cudaStream_t st) {
+  PrecWork<T>& w = c.pw<T>();
+  const Grid& g = c.g;
+  const int64_t nqt = g.nq[0] + g.nq[1] + g.nq[2];
+  double cm_all[MAXR];
+  schur_cm(c, cm_all);
+  launch_schur_dinv<T>(g, c.tab<T>(), c.sb2<T>(), cm_all, tau, w.pdinv, c.nt * c.nb, st);
+  for (int b = 0; b < c.nb; ++b)
+    launch_schur_stencil<T>(g, c.tab<T>(), c.dmq<T>() + b * nqt, tau, w.scoef + (int64_t)b * 16 * g.Np, st);
+  CKL();
 }
 
 // p = Shat^{-1} g by Chebyshev-Jacobi (w.gp -> w.pp)
@@ -724,15 +806,13 @@ void schur_solve(biot_ctx& c, double tau, cudaStream_t st, int k0, int nk) {
   ChebCoef cc = cheb_coefs(c.opts.schur_degree, c.schur_lmin, 1.1 * lmax);
   if (c.lumped_flux) {
     if (w.schur_tau != tau) {  // stencil and diagonal of this tau (prec_prepare normally did this)
-      launch_schur_dinv<T>(g, c.tab<T>(), c.sb2<T>(), cm_all, tau, w.pdinv, c.nt, st);
-      launch_schur_stencil<T>(g, c.tab<T>(), c.dmq<T>(), tau, w.scoef, st);
-      CKL();
+      schur_prepare<T>(c, tau, st);
       w.schur_tau = tau;
     }
-    const T* dinv = w.pdinv + (int64_t)k0 * g.Np;
+    const T* dinv = w.pdinv + (int64_t)k0 * c.nb * g.Np;
     for (int k = 0; k < cc.n; ++k) {
-      launch_schur_cheb_st<T>(g, c.tab<T>(), w.scoef, dinv, cm, cc.c1[k], cc.c2[k], k == 0 ? 1 : 0, w.gp, w.pp, w.pd, w.pxo, nk,
-                              st);
+      launch_schur_cheb_st<T>(g, c.tab<T>(), w.scoef, dinv, cm, cc.c1[k], cc.c2[k], k == 0 ? 1 : 0, w.gp, w.pp, w.pd, w.pxo,
+                              nk * c.nb, st);
       CKL();
       std::swap(w.pp, w.pxo);
     }
@@ -764,18 +844,20 @@ void block_solve(biot_ctx& c, double tau, int k0, int nk, cudaStream_t st) {
   const int64_t N = g.N, Nu = g.Nu, Np = g.Np;
   const int64_t nqt = g.nq[0] + g.nq[1] + g.nq[2];
   LevelWork<T>& lw = lwork<T>(c.lv[0]);
-  T* tA = w.tA + (int64_t)k0 * N;
-  T* tB = w.tB + (int64_t)k0 * N;
-  flux_solve<T>(c, tau, tA + Nu, N, nullptr, 0.0, w.fq, nqt, nk, st);
-  launch_p_minus_Bq<T>(g, c.tab<T>(), tA + g.offp, N, w.fq, nqt, tau, w.gp, Np, nk, st);
+  // levels k0 .. k0+nk-1 of every instance are the consecutive columns from k0 * nb on
+  const int cols = nk * c.nb;
+  T* tA = w.tA + (int64_t)k0 * c.lvN();
+  T* tB = w.tB + (int64_t)k0 * c.lvN();
+  flux_solve<T>(c, tau, tA + Nu, N, nullptr, 0.0, w.fq, nqt, cols, st);
+  launch_p_minus_Bq<T>(g, c.tab<T>(), tA + g.offp, N, w.fq, nqt, tau, w.gp, Np, cols, st);
   CKL();
   schur_solve<T>(c, tau, st, k0, nk);
-  flux_solve<T>(c, tau, tA + Nu, N, w.pp, tau, tB + Nu, N, nk, st);
-  copy2d<T>(tB + g.offp, N, w.pp, Np, Np, nk, st);
-  launch_u_rhs<T>(g, c.tab<T>(), tA, N, w.pp, Np, c.b * tau, lw.b, Nu, nk, st);
+  flux_solve<T>(c, tau, tA + Nu, N, w.pp, tau, tB + Nu, N, cols, st);
+  copy2d<T>(tB + g.offp, N, w.pp, Np, Np, cols, st);
+  launch_u_rhs<T>(g, c.tab<T>(), tA, N, w.pp, Np, c.b * tau, lw.b, Nu, cols, st);
   CKL();
-  vcycle<T>(c, tau, nk, st);
-  copy2d<T>(tB, N, lw.x, Nu, Nu, nk, st);
+  vcycle<T>(c, tau, cols, st);
+  copy2d<T>(tB, N, lw.x, Nu, Nu, cols, st);
 }
 
 // z = P r  (or P^T r)
@@ -788,13 +870,20 @@ void precondition_T(biot_ctx& c, double tau, const T* R, T* Z, int transpose, cu
   const int64_t nqt = g.nq[0] + g.nq[1] + g.nq[2];
   Level& L0 = c.lv[0];
   LevelWork<T>& lw = lwork<T>(L0);
+  // the Schur eigenvalue bounds use the FP64 flow-block buffers: obtain them before any of
+  // those buffers holds data of this application (a no-op once cached for this tau)
+  (void)schur_lmax(c, tau, st);
   double Wm[MAXR * MAXR], Vm[MAXR * MAXR];
   for (int a = 0; a < nt; ++a)
     for (int b = 0; b < nt; ++b) {
       Wm[a * nt + b] = transpose ? c.tb.V[b][a] : c.tb.W[a][b];
       Vm[a * nt + b] = transpose ? c.tb.W[b][a] : c.tb.V[a][b];
     }
-  launch_time_mix<T, T>(R, N, w.tA, N, nt, Wm, N, st);
+  // the time transform mixes the levels of each DoF: with level-major batched vectors
+  // the instances just extend the spatial index (nb * N entries per level)
+  const int64_t LN = c.lvN();
+  const int cols = nt * c.nb;
+  launch_time_mix<T, T>(R, LN, w.tA, LN, nt, Wm, LN, st);
   CKL();
   if (!transpose) {
     const int p0 = c.tb.pair;
@@ -803,31 +892,32 @@ void precondition_T(biot_ctx& c, double tau, const T* R, T* Z, int transpose, cu
       // [[L, beta S], [-beta S, L]]: y_p0 = L^{-1} r_p0, y_p0+1 = L^{-1} (r_p0+1 + beta S y_p0)
       block_solve<T>(c, tau, 0, p0 + 1, st);
       const double beta = c.tb.pair_beta;
-      T* r1 = w.tA + (int64_t)(p0 + 1) * N;
-      const T* y0 = w.tB + (int64_t)p0 * N;
-      launch_p_plus_ETu<T>(g, c.tab<T>(), r1 + g.offp, N, y0, N, beta * c.b, r1 + g.offp, N, 1, st);
+      T* r1 = w.tA + (int64_t)(p0 + 1) * LN;
+      const T* y0 = w.tB + (int64_t)p0 * LN;
+      launch_p_plus_ETu<T>(g, c.tab<T>(), r1 + g.offp, N, y0, N, beta * c.b, r1 + g.offp, N, c.nb, st);
       double mp = 1.0;
       for (int d = 0; d < g.dim; ++d) mp *= c.t64.wg[d];
-      launch_axpby<T>(r1 + g.offp, y0 + g.offp, beta * c.invM * mp, 1.0, Np, st);
+      if (c.nb == 1) launch_axpby<T>(r1 + g.offp, y0 + g.offp, beta * c.invM * mp, 1.0, Np, st);
+      else launch_axpby_rows<T>(r1 + g.offp, y0 + g.offp, beta * c.invM * mp, 1.0, Np, c.nb, N, st);
       CKL();
       block_solve<T>(c, tau, p0 + 1, nt - p0 - 1, st);
     } else {
       block_solve<T>(c, tau, 0, nt, st);
     }
   } else {
-    copy2d<T>(lw.b, Nu, w.tA, N, Nu, nt, st);
-    vcycle<T>(c, tau, nt, st);
-    copy2d<T>(w.tB, N, lw.x, Nu, Nu, nt, st);
-    launch_p_plus_ETu<T>(g, c.tab<T>(), w.tA + g.offp, N, lw.x, Nu, c.b * tau, w.gp, Np, nt, st);
+    copy2d<T>(lw.b, Nu, w.tA, N, Nu, cols, st);
+    vcycle<T>(c, tau, cols, st);
+    copy2d<T>(w.tB, N, lw.x, Nu, Nu, cols, st);
+    launch_p_plus_ETu<T>(g, c.tab<T>(), w.tA + g.offp, N, lw.x, Nu, c.b * tau, w.gp, Np, cols, st);
     CKL();
-    flux_solve<T>(c, tau, w.tA + Nu, N, nullptr, 0.0, w.fq, nqt, nt, st);
-    launch_p_minus_Bq<T>(g, c.tab<T>(), w.gp, Np, w.fq, nqt, -tau, w.gp, Np, nt, st);
+    flux_solve<T>(c, tau, w.tA + Nu, N, nullptr, 0.0, w.fq, nqt, cols, st);
+    launch_p_minus_Bq<T>(g, c.tab<T>(), w.gp, Np, w.fq, nqt, -tau, w.gp, Np, cols, st);
     CKL();
     schur_solve<T>(c, tau, st, 0, nt);
-    flux_solve<T>(c, tau, w.tA + Nu, N, w.pp, -tau, w.tB + Nu, N, nt, st);
-    copy2d<T>(w.tB + g.offp, N, w.pp, Np, Np, nt, st);
+    flux_solve<T>(c, tau, w.tA + Nu, N, w.pp, -tau, w.tB + Nu, N, cols, st);
+    copy2d<T>(w.tB + g.offp, N, w.pp, Np, Np, cols, st);
   }
-  launch_time_mix<T, T>(w.tB, N, Z, N, nt, Vm, N, st);
+  launch_time_mix<T, T>(w.tB, LN, Z, LN, nt, Vm, LN, st);
   CKL();
 }
 
@@ -843,6 +933,16 @@ void arnoldi_step_body(biot_ctx& c, double tau, int transpose, int j, cudaStream
   precondition_T<T>(c, tau, K.V[j], K.Z[j], transpose, st);
   apply_slab_T<T>(c, tau, K.Z[j], K.V[j + 1], transpose, st);
   T* w = K.V[j + 1];
+  if (c.nb > 1) {
+    // batched instances: every reduction and scalar per instance (block of HS scalars each)
+    const Seg sg = slab_seg(c);
+    launch_seg_multidot<T>(K.dV, j + 1, w, sg, c.partial, hd, HS, st);
+    launch_seg_multiaxpy_dot<T>(K.dV, j + 1, hd, HS, w, sg, 1, c.partial, hd + 64, HS, st);
+    launch_seg_multiaxpy_dot<T>(K.dV, j + 1, hd + 64, HS, w, sg, 2, c.partial, hd + 128, HS, st);
+    launch_seg_scale<T>(w, w, hd + 129, HS, sg, st);
+    CKL();
+    return;
+  }
   launch_multidot<T>(K.dV, j + 1, w, n, c.partial, hd, st);
   launch_multiaxpy_dot<T>(K.dV, j + 1, hd, w, n, 1, c.partial, hd + 64, st);
   launch_multiaxpy_dot<T>(K.dV, j + 1, hd + 64, w, n, 2, c.partial, hd + 128, st);
@@ -862,11 +962,7 @@ void prec_prepare(biot_ctx& c, double tau, cudaStream_t st) {
   double lm = schur_lmax(c, tau, st);
   (void)lm;
   if (w.schur_tau != tau) {
-    double cm[MAXR];
-    schur_cm(c, cm);
-    launch_schur_dinv<T>(c.g, c.tab<T>(), c.sb2<T>(), cm, tau, w.pdinv, c.nt, st);
-    launch_schur_stencil<T>(c.g, c.tab<T>(), c.dmq<T>(), tau, w.scoef, st);
-    CKL();
+    schur_prepare<T>(c, tau, st);
     w.schur_tau = tau;
   }
 }
@@ -988,6 +1084,215 @@ int gmres(biot_ctx& c, double tau, int transpose, const T* b, T* x, double tol_a
   }
 }
 
+// ---- batched solves ------------------------------------------------------------------
+// Per-instance scalars round trip through the pinned bhost / device bdev columns: the
+// first 4 nt nb entries serve the eigenvalue estimates, then slots of nb values each.
+int64_t bslot(const biot_ctx& c, int slot) { return 4 * (int64_t)c.nt * c.nb + (int64_t)slot * c.nb; }
+int64_t bdev_doubles(int nt, int nb) { return 4 * (int64_t)nt * nb + 10 * (int64_t)nb + 64; }
+void put_scalars(biot_ctx& c, const std::vector<double>& v, int slot, cudaStream_t st) {
+  // callers synchronise the stream before rewriting a slot
+  std::memcpy(c.bhost + bslot(c, slot), v.data(), c.nb * sizeof(double));
+  CK(cudaMemcpyAsync(c.bdev + bslot(c, slot), c.bhost + bslot(c, slot), c.nb * sizeof(double), cudaMemcpyHostToDevice, st));
+}
+
+// per-instance squared norms of a batched slab vector (synchronises st)
+template <typename T>
+std::vector<double> seg_norms2(biot_ctx& c, const T* v, int slot, cudaStream_t st) {
+  c.hptr[16 + slot] = (void*)v;
+  CK(cudaMemcpyAsync(c.ptrbuf + 16 + slot, c.hptr + 16 + slot, sizeof(void*), cudaMemcpyHostToDevice, st));
+  launch_seg_multidot<T>(reinterpret_cast<const T* const*>(c.ptrbuf + 16 + slot), 1, v, slab_seg(c), c.partial,
+                         c.bdev + bslot(c, 8), 1, st);
+  CKL();
+  CK(cudaMemcpyAsync(c.bhost + bslot(c, 8), c.bdev + bslot(c, 8), c.nb * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return std::vector<double>(c.bhost + bslot(c, 8), c.bhost + bslot(c, 9));
+}
+
+// One cycle of right-preconditioned FGMRES for every batched instance at once (x = 0 on
+// entry).  All instances share the Arnoldi steps (each a graph of batch-wide launches);
+// each keeps its own Hessenberg matrix, Givens rotations and stopping point: an instance
+// stops contributing once its residual estimate falls below tol_abs[b] (inactive
+// instances enter with b = 0 and stay at x = 0).  iters[b] counts the steps it used.
+template <typename T>
+void gmres_batch(biot_ctx& c, double tau, int transpose, const T* b, T* x, const std::vector<double>& tol_abs, int maxit,
+                 std::vector<int>& iters, cudaStream_t st) {
+  const int m = c.opts.gmres_restart;
+  const int nb = c.nb;
+  ensure_krylov<T>(c, m);
+  prec_prepare<T>(c, tau, st);
+  Krylov<T>& K = c.kry<T>();
+  const int64_t n = c.g.N * c.nt * nb;
+  const Seg sg = slab_seg(c);
+  double* hd = c.hdev;
+  CK(cudaMemcpyAsync(K.V[0], b, n * sizeof(T), cudaMemcpyDeviceToDevice, st));
+  launch_seg_multidot<T>(K.dV, 1, K.V[0], sg, c.partial, hd + 128, HS, st);
+  CKL();
+  CK(cudaMemcpy2DAsync(c.hhost, HS * sizeof(double), hd, HS * sizeof(double), 130 * sizeof(double), nb,
+                       cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  std::vector<double> beta(nb), scale(nb, 0.0);
+  std::vector<char> alive(nb, 0);
+  for (int i = 0; i < nb; ++i) {
+    beta[i] = std::sqrt(std::max(c.hhost[(int64_t)i * HS + 128], 0.0));
+    if (beta[i] > 0 && std::isfinite(beta[i]) && beta[i] > tol_abs[i]) {
+      alive[i] = 1;
+      scale[i] = 1.0 / beta[i];
+    }
+  }
+  put_scalars(c, scale, 0, st);
+  launch_seg_scale<T>(K.V[0], K.V[0], c.bdev + bslot(c, 0), 1, sg, st);
+  CKL();
+  std::vector<double> H((size_t)nb * (m + 1) * m, 0.0), cs((size_t)nb * m), sn((size_t)nb * m), gv((size_t)nb * (m + 1), 0.0);
+  std::vector<int> jl(nb, -1);
+  for (int i = 0; i < nb; ++i) gv[(size_t)i * (m + 1)] = alive[i] ? beta[i] : 0.0;
+  int steps = 0;
+  for (int j = 0; j < m && steps < maxit; ++j) {
+    bool any = false;
+    for (int i = 0; i < nb; ++i) any = any || alive[i];
+    if (!any) break;
+    arnoldi_step<T>(c, tau, transpose, j, st);
+    CK(cudaMemcpy2DAsync(c.hhost, HS * sizeof(double), hd, HS * sizeof(double), 130 * sizeof(double), nb,
+                         cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    ++steps;
+    for (int ib = 0; ib < nb; ++ib) {
+      if (!alive[ib]) continue;
+      const double* hh = c.hhost + (int64_t)ib * HS;
+      double* Hb = H.data() + (size_t)ib * (m + 1) * m;
+      double* csb = cs.data() + (size_t)ib * m;
+      double* snb = sn.data() + (size_t)ib * m;
+      double* gb = gv.data() + (size_t)ib * (m + 1);
+      for (int i = 0; i <= j; ++i) Hb[i * m + j] = hh[i] + hh[64 + i];
+      double hn = std::sqrt(std::max(hh[128], 0.0));
+      if (!std::isfinite(hn)) { alive[ib] = 0; continue; }
+      Hb[(j + 1) * m + j] = hn;
+      for (int i = 0; i < j; ++i) {
+        double a = Hb[i * m + j], bb = Hb[(i + 1) * m + j];
+        Hb[i * m + j] = csb[i] * a + snb[i] * bb;
+        Hb[(i + 1) * m + j] = -snb[i] * a + csb[i] * bb;
+      }
+      double a = Hb[j * m + j], bb = Hb[(j + 1) * m + j];
+      double rr = std::hypot(a, bb);
+      csb[j] = (rr > 0) ? a / rr : 1.0;
+      snb[j] = (rr > 0) ? bb / rr : 0.0;
+      Hb[j * m + j] = rr;
+      Hb[(j + 1) * m + j] = 0.0;
+      gb[j + 1] = -snb[j] * gb[j];
+      gb[j] = csb[j] * gb[j];
+      ++iters[ib];
+      jl[ib] = j;
+      if (std::fabs(gb[j + 1]) <= tol_abs[ib] || hn == 0.0) alive[ib] = 0;
+    }
+  }
+  // y_b = H_b^{-1} g_b per instance, x += Z y (coefficients beyond an instance's last step are 0)
+  int jmax = -1;
+  for (int ib = 0; ib < nb; ++ib) jmax = std::max(jmax, jl[ib]);
+  if (jmax < 0) return;
+  for (int ib = 0; ib < nb; ++ib) {
+    double* yb = c.hhost + (int64_t)ib * HS + 160;
+    for (int i = 0; i <= jmax; ++i) yb[i] = 0.0;
+    const double* Hb = H.data() + (size_t)ib * (m + 1) * m;
+    const double* gb = gv.data() + (size_t)ib * (m + 1);
+    for (int i = jl[ib]; i >= 0; --i) {
+      double s = gb[i];
+      for (int k = i + 1; k <= jl[ib]; ++k) s -= Hb[i * m + k] * yb[k];
+      yb[i] = (Hb[i * m + i] != 0.0) ? s / Hb[i * m + i] : 0.0;
+    }
+  }
+  CK(cudaMemcpy2DAsync(hd + 160, HS * sizeof(double), c.hhost + 160, HS * sizeof(double), (jmax + 1) * sizeof(double), nb,
+                       cudaMemcpyHostToDevice, st));
+  launch_seg_lincomb_add<T, T>(x, K.dV + (m + 1), jmax + 1, hd + 160, HS, sg, st);
+  CKL();
+  CK(cudaStreamSynchronize(st));  // hhost is rewritten by the next call
+}
+
+// Mixed-precision refinement of every batched instance (FP64 true residual and update,
+// one FP32 FGMRES cycle per refinement step), each to its own relative tolerance.
+// Per-instance results go to c.it_b / c.ref_b / c.res_b / c.rc_b.
+int solve_slab_batch(biot_ctx& c, double tau, const double* rhs, double* x, const biot_solve_opts& o, biot_stats& s,
+                     cudaStream_t st) {
+  double t0 = now_s();
+  const int nb = c.nb;
+  const int64_t n = c.g.N * c.nt * nb;
+  const Seg sg = slab_seg(c);
+  if (o.mode != BIOT_MIXED) fail(BIOT_EINVAL, "batched contexts solve in BIOT_MIXED mode");
+  c.it_b.assign(nb, 0);
+  c.ref_b.assign(nb, 0);
+  c.res_b.assign(nb, 0.0);
+  c.rc_b.assign(nb, BIOT_OK);
+  std::vector<double> bn = seg_norms2<double>(c, rhs, 0, st);
+  for (double& v : bn) v = std::sqrt(v);
+  for (int i = 0; i < nb; ++i)
+    if (!std::isfinite(bn[i])) fail(BIOT_EINVAL, "non-finite right-hand side");
+  if (!c.r64) c.r64 = dalloc<double>(n);
+  if (!c.d32) c.d32 = dalloc<float>(n);
+  if (!c.r32) c.r32 = dalloc<float>(n);
+  {  // instances with a zero right-hand side have the zero solution
+    std::vector<double> keep(nb);
+    for (int i = 0; i < nb; ++i) keep[i] = bn[i] == 0.0 ? 0.0 : 1.0;
+    put_scalars(c, keep, 1, st);
+    launch_seg_scale<double>(x, x, c.bdev + bslot(c, 1), 1, sg, st);
+    CKL();
+  }
+  std::vector<char> done(nb, 0);
+  for (int i = 0; i < nb; ++i) done[i] = bn[i] == 0.0;
+  int refs = 0, total = 0;
+  while (true) {
+    apply_slab_T<double>(c, tau, x, c.r64, o.transpose, st);
+    launch_axpby<double>(c.r64, rhs, 1.0, -1.0, n, st);
+    CKL();
+    std::vector<double> rn = seg_norms2<double>(c, c.r64, 1, st);
+    std::vector<double> sc(nb, 0.0), tol_in(nb, 0.0);
+    bool any = false;
+    for (int i = 0; i < nb; ++i) {
+      rn[i] = std::sqrt(std::max(rn[i], 0.0));
+      if (done[i]) continue;
+      c.res_b[i] = rn[i] / bn[i];
+      if (!std::isfinite(rn[i])) { c.rc_b[i] = BIOT_EBREAKDOWN; done[i] = 1; continue; }
+      if (rn[i] <= o.tol * bn[i]) { done[i] = 1; continue; }
+      if (c.it_b[i] >= o.max_iters || c.ref_b[i] >= 50) { c.rc_b[i] = BIOT_ENOCONV; done[i] = 1; continue; }
+      sc[i] = 1.0 / rn[i];
+      tol_in[i] = o.inner_tol;
+      any = true;
+    }
+    if (!any) break;
+    put_scalars(c, sc, 2, st);
+    launch_seg_scale<double>(c.r64, c.r64, c.bdev + bslot(c, 2), 1, sg, st);
+    launch_convert<double, float>(c.r64, c.r32, n, st);
+    CK(cudaMemsetAsync(c.d32, 0, n * sizeof(float), st));
+    CKL();
+    std::vector<int> it_in(nb, 0);
+    int budget = std::min(o.max_iters, c.opts.gmres_restart);
+    gmres_batch<float>(c, tau, o.transpose, c.r32, c.d32, tol_in, budget, it_in, st);
+    for (int i = 0; i < nb; ++i) {
+      if (sc[i] == 0.0) { rn[i] = 0.0; continue; }
+      c.it_b[i] += it_in[i];
+      c.ref_b[i] += 1;
+      total = std::max(total, c.it_b[i]);
+    }
+    put_scalars(c, rn, 3, st);  // x_b += ||r_b|| d_b (0 for finished instances)
+    launch_seg_add_scaled<double, float>(x, c.d32, c.bdev + bslot(c, 3), 1, sg, st);
+    CKL();
+    ++refs;
+  }
+  CK(cudaStreamSynchronize(st));
+  int rc = BIOT_OK;
+  double worst = 0;
+  int refs_max = 0;
+  for (int i = 0; i < nb; ++i) {
+    if (c.rc_b[i] != BIOT_OK && rc == BIOT_OK) rc = c.rc_b[i];
+    worst = std::max(worst, c.res_b[i]);
+    refs_max = std::max(refs_max, c.ref_b[i]);
+  }
+  s.iterations = total;
+  s.restarts = 0;
+  s.refinements = refs_max;
+  s.rel_residual = worst;
+  s.seconds = now_s() - t0;
+  (void)refs;
+  return rc;
+}
+
 // ---- slab solve ---------------------------------------------------------------------
 int solve_slab_impl(biot_ctx& c, double tau, const double* rhs, double* x, const biot_solve_opts& o, biot_stats& s,
                     cudaStream_t st_user) {
@@ -1004,6 +1309,7 @@ int solve_slab_impl(biot_ctx& c, double tau, const double* rhs, double* x, const
       cudaStreamWaitEvent(su, c.ev_out, 0);
     }
   } rejoin{c, st_user};
+  if (c.nb > 1) return solve_slab_batch(c, tau, rhs, x, o, s, st);
   const int64_t n = c.g.N * c.nt;
   int iters = 0, restarts = 0, refs = 0;
   double res = 0;
@@ -1166,8 +1472,9 @@ void build_levels(biot_ctx& c, cudaStream_t st) {
   }
 }
 
+// K: nb * n_cells values (instance-major for a batched context)
 void set_permeability(biot_ctx& c, const double* K, cudaStream_t st) {
-  const int64_t nc = c.g.ncells;
+  const int64_t nc = c.g.ncells * c.nb;
   std::vector<double> ks(nc);
   std::vector<float> kf(nc);
   for (int64_t i = 0; i < nc; ++i) {
@@ -1176,12 +1483,16 @@ void set_permeability(biot_ctx& c, const double* K, cudaStream_t st) {
     kf[i] = (float)ks[i];
   }
   c.Kcell.assign(K, K + nc);
-  CK(cudaMemcpy(c.kscale64, ks.data(), nc * sizeof(double), cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(c.kscale32, kf.data(), nc * sizeof(float), cudaMemcpyHostToDevice));
-  launch_diag_Mq<double>(c.g, c.t64, c.kscale64, c.dmq64, st);
-  launch_diag_Mq<float>(c.g, c.t32, c.kscale32, c.dmq32, st);
-  launch_diag_BDBt<double>(c.g, c.t64, c.dmq64, c.sb2_64, st);
-  launch_diag_BDBt<float>(c.g, c.t32, c.dmq32, c.sb2_32, st);
+  CK(cudaMemcpyAsync(c.kscale64, ks.data(), nc * sizeof(double), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(c.kscale32, kf.data(), nc * sizeof(float), cudaMemcpyHostToDevice, st));
+  const Grid& g = c.g;
+  const int64_t nqt = g.nq[0] + g.nq[1] + g.nq[2];
+  for (int b = 0; b < c.nb; ++b) {
+    launch_diag_Mq<double>(g, c.t64, c.kscale64 + b * g.ncells, c.dmq64 + b * nqt, st);
+    launch_diag_Mq<float>(g, c.t32, c.kscale32 + b * g.ncells, c.dmq32 + b * nqt, st);
+    launch_diag_BDBt<double>(g, c.t64, c.dmq64 + b * nqt, c.sb2_64 + b * g.Np, st);
+    launch_diag_BDBt<float>(g, c.t32, c.dmq32 + b * nqt, c.sb2_32 + b * g.Np, st);
+  }
   CKL();
   CK(cudaStreamSynchronize(st));
   c.schur_lmax_tau = -1;
@@ -1232,6 +1543,7 @@ void march_prepare(biot_ctx& c, int nterms, const double* const* f_terms, const 
     for (int m = 0; m < 8; ++m) c.m_f[m] = dalloc<double>(g.N);
     c.m_fdev = (const double**)dalloc<double*>(8);
     CK(cudaMemcpy((void*)c.m_fdev, c.m_f, 8 * sizeof(double*), cudaMemcpyHostToDevice));
+    CK(cudaDeviceSynchronize());  // the pageable copy above runs on the legacy stream
     c.m_U = dalloc<double>(g.N);
     c.m_SU = dalloc<double>(g.N);
     c.m_rhs = dalloc<double>(g.N * c.nt);
@@ -1266,7 +1578,7 @@ void build_slab_rhs(biot_ctx& c, double t0, double tau, int nterms, const double
   CKL();
   std::vector<double> coef(c.nt * std::max(1, nterms), 0.0);
   if (nterms) time_load_coefs(c, t0, tau, nterms, tcoef, coef.data());
-  launch_slab_rhs(g, mb.fdev, nterms, coef.data(), c.tb.phi0, c.nt, mb.SU + g.offp, mb.rhs, st);
+  launch_slab_rhs(g, mb.fdev, nterms, coef.data(), c.tb.phi0, c.nt, mb.SU + g.offp, mb.rhs, g.N, st);
   CKL();
 }
 
@@ -1300,6 +1612,90 @@ void march_impl(biot_ctx& c, double T, int slabs, int nterms, const double* cons
   CK(cudaStreamSynchronize(st));
   tot.seconds = now_s() - t_start;
   st_out = tot;
+}
+
+// March every batched instance over the same slabs (paper §Discretisation in Time).
+// Instance b has its own load terms f_terms[b * nterms + m] (n_space each, host or device),
+// initial state U0[b] and end state U_end[b]; the time profiles tcoef are shared.
+void march_batch_impl(biot_ctx& c, double T, int slabs, int nterms, const double* const* f_terms, const double* tcoef,
+                      const double* const* U0, double* const* U_end, const biot_solve_opts& o, int* iters, biot_stats* sb,
+                      int* status, cudaStream_t st) {
+  const Grid& g = c.g;
+  const int nb = c.nb;
+  const int64_t N = g.N, LN = c.lvN();
+  if (nterms < 0 || nterms > 8) fail(BIOT_EINVAL, "nterms must be in 0..8");
+  const int mt = std::max(1, nterms);
+  if (!c.bm_U || c.bm_terms < mt) {
+    if (c.bm_f) cudaFree(c.bm_f);
+    c.bm_f = dalloc<double>((int64_t)nb * mt * N);
+    c.bm_terms = mt;
+  }
+  if (!c.bm_U) {
+    c.bm_fdev = (const double**)dalloc<double*>((int64_t)nb * 8);
+    c.bm_U = dalloc<double>(LN);
+    c.bm_SU = dalloc<double>(LN);
+    c.bm_rhs = dalloc<double>(LN * c.nt);
+    c.bm_X = dalloc<double>(LN * c.nt);
+  }
+  std::vector<const double*> tab((size_t)nb * 8, nullptr);
+  for (int b = 0; b < nb; ++b)
+    for (int m = 0; m < nterms; ++m) {
+      const double* src = f_terms[(size_t)b * nterms + m];
+      if (!src) fail(BIOT_EINVAL, "NULL load term");
+      double* dst = c.bm_f + ((int64_t)b * mt + m) * N;
+      CK(cudaMemcpyAsync(dst, src, N * sizeof(double), is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+      tab[(size_t)b * 8 + m] = dst;
+    }
+  // pageable source: the copy is staged before the call returns and ordered on st
+  CK(cudaMemcpyAsync((void*)c.bm_fdev, tab.data(), tab.size() * sizeof(double*), cudaMemcpyHostToDevice, st));
+  launch_mask<double>(g, c.bm_f, N, nb * mt, st);
+  CKL();
+  for (int b = 0; b < nb; ++b) {
+    const double* u0 = U0 ? U0[b] : nullptr;
+    if (u0) CK(cudaMemcpyAsync(c.bm_U + b * N, u0, N * sizeof(double), is_device_ptr(u0) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    else CK(cudaMemsetAsync(c.bm_U + b * N, 0, N * sizeof(double), st));
+  }
+  CK(cudaStreamSynchronize(st));
+  const double tau = T / slabs;
+  for (int b = 0; b < nb; ++b) {
+    sb[b] = biot_stats{0, 0, 0, 0.0, 0.0};
+    status[b] = BIOT_OK;
+    if (iters) iters[b] = 0;
+  }
+  double t_start = now_s();
+  SlabCoef sj;
+  std::memset(&sj, 0, sizeof(sj));
+  sj.nt = 1;
+  sj.pu[0][0] = c.b;
+  sj.pp[0][0] = c.invM;
+  std::vector<double> coef(c.nt * mt, 0.0);
+  for (int nsl = 0; nsl < slabs; ++nsl) {
+    // right-hand sides: loads integrated over the slab plus the jump term S U(t_{n-1}^-)
+    launch_apply_p<double>(g, c.t64, sj, c.bm_U, N, c.bm_SU, N, st);
+    if (nterms) time_load_coefs(c, nsl * tau, tau, nterms, tcoef, coef.data());
+    for (int b = 0; b < nb; ++b)
+      launch_slab_rhs(g, c.bm_fdev + (size_t)b * 8, nterms, coef.data(), c.tb.phi0, c.nt, c.bm_SU + b * N + g.offp,
+                      c.bm_rhs + b * N, LN, st);
+    CKL();
+    for (int k = 0; k < c.nt; ++k) CK(cudaMemcpyAsync(c.bm_X + k * LN, c.bm_U, LN * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    biot_stats s;
+    solve_slab_impl(c, tau, c.bm_rhs, c.bm_X, o, s, st);
+    for (int b = 0; b < nb; ++b) {
+      sb[b].iterations += c.it_b[b];
+      sb[b].refinements += c.ref_b[b];
+      sb[b].rel_residual = std::max(sb[b].rel_residual, c.res_b[b]);
+      if (iters) iters[b] += c.it_b[b];
+      if (c.rc_b[b] != BIOT_OK && status[b] == BIOT_OK) status[b] = c.rc_b[b];  // first failing slab's code
+    }
+    CK(cudaMemcpyAsync(c.bm_U, c.bm_X + (int64_t)(c.nt - 1) * LN, LN * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  }
+  for (int b = 0; b < nb; ++b)
+    if (U_end && U_end[b])
+      CK(cudaMemcpyAsync(U_end[b], c.bm_U + b * N, N * sizeof(double),
+                         is_device_ptr(U_end[b]) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  const double secs = now_s() - t_start;
+  for (int b = 0; b < nb; ++b) sb[b].seconds = secs;
 }
 
 biot_solve_opts solve_defaults(const biot_solve_opts* o) {
@@ -1338,11 +1734,14 @@ biot_solve_opts solve_defaults(const biot_solve_opts* o) {
     return BIOT_ENOMEM;                               \
   }
 
-extern "C" int biot_setup(const biot_mesh* mesh, const biot_coeffs* co, int r, const biot_opts* opts, biot_t* out) {
+namespace {
+int setup_impl(const biot_mesh* mesh, const biot_coeffs* co, int r, const biot_opts* opts, int nb, biot_t* out) {
   if (!out || !mesh || !co) return BIOT_EINVAL;
   *out = nullptr;
   biot_ctx* c = new biot_ctx();
   try {
+    if (nb < 1 || nb > 4096) fail(BIOT_EINVAL, "batch size must be in 1..4096");
+    c->nb = nb;
     if (mesh->dim != 2 && mesh->dim != 3) fail(BIOT_EINVAL, "dim must be 2 or 3");
     for (int d = 0; d < mesh->dim; ++d) {
       if (mesh->n[d] < 1) fail(BIOT_EINVAL, "n must be >= 1");
@@ -1363,6 +1762,7 @@ extern "C" int biot_setup(const biot_mesh* mesh, const biot_coeffs* co, int r, c
       c->use_graphs = !(ng && ng[0] == '1');
     }
     c->g = make_grid(mesh->dim, mesh->n, mesh->lo, mesh->hi, mesh->u_bc, mesh->f_bc);
+    c->g.nb = nb;
     c->r = r;
     c->nt = r + 1;
     c->b = co->b;
@@ -1390,29 +1790,33 @@ extern "C" int biot_setup(const biot_mesh* mesh, const biot_coeffs* co, int r, c
     }
     c->opts = d;
     c->lumped_flux = d.flux_mass_exact ? 0 : 1;
+    if (nb > 1 && !c->lumped_flux) fail(BIOT_EINVAL, "batched contexts use the lumped Darcy mass (flux_mass_exact = 0)");
     c->beta = (d.beta_fs > 0) ? d.beta_fs : c->b * c->b / c->Kdr;
     build_tables(c->g, c->t64);
     c->t32 = cast_tables<float>(c->t64);
     c->tb = make_time_basis(r);
     const Grid& g = c->g;
     int64_t nqt = g.nq[0] + g.nq[1] + g.nq[2];
-    c->kscale64 = dalloc<double>(g.ncells);
-    c->kscale32 = dalloc<float>(g.ncells);
-    c->dmq64 = dalloc<double>(nqt);
-    c->dmq32 = dalloc<float>(nqt);
-    c->sb2_64 = dalloc<double>(g.Np);
-    c->sb2_32 = dalloc<float>(g.Np);
-    c->hdev = dalloc<double>(512);
+    c->kscale64 = dalloc<double>(g.ncells * nb);
+    c->kscale32 = dalloc<float>(g.ncells * nb);
+    c->dmq64 = dalloc<double>(nqt * nb);
+    c->dmq32 = dalloc<float>(nqt * nb);
+    c->sb2_64 = dalloc<double>(g.Np * nb);
+    c->sb2_32 = dalloc<float>(g.Np * nb);
+    c->hdev = dalloc<double>((int64_t)HS * nb + 256);
+    c->bdev = dalloc<double>(bdev_doubles(c->nt, nb));
     CK(cudaStreamCreateWithFlags(&c->ws, cudaStreamNonBlocking));
     CK(cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming));
     c->ptrbuf = dalloc<void*>(64);
     CK(cudaMallocHost((void**)&c->hptr, 64 * sizeof(void*)));
-    CK(cudaMallocHost((void**)&c->hhost, 512 * sizeof(double)));
-    c->partial = dalloc<double>(RED_BLOCKS * 16);
+    CK(cudaMallocHost((void**)&c->hhost, ((int64_t)HS * nb + 256) * sizeof(double)));
+    CK(cudaMallocHost((void**)&c->bhost, bdev_doubles(c->nt, nb) * sizeof(double)));
+    c->partial = dalloc<double>(
+        std::max<int64_t>(RED_BLOCKS * 16, std::max(seg_partial_doubles(c->nt * nb), seg_partial_doubles(nb))));
     c->lvl64 = dalloc<double>(g.N);
     c->lvl64b = dalloc<double>(g.N);
-    cudaStream_t st = 0;
+    cudaStream_t st = 0;  // set-up runs on the legacy stream, ordered with its synchronous copies
     set_permeability(*c, co->K_cell, st);
     build_levels(*c, st);
     CK(cudaStreamSynchronize(st));
@@ -1426,6 +1830,16 @@ extern "C" int biot_setup(const biot_mesh* mesh, const biot_coeffs* co, int r, c
   }
   *out = c;
   return BIOT_OK;
+}
+}  // namespace
+
+extern "C" int biot_setup(const biot_mesh* mesh, const biot_coeffs* co, int r, const biot_opts* opts, biot_t* out) {
+  return setup_impl(mesh, co, r, opts, 1, out);
+}
+
+extern "C" int biot_setup_batch(const biot_mesh* mesh, const biot_coeffs* co, int r, const biot_opts* opts, int nb,
+                                biot_t* out) {
+  return setup_impl(mesh, co, r, opts, nb, out);
 }
 
 extern "C" int biot_sizes(biot_t c, int64_t* n_space, int64_t* n_slab, int64_t* n_cells) {
@@ -1490,6 +1904,7 @@ extern "C" int biot_march(biot_t c, double T, int slabs, int nterms, const doubl
   API_BEGIN(c)
   if (!(T > 0) || slabs < 1) fail(BIOT_EINVAL, "march: T must be > 0 and slabs >= 1");
   if (nterms > 0 && (!f_terms || !tcoef)) fail(BIOT_EINVAL, "march: load terms missing");
+  if (c->nb > 1) fail(BIOT_EINVAL, "march: batched context (use biot_march_batch)");
   biot_solve_opts o = solve_defaults(opts);
   biot_stats s{0, 0, 0, 0.0, 0.0};
   int rc = BIOT_OK;
@@ -1499,11 +1914,43 @@ extern "C" int biot_march(biot_t c, double T, int slabs, int nterms, const doubl
   API_END(c)
 }
 
+extern "C" int biot_march_batch(biot_t c, double T, int slabs, int nterms, const double* const* f_terms, const double* tcoef,
+                                const double* const* U0, double* const* U_end, const biot_solve_opts* opts, int* iters,
+                                biot_stats* stats, int* status, void* stream) {
+  API_BEGIN(c)
+  if (!(T > 0) || slabs < 1) fail(BIOT_EINVAL, "march: T must be > 0 and slabs >= 1");
+  if (nterms > 0 && (!f_terms || !tcoef)) fail(BIOT_EINVAL, "march: load terms missing");
+  biot_solve_opts o = solve_defaults(opts);
+  if (c->nb > 1 && o.mode != BIOT_MIXED) fail(BIOT_EINVAL, "batched contexts solve in BIOT_MIXED mode");
+  if (o.transpose) fail(BIOT_EINVAL, "march: transpose is not a forward march");
+  std::vector<biot_stats> sb(c->nb);
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc = BIOT_OK;
+  if (c->nb == 1) {
+    march_impl(*c, T, slabs, nterms, f_terms, tcoef, U0 ? U0[0] : nullptr, U_end ? U_end[0] : nullptr, nullptr, nullptr, o,
+               nullptr, sb[0], st, rc);
+    if (iters) iters[0] = sb[0].iterations;
+    if (status) status[0] = rc;
+  } else {
+    std::vector<int> code(c->nb, BIOT_OK);
+    march_batch_impl(*c, T, slabs, nterms, f_terms, tcoef, U0, U_end, o, iters, sb.data(), code.data(), st);
+    for (int b = 0; b < c->nb; ++b) {
+      if (status) status[b] = code[b];
+      if (code[b] != BIOT_OK && rc == BIOT_OK) rc = code[b];
+    }
+  }
+  if (stats)
+    for (int b = 0; b < c->nb; ++b) stats[b] = sb[b];
+  return rc;
+  API_END(c)
+}
+
 extern "C" int biot_adjoint_grad(biot_t c, double T, int slabs, int nterms, const double* const* f_terms, const double* tcoef,
                                  const double* U0, const double* j_goal, const biot_solve_opts* opts, int recompute,
                                  double* J_out, double* dJ, void* stream) {
   API_BEGIN(c)
   if (!(T > 0) || slabs < 1 || !j_goal || !dJ) fail(BIOT_EINVAL, "adjoint_grad: bad arguments");
+  if (c->nb > 1) fail(BIOT_EINVAL, "adjoint_grad: batched context");
   cudaStream_t st = (cudaStream_t)stream;
   biot_solve_opts o = solve_defaults(opts);
   const Grid& g = c->g;
@@ -1814,13 +2261,6 @@ bool ctx_view(biot_t c, CtxView* v) {
 void ctx_set_error(biot_t c, const char* msg) {
   if (c) c->err = msg ? msg : "";
 }
-// batched solves drive many contexts from several host threads: no stream capture there
-void ctx_disable_graphs(biot_t c) {
-  if (!c) return;
-  for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second.exec);
-  c->graphs.clear();
-  c->use_graphs = false;
-}
 }  // namespace biot
 
 extern "C" const char* biot_last_error(biot_t c) {
@@ -1834,6 +2274,8 @@ extern "C" void biot_destroy(biot_t c) {
   F(c->kscale64); F(c->kscale32); F(c->dmq64); F(c->dmq32); F(c->sb2_64); F(c->sb2_32);
   F(c->hdev); F(c->partial); F(c->r64); F(c->a64); F(c->d32); F(c->r32); F(c->lvl64); F(c->lvl64b); F(c->Ainv);
   if (c->hhost) cudaFreeHost(c->hhost);
+  if (c->bhost) cudaFreeHost(c->bhost);
+  F(c->bdev);
   if (c->hptr) cudaFreeHost(c->hptr);
   F(c->ptrbuf);
   for (Level& L : c->lv) {
@@ -1856,5 +2298,6 @@ extern "C" void biot_destroy(biot_t c) {
   for (void* p : c->extra) F(p);
   for (int m = 0; m < 8; ++m) F(c->m_f[m]);
   F((void*)c->m_fdev); F(c->m_U); F(c->m_SU); F(c->m_rhs); F(c->m_X);
+  F(c->bm_f); F((void*)c->bm_fdev); F(c->bm_U); F(c->bm_SU); F(c->bm_rhs); F(c->bm_X);
   delete c;
 }

@@ -67,6 +67,7 @@ __global__ void __launch_bounds__(256) k_add_Ep(Grid g, TabT<T> tb, SlabCoef sc,
   const int iy = (int)(rr % g.nu[1]);
   const int iz = DIM == 3 ? (int)(rr / g.nu[1]) : 0;
   const EpNode<T, DIM> en(g, tb, ix, iy, iz);
+  const int b = blockIdx.y, nb = g.nb;  // instance of a batched grid
   T s[MAXR][DIM];  // s[k][c] = sum_l ep[k][l] (E_c p_l)
 #pragma unroll
   for (int k = 0; k < MAXR; ++k)
@@ -75,7 +76,7 @@ __global__ void __launch_bounds__(256) k_add_Ep(Grid g, TabT<T> tb, SlabCoef sc,
 #pragma unroll 1
   for (int l = 0; l < sc.nt; ++l) {
     T e[DIM];
-    en.eval(g, p_in + l * sp, e);
+    en.eval(g, p_in + (int64_t)(l * nb + b) * sp, e);
 #pragma unroll
     for (int k = 0; k < MAXR; ++k) {
       const T w = T(l == 0 ? sc.ep[k][0] : (l == 1 ? sc.ep[k][1] : sc.ep[k][2]));
@@ -89,7 +90,7 @@ __global__ void __launch_bounds__(256) k_add_Ep(Grid g, TabT<T> tb, SlabCoef sc,
     if (!u_free_mask(u_face_mask(g, c), ix, iy, iz, g.nu[0], g.nu[1], g.nu[2])) continue;
 #pragma unroll
     for (int k = 0; k < MAXR; ++k)
-      if (k < sc.nt) y[k * sy + c * nn + node] += s[k][c];
+      if (k < sc.nt) y[(int64_t)(k * nb + b) * sy + c * nn + node] += s[k][c];
   }
 }
 
@@ -179,7 +180,7 @@ __global__ void __launch_bounds__(U3_THREADS, ALLJ ? 2 : 1) k_apply_u3_col(Grid 
   for (int i = tid; i < 3 * 4 * 4 * 5; i += U3_THREADS) (&s_tab[0][0][0][0])[i] = (&tb.q2[0][0][0][0])[i];
   const int nx = g.nu[0], ny = g.nu[1], nz = g.nu[2];
   const int ntz = (nz + T3 - 1) / T3;
-  const int k = blockIdx.z / ntz;
+  const int k = blockIdx.z / ntz;  // column (temporal level x instance, level-major)
   const int X0 = blockIdx.x * T3, Y0 = blockIdx.y * T3, Z0 = (blockIdx.z - k * ntz) * T3;
   const T cf0 = T(2.0 * sc.mu + sc.lam), cf1 = T(sc.mu), cf2 = T(sc.lam);
   const int64_t nn = g.nnode;
@@ -285,7 +286,7 @@ __global__ void __launch_bounds__(U3_THREADS, ALLJ ? 2 : 1) k_apply_u3_col(Grid 
       for (int o = 0; o < 8; ++o) acc[o] += o8[o];
     }
     const int fm = c == 0 ? fm0 : (c == 1 ? fm1 : fm2);
-    const T au = T(sc.au[k]);
+    const T au = T(sc.au[k / sc.udiv]);
 #pragma unroll
     for (int o = 0; o < 8; ++o) {
       const int gx = X0 + o;
@@ -316,9 +317,9 @@ __global__ void __launch_bounds__(256) k_apply_u2(Grid g, TabT<T> tb, SlabCoef s
   const int rx = ex + 4, ry = ey + 4;
   const T cf[3] = {T(2.0 * sc.mu + sc.lam), T(sc.mu), T(sc.lam)};
   const int64_t nn = g.nnode;
-  for (int k = 0; k < sc.nt; ++k) {
+  {
+    const int k = blockIdx.z;  // column (temporal level x instance, level-major)
     const T* u = u_in + k * su;
-    __syncthreads();
     for (int i = tid; i < 2 * rx * ry; i += nth) {
       int c = i / (rx * ry);
       int rem = i - c * rx * ry;
@@ -359,7 +360,7 @@ __global__ void __launch_bounds__(256) k_apply_u2(Grid g, TabT<T> tb, SlabCoef s
           T acc = 0;
 #pragma unroll
           for (int op = 0; op < 4; ++op) acc += tap5(s_tab[0][op][rt], &s_px[c * 4 + op][ly * H2 + lx], 1);
-          out = T(sc.au[k]) * acc;
+          out = T(sc.au[k / sc.udiv]) * acc;
         } else {
           out = u_in[k * su + c * nn + node];
         }
@@ -377,6 +378,8 @@ __global__ void k_apply_q(Grid g, TabT<T> tb, SlabCoef sc, const T* __restrict__
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   int64_t nqt = g.nq[0] + g.nq[1] + g.nq[2];
   if (t >= nqt) return;
+  const int bi = blockIdx.y, nb = g.nb;  // instance of a batched grid
+  kscale += bi * g.ncells;
   int c = 0;
   int64_t r = t;
   while (r >= g.nq[c]) { r -= g.nq[c]; ++c; }
@@ -413,7 +416,7 @@ __global__ void k_apply_q(Grid g, TabT<T> tb, SlabCoef sc, const T* __restrict__
   int64_t pbase = 0;
   for (int d = 0; d < DIM; ++d) if (d != c) pbase += co[d] * pst[d];
   for (int k = 0; k < sc.nt; ++k) {
-    const T* xk = x + k * sx;
+    const T* xk = x + (int64_t)(k * nb + bi) * sx;
     T out;
     if (!fr) out = xk[gidx];
     else {
@@ -435,14 +438,14 @@ __global__ void k_apply_q(Grid g, TabT<T> tb, SlabCoef sc, const T* __restrict__
       for (int l = 0; l < sc.nt; ++l) {
         T w = T(sc.qp[k][l]);
         if (w == T(0)) continue;
-        const T* pl = x + l * sx + g.offp + pbase;
+        const T* pl = x + (int64_t)(l * nb + bi) * sx + g.offp + pbase;
         T bp = 0;
         for (int e = 0; e < ncell; ++e)
           for (int q = 0; q < 2; ++q) bp += tb.bd[c][la[e]][q] * pl[(int64_t)(2 * ce[e] + q) * pst[c]];
         out += w * wt * bp;
       }
     }
-    y[k * sy + gidx] = out;
+    y[(int64_t)(k * nb + bi) * sy + gidx] = out;
   }
 }
 
@@ -463,8 +466,9 @@ __global__ void __launch_bounds__(256) k_apply_p(Grid g, TabT<T> tb, SlabCoef sc
   for (int d = 0; d < DIM; ++d) mp *= tb.wg[d];
   T eu[MAXR], bq[MAXR], pv[MAXR];
   const EtPoint<T, DIM> et(g, tb, co);
+  const int bi = blockIdx.y, nb = g.nb;  // instance of a batched grid
   for (int l = 0; l < sc.nt; ++l) {
-    const T* xl = x + l * sx;
+    const T* xl = x + (int64_t)(l * nb + bi) * sx;
     const T acc = et.eval(g, xl);  // E^T u: the cell's 3^DIM nodes, all components
     eu[l] = acc;
     // B q: for each component c the 3 DoFs along c on this Gauss line
@@ -495,7 +499,7 @@ __global__ void __launch_bounds__(256) k_apply_p(Grid g, TabT<T> tb, SlabCoef sc
   for (int k = 0; k < sc.nt; ++k) {
     T out = T(sc.pq[k]) * bq[k];
     for (int l = 0; l < sc.nt; ++l) out += T(sc.pu[k][l]) * eu[l] + T(sc.pp[k][l]) * mp * pv[l];
-    y[k * sy + g.offp + t] = out;
+    y[(int64_t)(k * nb + bi) * sy + g.offp + t] = out;
   }
 }
 
@@ -528,19 +532,24 @@ __global__ void k_diag_A(Grid g, TabT<T> tb, double lam, double mu, T* __restric
 template <typename T>
 void launch_apply_u(const Grid& g, const TabT<T>& tb, const SlabCoef& sc, const T* u, int64_t su, const T* p, int64_t sp, T* y,
                     int64_t sy, cudaStream_t st) {
+  // columns: the nt temporal levels of every batched instance (or the caller's count)
+  SlabCoef scu = sc;
+  if (scu.ucols <= 0) { scu.ucols = sc.nt * g.nb; scu.udiv = g.nb; }
+  if (scu.udiv <= 0) scu.udiv = 1;
+  const int cols = scu.ucols;
   if (g.dim == 3) {
     constexpr bool ALLJ = sizeof(T) == 4;
-    dim3 grid((g.nu[0] + T3 - 1) / T3, (g.nu[1] + T3 - 1) / T3, ((g.nu[2] + T3 - 1) / T3) * sc.nt);
+    dim3 grid((g.nu[0] + T3 - 1) / T3, (g.nu[1] + T3 - 1) / T3, ((g.nu[2] + T3 - 1) / T3) * cols);
     size_t smem = sizeof(T) * (3 * H3 * H3 * H3 + (ALLJ ? 12 : 4) * H3 * H3 * T3 + 12 * H3 * T3 * T3);
     const int kind = sizeof(T) == 4 ? 0 : 1;
-    prof_begin(st, kind, (double)g.nnode * sc.nt);
-    (note_launch(), k_apply_u3_col<T, ALLJ><<<grid, U3_THREADS, smem, st>>>(g, tb, sc, u, su, y, sy));
+    prof_begin(st, kind, (double)g.nnode * cols);
+    (note_launch(), k_apply_u3_col<T, ALLJ><<<grid, U3_THREADS, smem, st>>>(g, tb, scu, u, su, y, sy));
     prof_end(st, kind);
   } else {
-    dim3 grid((g.nu[0] + T2 - 1) / T2, (g.nu[1] + T2 - 1) / T2, 1);
+    dim3 grid((g.nu[0] + T2 - 1) / T2, (g.nu[1] + T2 - 1) / T2, cols);
     const int kind = sizeof(T) == 4 ? 0 : 1;
-    prof_begin(st, kind, (double)g.nnode * sc.nt);
-    (note_launch(), k_apply_u2<T><<<grid, 256, 0, st>>>(g, tb, sc, u, su, y, sy));
+    prof_begin(st, kind, (double)g.nnode * cols);
+    (note_launch(), k_apply_u2<T><<<grid, 256, 0, st>>>(g, tb, scu, u, su, y, sy));
     prof_end(st, kind);
   }
   if (p) {
@@ -548,7 +557,7 @@ void launch_apply_u(const Grid& g, const TabT<T>& tb, const SlabCoef& sc, const 
     for (int k = 0; k < sc.nt; ++k)
       for (int l = 0; l < sc.nt; ++l) any = any || sc.ep[k][l] != 0.0;
     if (any) {
-      const int blocks = (int)((g.nnode + 255) / 256);
+      const dim3 blocks((unsigned)((g.nnode + 255) / 256), g.nb);
       if (g.dim == 3) (note_launch(), k_add_Ep<T, 3><<<blocks, 256, 0, st>>>(g, tb, sc, p, sp, y, sy));
       else (note_launch(), k_add_Ep<T, 2><<<blocks, 256, 0, st>>>(g, tb, sc, p, sp, y, sy));
     }
@@ -559,7 +568,7 @@ template <typename T>
 void launch_apply_q(const Grid& g, const TabT<T>& tb, const SlabCoef& sc, const T* kscale, const T* x, int64_t sx, T* y,
                     int64_t sy, cudaStream_t st) {
   int64_t n = g.nq[0] + g.nq[1] + g.nq[2];
-  int blocks = (int)((n + 255) / 256);
+  const dim3 blocks((unsigned)((n + 255) / 256), g.nb);
   if (g.dim == 3) (note_launch(), k_apply_q<T, 3><<<blocks, 256, 0, st>>>(g, tb, sc, kscale, x, sx, y, sy));
   else (note_launch(), k_apply_q<T, 2><<<blocks, 256, 0, st>>>(g, tb, sc, kscale, x, sx, y, sy));
 }
@@ -567,7 +576,7 @@ void launch_apply_q(const Grid& g, const TabT<T>& tb, const SlabCoef& sc, const 
 template <typename T>
 void launch_apply_p(const Grid& g, const TabT<T>& tb, const SlabCoef& sc, const T* x, int64_t sx, T* y, int64_t sy,
                     cudaStream_t st) {
-  int blocks = (int)((g.Np + 255) / 256);
+  const dim3 blocks((unsigned)((g.Np + 255) / 256), g.nb);
   if (g.dim == 3) (note_launch(), k_apply_p<T, 3><<<blocks, 256, 0, st>>>(g, tb, sc, x, sx, y, sy));
   else (note_launch(), k_apply_p<T, 2><<<blocks, 256, 0, st>>>(g, tb, sc, x, sx, y, sy));
 }

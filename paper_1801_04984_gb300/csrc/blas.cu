@@ -49,8 +49,8 @@ struct DotAcc<float> {
   __device__ double get() const { return (double)a.hi + (double)a.lo; }
 };
 
-// block-reduce `cnt` doubles per thread (in smem), write to partial[blockIdx.x * stride + i]
-__device__ inline void block_reduce_store(double* vals, int cnt, double* partial, int stride) {
+// block-reduce `cnt` doubles per thread (in smem), write to partial[bid * stride + i]
+__device__ inline void block_reduce_store(double* vals, int cnt, double* partial, int stride, int64_t bid) {
   __shared__ double sh[NV + 1][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int i = 0; i < cnt; ++i) {
@@ -62,7 +62,7 @@ __device__ inline void block_reduce_store(double* vals, int cnt, double* partial
   if (threadIdx.x < cnt) {
     double s = 0;
     for (int w = 0; w < nw; ++w) s += sh[threadIdx.x][w];
-    partial[(int64_t)blockIdx.x * stride + threadIdx.x] = s;
+    partial[bid * stride + threadIdx.x] = s;
   }
 }
 
@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(256) k_multidot(const TV* const* __restrict__ 
   double vals[NV];
 #pragma unroll
   for (int i = 0; i < NV; ++i) vals[i] = acc[i].get();
-  block_reduce_store(vals, nv, partial, NV + 1);
+  block_reduce_store(vals, nv, partial, NV + 1, blockIdx.x);
 }
 
 // sum partial[b][i] over blocks b (fixed order) -> out[i]
@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(256) k_multiaxpy(const TV* const* __restrict__
   double vals[NV];
 #pragma unroll
   for (int i = 0; i < NV; ++i) vals[i] = acc[i].get();
-  block_reduce_store(vals, mode == 1 ? nv : 1, partial, NV + 1);
+  block_reduce_store(vals, mode == 1 ? nv : 1, partial, NV + 1, blockIdx.x);
 }
 
 template <typename TV>
@@ -247,6 +247,204 @@ void launch_time_mix(const TI* in, int64_t sin, TO* out, int64_t sout, int nt, c
   (note_launch(), k_time_mix<TI, TO><<<RED_BLOCKS * 2, 256, 0, st>>>(in, sin, out, sout, nt, m, n));
 }
 
+// ---------------------------------------------------------------------------
+// Segmented (per-instance) vector kernels of a batch of independent problems.
+// Element e of level k of instance b sits at k * lstride + b * istride + e
+// (e < len); block (x, b) of a (gx, nb) grid works on instance b only, so
+// every instance gets its own inner products and its own scalars (Krylov
+// coefficients, normalisations), in the same deterministic order as above.
+int seg_gx(int nb) {
+  int gx = (RED_BLOCKS + nb - 1) / nb;
+  return gx < 2 ? 2 : (gx > RED_BLOCKS ? RED_BLOCKS : gx);
+}
+int64_t seg_partial_doubles(int nb) { return (int64_t)seg_gx(nb) * nb * (NV + 1); }
+
+template <typename TV>
+__global__ void __launch_bounds__(256) k_seg_multidot(const TV* const* __restrict__ V, int nv, const TV* __restrict__ w, Seg sg,
+                                                      double* __restrict__ partial) {
+  const int b = blockIdx.y;
+  DotAcc<TV> acc[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) acc[i].init();
+  const int64_t step = (int64_t)gridDim.x * blockDim.x;
+  for (int k = 0; k < sg.nt; ++k) {
+    const int64_t base = k * sg.lstride + b * sg.istride;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < sg.len; e += step) {
+      const TV we = w[base + e];
+#pragma unroll
+      for (int i = 0; i < NV; ++i)
+        if (i < nv) acc[i].add(V[i][base + e], we);
+    }
+  }
+  double vals[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) vals[i] = acc[i].get();
+  block_reduce_store(vals, nv, partial, NV + 1, (int64_t)b * gridDim.x + blockIdx.x);
+}
+
+// per instance b (one block each): out[b * ostride + i] = sum over its gx partials;
+// with rsq, out[b * ostride + 1] = 1/sqrt(out[b * ostride]) (0 when not positive)
+__global__ void k_seg_final(const double* __restrict__ partial, int gx, int cnt, double* __restrict__ out, int ostride, int rsq) {
+  __shared__ double sh[256];
+  const int b = blockIdx.x;
+  for (int i = 0; i < cnt; ++i) {
+    double s = 0;
+    for (int x = threadIdx.x; x < gx; x += blockDim.x) s += partial[((int64_t)b * gx + x) * (NV + 1) + i];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+      if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      out[(int64_t)b * ostride + i] = sh[0];
+      if (rsq && i == 0) out[(int64_t)b * ostride + 1] = sh[0] > 0.0 ? 1.0 / sqrt(sh[0]) : 0.0;
+    }
+    __syncthreads();
+  }
+}
+
+template <typename TV>
+void launch_seg_multidot(const TV* const* V, int nv, const TV* w, const Seg& sg, double* partial, double* out, int ostride,
+                         cudaStream_t st) {
+  const int gx = seg_gx(sg.nb);
+  for (int c0 = 0; c0 < nv; c0 += NV) {
+    int cnt = (nv - c0 < NV) ? nv - c0 : NV;
+    (note_launch(), k_seg_multidot<TV><<<dim3(gx, sg.nb), 256, 0, st>>>(V + c0, cnt, w, sg, partial));
+    (note_launch(), k_seg_final<<<sg.nb, 256, 0, st>>>(partial, gx, cnt, out + c0, ostride, 0));
+  }
+}
+
+// w -= sum_i V_i h[b * hstride + i]; mode 1: partial dots V^T w_new; mode 2: ||w_new||^2
+template <typename TV>
+__global__ void __launch_bounds__(256) k_seg_multiaxpy(const TV* const* __restrict__ V, int nv, const double* __restrict__ h,
+                                                       int hstride, TV* __restrict__ w, Seg sg, int mode, double* __restrict__ partial) {
+  const int b = blockIdx.y;
+  TV hv[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) hv[i] = (i < nv) ? (TV)h[(int64_t)b * hstride + i] : TV(0);
+  DotAcc<TV> acc[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) acc[i].init();
+  const int64_t step = (int64_t)gridDim.x * blockDim.x;
+  for (int k = 0; k < sg.nt; ++k) {
+    const int64_t base = k * sg.lstride + b * sg.istride;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < sg.len; e += step) {
+      TV v[NV];
+      TV we = w[base + e];
+#pragma unroll
+      for (int i = 0; i < NV; ++i)
+        if (i < nv) { v[i] = V[i][base + e]; we -= hv[i] * v[i]; }
+      w[base + e] = we;
+      if (mode == 1) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i)
+          if (i < nv) acc[i].add(v[i], we);
+      } else if (mode == 2) {
+        acc[0].add(we, we);
+      }
+    }
+  }
+  if (mode == 0) return;
+  double vals[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) vals[i] = acc[i].get();
+  block_reduce_store(vals, mode == 1 ? nv : 1, partial, NV + 1, (int64_t)b * gridDim.x + blockIdx.x);
+}
+
+template <typename TV>
+void launch_seg_multiaxpy_dot(const TV* const* V, int nv, const double* h, int hstride, TV* w, const Seg& sg, int mode,
+                              double* partial, double* out, int ostride, cudaStream_t st) {
+  const int gx = seg_gx(sg.nb);
+  const dim3 grid(gx, sg.nb);
+  if (nv <= NV) {
+    (note_launch(), k_seg_multiaxpy<TV><<<grid, 256, 0, st>>>(V, nv, h, hstride, w, sg, mode, partial));
+    if (mode == 1) (note_launch(), k_seg_final<<<sg.nb, 256, 0, st>>>(partial, gx, nv, out, ostride, 0));
+    if (mode == 2) (note_launch(), k_seg_final<<<sg.nb, 256, 0, st>>>(partial, gx, 1, out, ostride, 1));
+    return;
+  }
+  for (int c0 = 0; c0 < nv; c0 += NV) {
+    int cnt = (nv - c0 < NV) ? nv - c0 : NV;
+    bool last = c0 + NV >= nv;
+    int m = (last && mode == 2) ? 2 : 0;
+    (note_launch(), k_seg_multiaxpy<TV><<<grid, 256, 0, st>>>(V + c0, cnt, h + c0, hstride, w, sg, m, partial));
+    if (m == 2) (note_launch(), k_seg_final<<<sg.nb, 256, 0, st>>>(partial, gx, 1, out, ostride, 1));
+  }
+  if (mode == 1) launch_seg_multidot<TV>(V, nv, w, sg, partial, out, ostride, st);
+}
+
+// y = x * s[b * sstride] per instance
+template <typename T>
+__global__ void k_seg_scale(T* __restrict__ y, const T* __restrict__ x, const double* __restrict__ s, int sstride, Seg sg) {
+  const int b = blockIdx.y;
+  const T f = (T)s[(int64_t)b * sstride];
+  const int64_t step = (int64_t)gridDim.x * blockDim.x;
+  for (int k = 0; k < sg.nt; ++k) {
+    const int64_t base = k * sg.lstride + b * sg.istride;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < sg.len; e += step) y[base + e] = x[base + e] * f;
+  }
+}
+template <typename T>
+void launch_seg_scale(T* y, const T* x, const double* s, int sstride, const Seg& sg, cudaStream_t st) {
+  (note_launch(), k_seg_scale<T><<<dim3(seg_gx(sg.nb), sg.nb), 256, 0, st>>>(y, x, s, sstride, sg));
+}
+
+// y = a[b] x + c[b] y per instance (a, c device arrays, one value per instance)
+template <typename T>
+__global__ void k_seg_axpby(T* __restrict__ y, const T* __restrict__ x, const double* __restrict__ a, const double* __restrict__ c,
+                            Seg sg) {
+  const int b = blockIdx.y;
+  const T av = (T)a[b], cv = (T)c[b];
+  const int64_t step = (int64_t)gridDim.x * blockDim.x;
+  for (int k = 0; k < sg.nt; ++k) {
+    const int64_t base = k * sg.lstride + b * sg.istride;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < sg.len; e += step)
+      y[base + e] = av * x[base + e] + cv * y[base + e];
+  }
+}
+template <typename T>
+void launch_seg_axpby(T* y, const T* x, const double* a, const double* c, const Seg& sg, cudaStream_t st) {
+  (note_launch(), k_seg_axpby<T><<<dim3(seg_gx(sg.nb), sg.nb), 256, 0, st>>>(y, x, a, c, sg));
+}
+
+// y += sum_i Z_i c[b * cstride + i] per instance (arithmetic in the precision of y)
+template <typename TY, typename TZ>
+__global__ void k_seg_lincomb_add(TY* __restrict__ y, const TZ* const* __restrict__ Z, int nz, const double* __restrict__ c,
+                                  int cstride, Seg sg) {
+  const int b = blockIdx.y;
+  const double* cb = c + (int64_t)b * cstride;
+  const int64_t step = (int64_t)gridDim.x * blockDim.x;
+  for (int k = 0; k < sg.nt; ++k) {
+    const int64_t base = k * sg.lstride + b * sg.istride;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < sg.len; e += step) {
+      TY s = y[base + e];
+      for (int i = 0; i < nz; ++i) s += TY(cb[i]) * TY(Z[i][base + e]);
+      y[base + e] = s;
+    }
+  }
+}
+template <typename TY, typename TZ>
+void launch_seg_lincomb_add(TY* y, const TZ* const* Z, int nz, const double* c, int cstride, const Seg& sg, cudaStream_t st) {
+  (note_launch(), k_seg_lincomb_add<TY, TZ><<<dim3(seg_gx(sg.nb), sg.nb), 256, 0, st>>>(y, Z, nz, c, cstride, sg));
+}
+
+// x += s[b * sstride] * d per instance (mixed-precision refinement update)
+template <typename TX, typename TD>
+__global__ void k_seg_add_scaled(TX* __restrict__ x, const TD* __restrict__ d, const double* __restrict__ s, int sstride, Seg sg) {
+  const int b = blockIdx.y;
+  const double f = s[(int64_t)b * sstride];
+  const int64_t step = (int64_t)gridDim.x * blockDim.x;
+  for (int k = 0; k < sg.nt; ++k) {
+    const int64_t base = k * sg.lstride + b * sg.istride;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < sg.len; e += step)
+      x[base + e] = (TX)((double)x[base + e] + f * (double)d[base + e]);
+  }
+}
+template <typename TX, typename TD>
+void launch_seg_add_scaled(TX* x, const TD* d, const double* s, int sstride, const Seg& sg, cudaStream_t st) {
+  (note_launch(), k_seg_add_scaled<TX, TD><<<dim3(seg_gx(sg.nb), sg.nb), 256, 0, st>>>(x, d, s, sstride, sg));
+}
+
 template void launch_multidot<double>(const double* const*, int, const double*, int64_t, double*, double*, cudaStream_t);
 template void launch_multidot<float>(const float* const*, int, const float*, int64_t, double*, double*, cudaStream_t);
 template void launch_multiaxpy_dot<double>(const double* const*, int, const double*, double*, int64_t, int, double*, double*,
@@ -268,5 +466,39 @@ template void launch_time_mix<double, double>(const double*, int64_t, double*, i
                                               cudaStream_t);
 template void launch_time_mix<float, float>(const float*, int64_t, float*, int64_t, int, const double*, int64_t, cudaStream_t);
 template void launch_time_mix<double, float>(const double*, int64_t, float*, int64_t, int, const double*, int64_t, cudaStream_t);
+
+// y_r = a x_r + b y_r on `rows` vectors of length n at stride s (one row per grid y)
+template <typename T>
+__global__ void k_axpby_rows(T* __restrict__ y, const T* __restrict__ x, T a, T b, int64_t n, int64_t s) {
+  const int64_t off = (int64_t)blockIdx.y * s;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    y[off + e] = a * x[off + e] + b * y[off + e];
+}
+template <typename T>
+void launch_axpby_rows(T* y, const T* x, double a, double b, int64_t n, int rows, int64_t s, cudaStream_t st) {
+  int gx = (int)((n + 255) / 256);
+  const int cap = seg_gx(rows) * 2;
+  if (gx > cap) gx = cap;
+  (note_launch(), k_axpby_rows<T><<<dim3(gx, rows), 256, 0, st>>>(y, x, (T)a, (T)b, n, s));
+}
+
+template void launch_seg_multidot<double>(const double* const*, int, const double*, const Seg&, double*, double*, int, cudaStream_t);
+template void launch_seg_multidot<float>(const float* const*, int, const float*, const Seg&, double*, double*, int, cudaStream_t);
+template void launch_seg_multiaxpy_dot<double>(const double* const*, int, const double*, int, double*, const Seg&, int, double*,
+                                               double*, int, cudaStream_t);
+template void launch_seg_multiaxpy_dot<float>(const float* const*, int, const double*, int, float*, const Seg&, int, double*,
+                                              double*, int, cudaStream_t);
+template void launch_seg_scale<double>(double*, const double*, const double*, int, const Seg&, cudaStream_t);
+template void launch_seg_scale<float>(float*, const float*, const double*, int, const Seg&, cudaStream_t);
+template void launch_seg_axpby<double>(double*, const double*, const double*, const double*, const Seg&, cudaStream_t);
+template void launch_seg_axpby<float>(float*, const float*, const double*, const double*, const Seg&, cudaStream_t);
+template void launch_seg_lincomb_add<double, double>(double*, const double* const*, int, const double*, int, const Seg&, cudaStream_t);
+template void launch_seg_lincomb_add<double, float>(double*, const float* const*, int, const double*, int, const Seg&, cudaStream_t);
+template void launch_seg_lincomb_add<float, float>(float*, const float* const*, int, const double*, int, const Seg&, cudaStream_t);
+template void launch_seg_add_scaled<double, float>(double*, const float*, const double*, int, const Seg&, cudaStream_t);
+template void launch_seg_add_scaled<double, double>(double*, const double*, const double*, int, const Seg&, cudaStream_t);
+
+template void launch_axpby_rows<double>(double*, const double*, double, double, int64_t, int, int64_t, cudaStream_t);
+template void launch_axpby_rows<float>(float*, const float*, double, double, int64_t, int, int64_t, cudaStream_t);
 
 }  // namespace biot

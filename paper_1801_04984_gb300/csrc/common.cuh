@@ -36,6 +36,9 @@ struct Grid {
   int64_t offp;
   int64_t N;       // DoFs per temporal level
   int64_t ncells;
+  int nb;          // independent instances batched on this grid (1: a single problem).  Batched
+                   // vectors are level-major: column (k, b) of a slab vector starts at
+                   // (k * nb + b) * N; per-instance coefficient arrays are instance-major.
 };
 
 // 1-D operator taps.  Row types of a Q2 node row: 0 interior vertex, 1 mid
@@ -101,6 +104,9 @@ struct SlabCoef {
   double pp[MAXR][MAXR];
   double pq[MAXR];
   double lam, mu;  // Lamé coefficients
+  // elasticity kernels: number of columns processed and the divisor that maps a column
+  // to its coefficient au[col / udiv] (0: nt * nb columns, divisor nb)
+  int ucols, udiv;
 };
 
 }  // namespace biot

@@ -58,6 +58,32 @@ void launch_scale_into(T* y, const T* x, const double* s, int inv, int64_t n, cu
 template <typename TY, typename TZ>
 void launch_lincomb_add(TY* y, const TZ* const* Z, int nz, const double* c, int64_t n, cudaStream_t st);
 void launch_residual(const double* b, const double* Ax, double* r, int64_t n, cudaStream_t st);  // r = b - Ax
+// Segmented vectors of a batch of independent problems: element e (< len) of level k
+// of instance b at k * lstride + b * istride + e.  Every segmented kernel runs on a
+// (seg_gx(nb), nb) grid and keeps one result / scalar per instance.
+struct Seg {
+  int nb, nt;
+  int64_t len, istride, lstride;
+};
+int seg_gx(int nb);
+int64_t seg_partial_doubles(int nb);  // size of the partial buffer a segmented reduction needs
+template <typename TV>
+void launch_seg_multidot(const TV* const* V, int nv, const TV* w, const Seg& sg, double* partial, double* out, int ostride,
+                         cudaStream_t st);  // out[b * ostride + i] = V_i^T w over instance b
+template <typename TV>
+void launch_seg_multiaxpy_dot(const TV* const* V, int nv, const double* h, int hstride, TV* w, const Seg& sg, int mode,
+                              double* partial, double* out, int ostride, cudaStream_t st);
+template <typename T>
+void launch_seg_scale(T* y, const T* x, const double* s, int sstride, const Seg& sg, cudaStream_t st);
+template <typename T>
+void launch_seg_axpby(T* y, const T* x, const double* a, const double* c, const Seg& sg, cudaStream_t st);
+template <typename TY, typename TZ>
+void launch_seg_lincomb_add(TY* y, const TZ* const* Z, int nz, const double* c, int cstride, const Seg& sg, cudaStream_t st);
+template <typename TX, typename TD>
+void launch_seg_add_scaled(TX* x, const TD* d, const double* s, int sstride, const Seg& sg, cudaStream_t st);
+// y_r = a x_r + b y_r for rows r < rows of length n at stride s
+template <typename T>
+void launch_axpby_rows(T* y, const T* x, double a, double b, int64_t n, int rows, int64_t s, cudaStream_t st);
 // time transform: out[k] = sum_l C[k][l] in[l] over nt levels of length n (strided)
 template <typename TI, typename TO>
 void launch_time_mix(const TI* in, int64_t sin, TO* out, int64_t sout, int nt, const double* C, int64_t n, cudaStream_t st);
@@ -115,7 +141,7 @@ void launch_grad_pair(const Grid& g, const TabT<double>& tb, const double* kscal
                       double* grad, cudaStream_t st);
 // y_k = sum_m c[k][m] f_m (masked) + phi0[k] * sp (pressure block only), k < nt
 void launch_slab_rhs(const Grid& g, const double* const* f, int nterms, const double* c, const double* phi0, int nt,
-                     const double* sp, double* y, cudaStream_t st);
+                     const double* sp, double* y, int64_t ys, cudaStream_t st);  // level k at y + k * ys
 
 template <typename T>
 void launch_schur_dinv(const Grid& g, const TabT<T>& tb, const T* sb2, const double* cm, double tau, T* dinv, int nrhs,

@@ -329,9 +329,10 @@ __global__ void k_q_jacobi(Grid g, const T* __restrict__ rq, int64_t srq, const 
   QIdx<T> q;
   if (!decode_q<DIM>(g, tb.wg, t, q)) return;
   bool fr = q_free(g, q.c, q.ia);
+  const int64_t nqt = g.nq[0] + g.nq[1] + g.nq[2];
   for (int r = 0; r < nrhs; ++r) {
     T v = rq[r * srq + t];
-    q0[r * sq + t] = fr ? v / (T(tau) * dmq[t]) : v;
+    q0[r * sq + t] = fr ? v / (T(tau) * dmq[(r % g.nb) * nqt + t]) : v;
   }
 }
 
@@ -353,8 +354,11 @@ __global__ void k_BTp_scaled(Grid g, TabT<T> tb, const T* __restrict__ p, int64_
   QIdx<T> q;
   if (!decode_q<DIM>(g, tb.wg, t, q)) return;
   bool fr = q_free(g, q.c, q.ia);
-  const T dinv = T(1) / dmq[t];
-  for (int r = 0; r < nrhs; ++r) tq[r * sq + t] = fr ? gather_BTp<T>(g, tb, q, p + r * spp) * dinv : T(0);
+  const int64_t nqt = g.nq[0] + g.nq[1] + g.nq[2];
+  for (int r = 0; r < nrhs; ++r) {
+    const T dinv = T(1) / dmq[(r % g.nb) * nqt + t];
+    tq[r * sq + t] = fr ? gather_BTp<T>(g, tb, q, p + r * spp) * dinv : T(0);
+  }
 }
 
 // out_p = cm[r] * mp * p + tau * B tq
@@ -369,7 +373,7 @@ __global__ void k_schur_out(Grid g, TabT<T> tb, const T* __restrict__ p, int64_t
   T mp = 1;
   for (int d = 0; d < DIM; ++d) mp *= tb.wg[d];
   for (int r = 0; r < nrhs; ++r)
-    out[r * so + t] = T(cm.c[r]) * mp * p[r * spp + t] + T(tau) * gather_Bq<T, DIM>(g, tb, t, tq + r * sq, nullptr);
+    out[r * so + t] = T(cm.c[r / g.nb]) * mp * p[r * spp + t] + T(tau) * gather_Bq<T, DIM>(g, tb, t, tq + r * sq, nullptr);
 }
 
 // q = (Rq + bt B^T p) / (tau dmq) on free flux DoFs, Rq on constrained
@@ -380,8 +384,9 @@ __global__ void k_q_final(Grid g, TabT<T> tb, const T* __restrict__ rq, int64_t 
   QIdx<T> q;
   if (!decode_q<DIM>(g, tb.wg, t, q)) return;
   bool fr = q_free(g, q.c, q.ia);
-  const T den = T(1) / (T(tau) * dmq[t]);
+  const int64_t nqt = g.nq[0] + g.nq[1] + g.nq[2];
   for (int r = 0; r < nrhs; ++r) {
+    const T den = T(1) / (T(tau) * dmq[(r % g.nb) * nqt + t]);
     T v = rq[r * srq + t];
     if (fr) v = (v + T(bt) * gather_BTp<T>(g, tb, q, p + r * spp)) * den;
     qo[r * sq + t] = v;
@@ -451,7 +456,8 @@ void launch_schur_apply(const Grid& g, const TabT<T>& tb, const T* p, int64_t sp
                         const double* cm, T* out, int64_t so, int nrhs, cudaStream_t st) {
   int64_t nqt = g.nq[0] + g.nq[1] + g.nq[2];
   RhsCoef rc;
-  for (int r = 0; r < MAXR; ++r) rc.c[r] = (r < nrhs) ? cm[r] : 0.0;
+  const int nlev = (nrhs + g.nb - 1) / g.nb;  // nrhs counts columns (level x instance)
+  for (int r = 0; r < MAXR; ++r) rc.c[r] = (r < nlev) ? cm[r] : 0.0;
   if (g.dim == 3) {
     (note_launch(), k_BTp_scaled<T, 3><<<(int)((nqt + 255) / 256), 256, 0, st>>>(g, tb, p, spp, dmq, tq, sq, nrhs));
     (note_launch(), k_schur_out<T, 3><<<(int)((g.Np + 255) / 256), 256, 0, st>>>(g, tb, p, spp, tq, sq, tau, rc, out, so, nrhs));
@@ -594,43 +600,45 @@ struct RhsTab {
   double phi0[MAXR];
 };
 __global__ void k_slab_rhs(Grid g, const double* const* __restrict__ f, int nterms, RhsTab tab, int nt,
-                           const double* __restrict__ sp, double* __restrict__ y) {
+                           const double* __restrict__ sp, double* __restrict__ y, int64_t ys) {
   int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= g.N) return;
   for (int k = 0; k < nt; ++k) {
     double s = 0;
     for (int m = 0; m < nterms; ++m) s += tab.c[k][m] * f[m][e];
     if (e >= g.offp && sp) s += tab.phi0[k] * sp[e - g.offp];
-    y[k * g.N + e] = s;
+    y[k * ys + e] = s;
   }
 }
 void launch_slab_rhs(const Grid& g, const double* const* f, int nterms, const double* c, const double* phi0, int nt,
-                     const double* sp, double* y, cudaStream_t st) {
+                     const double* sp, double* y, int64_t ys, cudaStream_t st) {
   RhsTab tab;
   for (int k = 0; k < MAXR; ++k) {
     for (int m = 0; m < 8; ++m) tab.c[k][m] = (k < nt && m < nterms) ? c[k * nterms + m] : 0.0;
     tab.phi0[k] = (k < nt) ? phi0[k] : 0.0;
   }
-  (note_launch(), k_slab_rhs<<<(int)((g.N + 255) / 256), 256, 0, st>>>(g, f, nterms, tab, nt, sp, y));
+  (note_launch(), k_slab_rhs<<<(int)((g.N + 255) / 256), 256, 0, st>>>(g, f, nterms, tab, nt, sp, y, ys));
 }
 
 
 // inverse Jacobi diagonal of the flux-pressure Schur approximation per rhs:
 // dinv[r][i] = 1 / (cm[r] * mp + tau * sb2[i])
 template <typename T>
-__global__ void k_schur_dinv(const T* __restrict__ sb2, double mp, RhsCoef cm, double tau, T* __restrict__ dinv, int64_t np, int nrhs) {
+__global__ void k_schur_dinv(const T* __restrict__ sb2, double mp, RhsCoef cm, double tau, T* __restrict__ dinv, int64_t np, int nrhs,
+                             int nb) {
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= np) return;
-  for (int r = 0; r < nrhs; ++r) dinv[r * np + t] = T(1) / (T(cm.c[r] * mp) + T(tau) * sb2[t]);
+  for (int r = 0; r < nrhs; ++r) dinv[r * np + t] = T(1) / (T(cm.c[r / nb] * mp) + T(tau) * sb2[(r % nb) * np + t]);
 }
 template <typename T>
 void launch_schur_dinv(const Grid& g, const TabT<T>& tb, const T* sb2, const double* cm, double tau, T* dinv, int nrhs,
                        cudaStream_t st) {
   RhsCoef rc;
-  for (int r = 0; r < MAXR; ++r) rc.c[r] = (r < nrhs) ? cm[r] : 0.0;
+  const int nlev = (nrhs + g.nb - 1) / g.nb;  // nrhs counts columns (level x instance)
+  for (int r = 0; r < MAXR; ++r) rc.c[r] = (r < nlev) ? cm[r] : 0.0;
   double mp = 1.0;
   for (int d = 0; d < g.dim; ++d) mp *= (double)tb.wg[d];
-  (note_launch(), k_schur_dinv<T><<<(int)((g.Np + 255) / 256), 256, 0, st>>>(sb2, mp, rc, tau, dinv, g.Np, nrhs));
+  (note_launch(), k_schur_dinv<T><<<(int)((g.Np + 255) / 256), 256, 0, st>>>(sb2, mp, rc, tau, dinv, g.Np, nrhs, g.nb));
 }
 
 // Chebyshev step with a per-rhs diagonal (stride n between rhs for every array)
@@ -910,9 +918,10 @@ __global__ void __launch_bounds__(256) k_schur_cheb_st(Grid g, const T* __restri
                                                        const T* __restrict__ x, T* __restrict__ d, T* __restrict__ xo) {
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= g.Np) return;
-  const int r = blockIdx.y;
+  const int r = blockIdx.y;  // column: level r / nb of instance r % nb
   const int64_t np = g.Np;
   const int64_t i = r * np + t;
+  coef += (int64_t)(r % g.nb) * 16 * np;
   const T di = dinv[i];
   if (first) {
     const T dn = c2 * di * b[i];
@@ -929,7 +938,7 @@ __global__ void __launch_bounds__(256) k_schur_cheb_st(Grid g, const T* __restri
   const int64_t pst[3] = {1, ng0, (int64_t)ng0 * ng1};
   const T* xr = x + r * np;
   const T xs = xr[t];
-  T acc = (T(cm.c[r]) * mp + coef[t]) * xs;
+  T acc = (T(cm.c[r / g.nb]) * mp + coef[t]) * xs;
 #pragma unroll
   for (int c = 0; c < DIM; ++c) {
     const int cc = co[c];
@@ -961,7 +970,8 @@ template <typename T>
 void launch_schur_cheb_st(const Grid& g, const TabT<T>& tb, const T* coef, const T* dinv, const double* cm, double c1, double c2,
                           int first, const T* b, const T* x, T* d, T* xo, int nrhs, cudaStream_t st) {
   RhsCoef rc;
-  for (int r = 0; r < MAXR; ++r) rc.c[r] = (r < nrhs) ? cm[r] : 0.0;
+  const int nlev = (nrhs + g.nb - 1) / g.nb;  // nrhs counts columns (level x instance)
+  for (int r = 0; r < MAXR; ++r) rc.c[r] = (r < nlev) ? cm[r] : 0.0;
   double mp = 1.0;
   for (int k = 0; k < g.dim; ++k) mp *= (double)tb.wg[k];
   dim3 grid((unsigned)((g.Np + 255) / 256), nrhs);

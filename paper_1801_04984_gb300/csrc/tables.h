@@ -121,6 +121,7 @@ inline Grid make_grid(int dim, const int* n, const double* lo, const double* hi,
   g.Np = (int64_t)g.ng[0] * g.ng[1] * g.ng[2];
   g.N = off + g.Np;
   g.ncells = (int64_t)g.n[0] * g.n[1] * g.n[2];
+  g.nb = 1;
   return g;
 }
 
