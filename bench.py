@@ -367,7 +367,7 @@ def main():
                 "share_of_step": (el_ms / 1e3) / t_prof if t_prof > 0 else None,
                 "algorithmic_gbs": 24.0 * el_units / (el_ms / 1e3) / 1e9 if el_ms > 0 else None,
                 "hbm_peak_gbs": hbm_peak_measured(ROOT)}
-    schur = {"kernel": "k_schur_cheb<float> (one Chebyshev step, flux-pressure Schur)", "launches_per_step": sch[0],
+    schur = {"kernel": "k_schur_cheb_st<float> (one Chebyshev step, flux-pressure Schur)", "launches_per_step": sch[0],
              "avg_launch_us": 1e3 * sch[1] / max(1, sch[0]), "share_of_step": (sch[1] / 1e3) / t_prof if t_prof > 0 else None}
     s_mean = stats[-1]
     cpu = None

@@ -438,9 +438,10 @@ void apply_slab_T(biot_ctx& c, double tau, const T* x, T* y, int transpose, cuda
   CKL();
 }
 
-// tau A x on one MG level, nrhs vectors of stride Nu
+// tau A x on one MG level, nrhs vectors of stride Nu (epi: fused smoothing step or residual)
 template <typename T>
-void apply_A(const Level& L, double lam, double mu, double tau, const T* x, T* y, int nrhs, cudaStream_t st) {
+void apply_A(const Level& L, double lam, double mu, double tau, const T* x, T* y, int nrhs, cudaStream_t st,
+             const UEpi<T>* epi = nullptr) {
   SlabCoef sc;
   std::memset(&sc, 0, sizeof(sc));
   sc.nt = 1;
@@ -449,7 +450,7 @@ void apply_A(const Level& L, double lam, double mu, double tau, const T* x, T* y
   sc.au[0] = tau;
   sc.ucols = nrhs;  // every column (temporal level x batched instance) takes tau A
   sc.udiv = nrhs;
-  launch_apply_u<T>(L.g, ltab<T>(L), sc, x, L.g.Nu, nullptr, 0, y, L.g.Nu, st);
+  launch_apply_u<T>(L.g, ltab<T>(L), sc, x, L.g.Nu, nullptr, 0, y, L.g.Nu, st, epi);
   CKL();
 }
 
@@ -676,8 +677,20 @@ void smooth(biot_ctx& c, Level& L, double tau, int nrhs, bool zero_start, cudaSt
   const int64_t n = L.g.Nu;
   for (int k = 0; k < cc.n; ++k) {
     bool first = (k == 0 && zero_start);
-    if (!first) apply_A<T>(L, c.lam, c.mu, tau, w.x, w.Ax, nrhs, st);
-    launch_cheb_update<T>(w.b, w.Ax, ldinv<T>(L), w.d, w.x, w.xo, cc.c1[k], cc.c2[k] / tau, first ? 1 : 0, n, nrhs, n, st);
+    if (first) {
+      launch_cheb_update<T>(w.b, w.Ax, ldinv<T>(L), w.d, w.x, w.xo, cc.c1[k], cc.c2[k] / tau, 1, n, nrhs, n, st);
+    } else {
+      // the operator's output stage does the Chebyshev-Jacobi update (no separate pass)
+      UEpi<T> ep;
+      ep.mode = EPI_CHEB;
+      ep.b = w.b;
+      ep.dinv = ldinv<T>(L);
+      ep.d = w.d;
+      ep.xo = w.xo;
+      ep.c1 = (T)cc.c1[k];
+      ep.c2 = (T)(cc.c2[k] / tau);
+      apply_A<T>(L, c.lam, c.mu, tau, w.x, nullptr, nrhs, st, &ep);
+    }
     CKL();
     std::swap(w.x, w.xo);
   }
@@ -691,8 +704,10 @@ void vcycle(biot_ctx& c, double tau, int nrhs, cudaStream_t st) {
     Level& L = c.lv[l];
     LevelWork<T>& w = lwork<T>(L);
     smooth<T>(c, L, tau, nrhs, true, st);
-    apply_A<T>(L, c.lam, c.mu, tau, w.x, w.Ax, nrhs, st);
-    launch_axpby<T>(w.Ax, w.b, 1.0, -1.0, L.g.Nu * nrhs, st);  // residual in Ax
+    UEpi<T> ep;  // residual b - tau A x in Ax, fused into the operator's output stage
+    ep.mode = EPI_RESID;
+    ep.b = w.b;
+    apply_A<T>(L, c.lam, c.mu, tau, w.x, w.Ax, nrhs, st, &ep);
     CKL();
     Level& C = c.lv[l + 1];
     launch_restrict<T>(L.g, C.g, w.Ax, L.g.Nu, lwork<T>(C).b, C.g.Nu, nrhs, st);
@@ -1805,6 +1820,7 @@ int setup_impl(const biot_mesh* mesh, const biot_coeffs* co, int r, const biot_o
     c->sb2_32 = dalloc<float>(g.Np * nb);
     c->hdev = dalloc<double>((int64_t)HS * nb + 256);
     c->bdev = dalloc<double>(bdev_doubles(c->nt, nb));
+
     CK(cudaStreamCreateWithFlags(&c->ws, cudaStreamNonBlocking));
     CK(cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming));
@@ -2276,6 +2292,7 @@ extern "C" void biot_destroy(biot_t c) {
   if (c->hhost) cudaFreeHost(c->hhost);
   if (c->bhost) cudaFreeHost(c->bhost);
   F(c->bdev);
+
   if (c->hptr) cudaFreeHost(c->hptr);
   F(c->ptrbuf);
   for (Level& L : c->lv) {

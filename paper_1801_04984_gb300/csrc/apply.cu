@@ -52,6 +52,30 @@ __device__ inline T tap5(const T* c, const T* v, int stride) {
   return c[0] * v[0] + c[1] * v[stride] + c[2] * v[2 * stride] + c[3] * v[3 * stride] + c[4] * v[4 * stride];
 }
 
+// Output stage of the elasticity kernels for one entry i (column offset included) of
+// component-node cn: Ax is (tau A x)_i, x_i the input.  EPI_NONE stores Ax; EPI_CHEB does
+// one Chebyshev-Jacobi smoothing step (r = b - Ax, d = c1 d + c2 Dinv r, xo = x + d; rows
+// with Dinv = 0 are constrained: xo = b, d = 0); EPI_RESID stores the residual b - Ax.
+template <typename T>
+__device__ __forceinline__ void u_epilogue(int mode, const UEpi<T>& ep, T* __restrict__ y, int64_t i, int64_t cn, T Ax, T x) {
+  if (mode == EPI_NONE) {
+    y[i] = Ax;
+  } else if (mode == EPI_RESID) {
+    y[i] = ep.b[i] - Ax;
+  } else {
+    const T di = ep.dinv[cn], bi = ep.b[i];
+    if (di == T(0)) {
+      ep.xo[i] = bi;
+      ep.d[i] = T(0);
+    } else {
+      T dn = ep.c2 * di * (bi - Ax);
+      if (ep.c1 != T(0)) dn += ep.c1 * ep.d[i];
+      ep.d[i] = dn;
+      ep.xo[i] = x + dn;
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Y_k += E (sum_l ep[k][l] p_l) on the free displacement rows (§Monolithic
 // Approach: the -b E p block of A_s and its time mixing), one thread per Q2 node
@@ -110,25 +134,45 @@ constexpr int U3_THREADS = 384;
 // ALLJ (FP32): the z pass runs for the three input components at once (12
 // z-pass arrays); otherwise (FP64, twice the shared memory per value) component
 // by component with the y pass accumulating into the pre-x arrays.
+// Reference 1-D Q2 rows with integer taps (unit cell, before the per-direction scale):
+// mass x30 (scale h/30), stiffness x3 (scale 1/(3h)), derivative coupling G and its
+// transpose x6 (scale 1/6).  Vertex rows have 5 taps (offsets -2..2), mid rows 3; a
+// vertex row on the domain boundary keeps only its own cell's centre entry.
+template <int OP>
+__host__ __device__ constexpr float ref_vertex(int k) {
+  constexpr float M[5] = {-1.f, 2.f, 8.f, 2.f, -1.f}, K[5] = {1.f, -8.f, 14.f, -8.f, 1.f};
+  constexpr float G[5] = {1.f, -4.f, 0.f, 4.f, -1.f}, Gt[5] = {-1.f, 4.f, 0.f, -4.f, 1.f};
+  return OP == 0 ? M[k] : (OP == 1 ? K[k] : (OP == 2 ? G[k] : Gt[k]));
+}
+template <int OP>
+__host__ __device__ constexpr float ref_mid(int k) {  // offsets -1, 0, 1
+  constexpr float M[3] = {2.f, 16.f, 2.f}, K[3] = {-8.f, 16.f, -8.f}, G[3] = {-4.f, 0.f, 4.f}, Gt[3] = {4.f, 0.f, -4.f};
+  return OP == 0 ? M[k] : (OP == 1 ? K[k] : (OP == 2 ? G[k] : Gt[k]));
+}
+template <int OP>
+__host__ __device__ constexpr float ref_centre_lo() { return OP == 0 ? 4.f : (OP == 1 ? 7.f : -3.f); }
+template <int OP>
+__host__ __device__ constexpr float ref_centre_hi() { return OP == 0 ? 4.f : (OP == 1 ? 7.f : 3.f); }
+
 template <int OP, typename T>
-__device__ __forceinline__ void col8(const T (&tab)[4][4][5], int g0, int nn, const T* w, T* out) {
-  // w[0..11]: staged line (offset -2), out[0..7]: outputs of operator OP along the line
+__device__ __forceinline__ void col8(int g0, int nn, const T* w, T* out) {
+  // w[0..11]: staged line (offset -2), out[0..7]: unscaled outputs of operator OP along the line
 #pragma unroll
   for (int o = 0; o < 8; ++o) {
     const int gi = g0 + o;
     if ((o & 1) == 0) {
-      const int rt = (gi == 0) ? 2 : ((gi == nn - 1) ? 3 : 0);
-      out[o] = tab[OP][0][0] * w[o] + tab[OP][0][1] * w[o + 1] + tab[OP][rt][2] * w[o + 2] + tab[OP][0][3] * w[o + 3] +
-               tab[OP][0][4] * w[o + 4];
+      const T cc = (gi == 0) ? T(ref_centre_lo<OP>()) : ((gi == nn - 1) ? T(ref_centre_hi<OP>()) : T(ref_vertex<OP>(2)));
+      out[o] = T(ref_vertex<OP>(0)) * w[o] + T(ref_vertex<OP>(1)) * w[o + 1] + cc * w[o + 2] + T(ref_vertex<OP>(3)) * w[o + 3] +
+               T(ref_vertex<OP>(4)) * w[o + 4];
     } else {
-      out[o] = tab[OP][1][1] * w[o + 1] + tab[OP][1][2] * w[o + 2] + tab[OP][1][3] * w[o + 3];
+      out[o] = T(ref_mid<OP>(0)) * w[o + 1] + T(ref_mid<OP>(1)) * w[o + 2] + T(ref_mid<OP>(2)) * w[o + 3];
     }
   }
 }
 
 template <int Q, typename T>
-__device__ __forceinline__ void ypass_target(const T* __restrict__ s_zo, T* __restrict__ s_px, const T (&tab)[4][4][5], int Y0,
-                                             int ny, int lz, int lx, T cf0, T cf1, T cf2, int jonly) {
+__device__ __forceinline__ void ypass_target(const T* __restrict__ s_zo, T* __restrict__ s_px, const T (&sz)[4], const T (&sy)[4],
+                                             int Y0, int ny, int lz, int lx, T cf0, T cf1, T cf2, int jonly) {
   constexpr int HH = H3 * H3, ZO = H3 * H3 * T3, PX = H3 * T3 * T3;
   T acc[8];
 #pragma unroll
@@ -144,12 +188,13 @@ __device__ __forceinline__ void ypass_target(const T* __restrict__ s_zo, T* __re
     for (int y = 0; y < 12; ++y) w[y] = src[y * H3];
     T o8[8];
     switch (tm.yop) {
-      case 0: col8<0>(tab, Y0, ny, w, o8); break;
-      case 1: col8<1>(tab, Y0, ny, w, o8); break;
-      case 2: col8<2>(tab, Y0, ny, w, o8); break;
-      default: col8<3>(tab, Y0, ny, w, o8); break;
+      case 0: col8<0>(Y0, ny, w, o8); break;
+      case 1: col8<1>(Y0, ny, w, o8); break;
+      case 2: col8<2>(Y0, ny, w, o8); break;
+      default: col8<3>(Y0, ny, w, o8); break;
     }
-    const T cfv = tm.coef == 0 ? cf0 : (tm.coef == 1 ? cf1 : cf2);
+    // the term's material coefficient with the z and y scales of its 1-D operators
+    const T cfv = (tm.coef == 0 ? cf0 : (tm.coef == 1 ? cf1 : cf2)) * sz[tm.zop] * sy[tm.yop];
 #pragma unroll
     for (int o = 0; o < 8; ++o) acc[o] += cfv * o8[o];
   }
@@ -166,7 +211,7 @@ __device__ __forceinline__ void ypass_target(const T* __restrict__ s_zo, T* __re
 template <typename T, bool ALLJ>
 __global__ void __launch_bounds__(U3_THREADS, ALLJ ? 2 : 1) k_apply_u3_col(Grid g, TabT<T> tb, SlabCoef sc,
                                                                             const T* __restrict__ u_in, int64_t su,
-                                                                            T* __restrict__ y, int64_t sy) {
+                                                                            T* __restrict__ y, int64_t sy, UEpi<T> ep) {
   constexpr int HH = H3 * H3, HHH = H3 * H3 * H3;
   constexpr int ZO = H3 * H3 * T3;
   constexpr int PX = H3 * T3 * T3;
@@ -175,9 +220,14 @@ __global__ void __launch_bounds__(U3_THREADS, ALLJ ? 2 : 1) k_apply_u3_col(Grid 
   T* s_in = reinterpret_cast<T*>(smem_raw);  // 3 * H3^3
   T* s_zo = s_in + 3 * HHH;                  // NZO * ZO
   T* s_px = s_zo + NZO * ZO;                 // 12 * PX
-  __shared__ T s_tab[3][4][4][5];
   const int tid = threadIdx.x;
-  for (int i = tid; i < 3 * 4 * 4 * 5; i += U3_THREADS) (&s_tab[0][0][0][0])[i] = (&tb.q2[0][0][0][0])[i];
+  T scx[4], scy[4], scz[4];  // per-direction scales of the reference 1-D operators
+#pragma unroll
+  for (int op = 0; op < 4; ++op) {
+    scx[op] = tb.opscale[0][op];
+    scy[op] = tb.opscale[1][op];
+    scz[op] = tb.opscale[2][op];
+  }
   const int nx = g.nu[0], ny = g.nu[1], nz = g.nu[2];
   const int ntz = (nz + T3 - 1) / T3;
   const int k = blockIdx.z / ntz;  // column (temporal level x instance, level-major)
@@ -223,16 +273,16 @@ __global__ void __launch_bounds__(U3_THREADS, ALLJ ? 2 : 1) k_apply_u3_col(Grid 
       for (int z = 0; z < 12; ++z) w[z] = src[z * HH];
       T o8[8];
       T* dst = s_zo + (ALLJ ? c * 4 : 0) * ZO + rem;
-      col8<0>(s_tab[2], Z0, nz, w, o8);
+      col8<0>(Z0, nz, w, o8);
 #pragma unroll
       for (int o = 0; o < 8; ++o) dst[o * HH] = o8[o];
-      col8<1>(s_tab[2], Z0, nz, w, o8);
+      col8<1>(Z0, nz, w, o8);
 #pragma unroll
       for (int o = 0; o < 8; ++o) dst[ZO + o * HH] = o8[o];
-      col8<2>(s_tab[2], Z0, nz, w, o8);
+      col8<2>(Z0, nz, w, o8);
 #pragma unroll
       for (int o = 0; o < 8; ++o) dst[2 * ZO + o * HH] = o8[o];
-      col8<3>(s_tab[2], Z0, nz, w, o8);
+      col8<3>(Z0, nz, w, o8);
 #pragma unroll
       for (int o = 0; o < 8; ++o) dst[3 * ZO + o * HH] = o8[o];
     }
@@ -243,29 +293,30 @@ __global__ void __launch_bounds__(U3_THREADS, ALLJ ? 2 : 1) k_apply_u3_col(Grid 
       const int q = it / (T3 * H3), rem = it - q * (T3 * H3);
       const int lz = rem / H3, lx = rem - lz * H3;
       switch (q) {
-        case 0: ypass_target<0>(s_zo, s_px, s_tab[1], Y0, ny, lz, lx, cf0, cf1, cf2, jo); break;
-        case 1: ypass_target<1>(s_zo, s_px, s_tab[1], Y0, ny, lz, lx, cf0, cf1, cf2, jo); break;
-        case 2: ypass_target<2>(s_zo, s_px, s_tab[1], Y0, ny, lz, lx, cf0, cf1, cf2, jo); break;
-        case 3: ypass_target<3>(s_zo, s_px, s_tab[1], Y0, ny, lz, lx, cf0, cf1, cf2, jo); break;
-        case 4: ypass_target<4>(s_zo, s_px, s_tab[1], Y0, ny, lz, lx, cf0, cf1, cf2, jo); break;
-        case 5: ypass_target<5>(s_zo, s_px, s_tab[1], Y0, ny, lz, lx, cf0, cf1, cf2, jo); break;
-        case 6: ypass_target<6>(s_zo, s_px, s_tab[1], Y0, ny, lz, lx, cf0, cf1, cf2, jo); break;
-        case 7: ypass_target<7>(s_zo, s_px, s_tab[1], Y0, ny, lz, lx, cf0, cf1, cf2, jo); break;
-        case 8: ypass_target<8>(s_zo, s_px, s_tab[1], Y0, ny, lz, lx, cf0, cf1, cf2, jo); break;
-        case 9: ypass_target<9>(s_zo, s_px, s_tab[1], Y0, ny, lz, lx, cf0, cf1, cf2, jo); break;
-        case 10: ypass_target<10>(s_zo, s_px, s_tab[1], Y0, ny, lz, lx, cf0, cf1, cf2, jo); break;
-        default: ypass_target<11>(s_zo, s_px, s_tab[1], Y0, ny, lz, lx, cf0, cf1, cf2, jo); break;
+        case 0: ypass_target<0>(s_zo, s_px, scz, scy, Y0, ny, lz, lx, cf0, cf1, cf2, jo); break;
+        case 1: ypass_target<1>(s_zo, s_px, scz, scy, Y0, ny, lz, lx, cf0, cf1, cf2, jo); break;
+        case 2: ypass_target<2>(s_zo, s_px, scz, scy, Y0, ny, lz, lx, cf0, cf1, cf2, jo); break;
+        case 3: ypass_target<3>(s_zo, s_px, scz, scy, Y0, ny, lz, lx, cf0, cf1, cf2, jo); break;
+        case 4: ypass_target<4>(s_zo, s_px, scz, scy, Y0, ny, lz, lx, cf0, cf1, cf2, jo); break;
+        case 5: ypass_target<5>(s_zo, s_px, scz, scy, Y0, ny, lz, lx, cf0, cf1, cf2, jo); break;
+        case 6: ypass_target<6>(s_zo, s_px, scz, scy, Y0, ny, lz, lx, cf0, cf1, cf2, jo); break;
+        case 7: ypass_target<7>(s_zo, s_px, scz, scy, Y0, ny, lz, lx, cf0, cf1, cf2, jo); break;
+        case 8: ypass_target<8>(s_zo, s_px, scz, scy, Y0, ny, lz, lx, cf0, cf1, cf2, jo); break;
+        case 9: ypass_target<9>(s_zo, s_px, scz, scy, Y0, ny, lz, lx, cf0, cf1, cf2, jo); break;
+        case 10: ypass_target<10>(s_zo, s_px, scz, scy, Y0, ny, lz, lx, cf0, cf1, cf2, jo); break;
+        default: ypass_target<11>(s_zo, s_px, scz, scy, Y0, ny, lz, lx, cf0, cf1, cf2, jo); break;
       }
     }
   }
   __syncthreads();
-  // x pass and output: item = (component, z, y) line along x
-  T* yk = y + k * sy;
+  // x pass: item = (component, z, y) line along x; results staged in shared memory
+  // (s_in is free again) so the output stage below runs on every thread with
+  // consecutive threads on consecutive x
+  T* s_out = s_in;  // [c][lz][ly][lx], 3 * T3^3
+  const T au = T(sc.au[k / sc.udiv]);
   for (int it = tid; it < 3 * T3 * T3; it += U3_THREADS) {
     const int c = it / (T3 * T3), rem = it - c * (T3 * T3);
     const int lz = rem / T3, ly = rem - lz * T3;
-    const int gy = Y0 + ly, gz = Z0 + lz;
-    if (gy >= ny || gz >= nz) continue;
     T acc[8];
 #pragma unroll
     for (int o = 0; o < 8; ++o) acc[o] = 0;
@@ -277,36 +328,38 @@ __global__ void __launch_bounds__(U3_THREADS, ALLJ ? 2 : 1) k_apply_u3_col(Grid 
       for (int x = 0; x < 12; ++x) w[x] = src[op * PX + x];
       T o8[8];
       switch (op) {
-        case 0: col8<0>(s_tab[0], X0, nx, w, o8); break;
-        case 1: col8<1>(s_tab[0], X0, nx, w, o8); break;
-        case 2: col8<2>(s_tab[0], X0, nx, w, o8); break;
-        default: col8<3>(s_tab[0], X0, nx, w, o8); break;
+        case 0: col8<0>(X0, nx, w, o8); break;
+        case 1: col8<1>(X0, nx, w, o8); break;
+        case 2: col8<2>(X0, nx, w, o8); break;
+        default: col8<3>(X0, nx, w, o8); break;
       }
 #pragma unroll
-      for (int o = 0; o < 8; ++o) acc[o] += o8[o];
+      for (int o = 0; o < 8; ++o) acc[o] += scx[op] * o8[o];
     }
+    T* dst = s_out + it * T3;
+#pragma unroll
+    for (int o = 0; o < 8; ++o) dst[o] = au * acc[o];
+  }
+  __syncthreads();
+  // output stage: constrained rows return the input; optional fused smoothing step / residual
+  const int64_t ko = (int64_t)k * sy;  // column offset of the outputs (and of the epilogue arrays)
+  for (int it = tid; it < 3 * T3 * T3 * T3; it += U3_THREADS) {
+    const int c = it / (T3 * T3 * T3), rem = it - c * (T3 * T3 * T3);
+    const int lz = rem / (T3 * T3), ly = (rem / T3) % T3, lx = rem % T3;
+    const int gx = X0 + lx, gy = Y0 + ly, gz = Z0 + lz;
+    if (gx >= nx || gy >= ny || gz >= nz) continue;
     const int fm = c == 0 ? fm0 : (c == 1 ? fm1 : fm2);
-    const T au = T(sc.au[k / sc.udiv]);
-#pragma unroll
-    for (int o = 0; o < 8; ++o) {
-      const int gx = X0 + o;
-      if (gx >= nx) break;
-      const int64_t node = ((int64_t)gz * ny + gy) * nx + gx;
-      T out;
-      if (u_free_mask(fm, gx, gy, gz, nx, ny, nz)) {
-        out = au * acc[o];
-      } else {
-        out = u[c * nn + node];
-      }
-      yk[c * nn + node] = out;
-    }
+    const int64_t cn = c * nn + ((int64_t)gz * ny + gy) * nx + gx;
+    const bool fr = u_free_mask(fm, gx, gy, gz, nx, ny, nz);
+    const T xv = (ep.mode == EPI_CHEB || !fr) ? u[cn] : T(0);
+    u_epilogue<T>(ep.mode, ep, y, ko + cn, cn, fr ? s_out[it] : xv, xv);
   }
 }
 
 // 2-D displacement rows: tiles of 16x16 nodes, passes y then x.
 template <typename T>
 __global__ void __launch_bounds__(256) k_apply_u2(Grid g, TabT<T> tb, SlabCoef sc, const T* __restrict__ u_in, int64_t su,
-                                                  T* __restrict__ y, int64_t sy) {
+                                                  T* __restrict__ y, int64_t sy, UEpi<T> ep) {
   __shared__ T s_in[2][H2 * H2];
   __shared__ T s_px[8][T2 * H2];
   __shared__ T s_tab[2][4][4][5];
@@ -348,13 +401,15 @@ __global__ void __launch_bounds__(256) k_apply_u2(Grid g, TabT<T> tb, SlabCoef s
       }
     }
     __syncthreads();
-    T* yk = y + k * sy;
+    const int64_t ko = (int64_t)k * sy;
     for (int i = tid; i < ex * ey; i += nth) {
       int ly = i / ex, lx = i - ly * ex;
       int gx = X0 + lx, gy = Y0 + ly;
       int rt = rowtype(gx, g.nu[0]);
       int64_t node = (int64_t)gy * g.nu[0] + gx;
       for (int c = 0; c < 2; ++c) {
+        const int64_t cn = c * nn + node;
+        const T xv = u[cn];
         T out;
         if (u_free(g, c, gx, gy, 0)) {
           T acc = 0;
@@ -362,9 +417,9 @@ __global__ void __launch_bounds__(256) k_apply_u2(Grid g, TabT<T> tb, SlabCoef s
           for (int op = 0; op < 4; ++op) acc += tap5(s_tab[0][op][rt], &s_px[c * 4 + op][ly * H2 + lx], 1);
           out = T(sc.au[k / sc.udiv]) * acc;
         } else {
-          out = u_in[k * su + c * nn + node];
+          out = xv;
         }
-        yk[c * nn + node] = out;
+        u_epilogue<T>(ep.mode, ep, y, ko + cn, cn, out, xv);
       }
     }
   }
@@ -531,7 +586,10 @@ __global__ void k_diag_A(Grid g, TabT<T> tb, double lam, double mu, T* __restric
 // host launchers
 template <typename T>
 void launch_apply_u(const Grid& g, const TabT<T>& tb, const SlabCoef& sc, const T* u, int64_t su, const T* p, int64_t sp, T* y,
-                    int64_t sy, cudaStream_t st) {
+                    int64_t sy, cudaStream_t st, const UEpi<T>* epi) {
+  UEpi<T> ep;
+  if (epi) ep = *epi;
+  else { ep = UEpi<T>(); ep.mode = EPI_NONE; }
   // columns: the nt temporal levels of every batched instance (or the caller's count)
   SlabCoef scu = sc;
   if (scu.ucols <= 0) { scu.ucols = sc.nt * g.nb; scu.udiv = g.nb; }
@@ -543,13 +601,13 @@ void launch_apply_u(const Grid& g, const TabT<T>& tb, const SlabCoef& sc, const 
     size_t smem = sizeof(T) * (3 * H3 * H3 * H3 + (ALLJ ? 12 : 4) * H3 * H3 * T3 + 12 * H3 * T3 * T3);
     const int kind = sizeof(T) == 4 ? 0 : 1;
     prof_begin(st, kind, (double)g.nnode * cols);
-    (note_launch(), k_apply_u3_col<T, ALLJ><<<grid, U3_THREADS, smem, st>>>(g, tb, scu, u, su, y, sy));
+    (note_launch(), k_apply_u3_col<T, ALLJ><<<grid, U3_THREADS, smem, st>>>(g, tb, scu, u, su, y, sy, ep));
     prof_end(st, kind);
   } else {
     dim3 grid((g.nu[0] + T2 - 1) / T2, (g.nu[1] + T2 - 1) / T2, cols);
     const int kind = sizeof(T) == 4 ? 0 : 1;
     prof_begin(st, kind, (double)g.nnode * cols);
-    (note_launch(), k_apply_u2<T><<<grid, 256, 0, st>>>(g, tb, scu, u, su, y, sy));
+    (note_launch(), k_apply_u2<T><<<grid, 256, 0, st>>>(g, tb, scu, u, su, y, sy, ep));
     prof_end(st, kind);
   }
   if (p) {
@@ -601,7 +659,7 @@ void apply_init_attributes() {
 
 #define INST(T)                                                                                                        \
   template void launch_apply_u<T>(const Grid&, const TabT<T>&, const SlabCoef&, const T*, int64_t, const T*, int64_t, T*, \
-                                  int64_t, cudaStream_t);                                                              \
+                                  int64_t, cudaStream_t, const UEpi<T>*);                                              \
   template void launch_apply_q<T>(const Grid&, const TabT<T>&, const SlabCoef&, const T*, const T*, int64_t, T*, int64_t, \
                                   cudaStream_t);                                                                       \
   template void launch_apply_p<T>(const Grid&, const TabT<T>&, const SlabCoef&, const T*, int64_t, T*, int64_t,         \

@@ -22,9 +22,21 @@ void prof_end(cudaStream_t st, int kind);
 void prof_collect(int kind, long long* n, double* ms, double* units);
 
 // ---- slab operator pieces (apply.cu) --------------------------------------
+// Optional fused output stage of the elasticity operator (multigrid smoothing and
+// residuals; arrays share the output's column layout, dinv is one column shared by all)
+enum { EPI_NONE = 0, EPI_CHEB = 1, EPI_RESID = 2 };
+template <typename T>
+struct UEpi {
+  int mode = EPI_NONE;
+  const T* b = nullptr;     // right-hand side (CHEB, RESID)
+  const T* dinv = nullptr;  // inverse Jacobi diagonal, 0 on constrained rows (CHEB)
+  T* d = nullptr;           // Chebyshev direction, updated in place (CHEB)
+  T* xo = nullptr;          // new iterate (CHEB; y is not written then)
+  T c1 = 0, c2 = 0;
+};
 template <typename T>
 void launch_apply_u(const Grid& g, const TabT<T>& tb, const SlabCoef& sc, const T* u, int64_t su, const T* p, int64_t sp, T* y,
-                    int64_t sy, cudaStream_t st);
+                    int64_t sy, cudaStream_t st, const UEpi<T>* epi = nullptr);
 template <typename T>
 void launch_apply_q(const Grid& g, const TabT<T>& tb, const SlabCoef& sc, const T* kscale, const T* x, int64_t sx, T* y,
                     int64_t sy, cudaStream_t st);

@@ -13,6 +13,9 @@ struct TabT {
   T bd[3][3][2];
   T mq[3][3][3];
   T wg[3];
+  // scale of the integer-tap reference rows per direction and operator: mass h/30,
+  // stiffness 1/(3h), G and G^T 1/6 (the elasticity kernels' constant-tap form)
+  T opscale[3][4];
 };
 
 // 1-D Q2 shape functions on [0,1] with nodes {0, 1/2, 1}
@@ -70,6 +73,10 @@ inline void build_tables(const Grid& g, TabT<double>& t) {
     for (int a = 0; a < 3; ++a)
       for (int b = 0; b < 3; ++b) t.mq[d][a][b] = (double)(Ml[a][b] * h / 30.0L);
     t.wg[d] = (double)(0.5L * h);
+    t.opscale[d][0] = (double)(h / 30.0L);
+    t.opscale[d][1] = (double)(1.0L / (3.0L * h));
+    t.opscale[d][2] = (double)(1.0L / 6.0L);
+    t.opscale[d][3] = (double)(1.0L / 6.0L);
   }
 }
 
