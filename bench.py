@@ -32,7 +32,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "slab solve time & space-time DoF/s at 1e-8 rel err: mixed-precision vs FP64, 1 GB300"
-WORKLOAD = ("3D Biot, unit cube, 32^3 hexes, Q2 displacement / RT1 flux / DGQ1 pressure, dG(1), T=1 in 16 slabs; "
+WORKLOAD = ("3D Biot, unit cube, {n}^3 hexes, Q2 displacement / RT1 flux / DGQ1 pressure, dG({r}), T=1 in {slabs} slabs; "
             "layered log-normal K (std 1.5, 4-cell z-layers, seed 1801); lambda=mu=1, b=0.8, 1/M=0.05; "
             "drained top with unit compressive load, roller/no-flow elsewhere")
 COEF = dict(lam=1.0, mu=1.0, b=0.8, invM=0.05, eta=1.0, K_dr=1.0 + 2.0 / 3.0)
@@ -377,7 +377,7 @@ def main():
         "metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD if (n, r, slabs) == (32, 1, 16) else "%s (n=%d, r=%d, slabs=%d)" % (WORKLOAD, n, r, slabs),
+        "config": {"workload": WORKLOAD.format(n=n, r=r, slabs=slabs),
                    "n_slab": ctx.n_slab, "slabs": slabs, "solver": "FGMRES(30) FP32 inner + FP64 refinement, tol 1e-10",
                    "l2": "256 MB buffer written before every timed step (> 129 MB L2)",
                    "parallelism": "replicas" if ws > 1 else "single GPU"},

@@ -363,6 +363,43 @@ class Context:
                                                      _ptr(f, torch.float64, self.n_space, "f"), _stream()))
 
 
+def _goal_function_class():
+    import torch
+
+    class GoalOfLogK(torch.autograd.Function):
+        """J(g) = j^T U(T^-) as a differentiable function of the cellwise log-permeability g
+        (K = K0 exp(g)).  forward runs biot_adjoint_grad, which returns J and dJ/dg together
+        (the dual problem marched backwards with checkpoint recomputation); backward scales
+        that gradient by the incoming one.  No arithmetic of the method runs in Python."""
+
+        @staticmethod
+        def forward(fctx, g, context, K0, T, slabs, f_terms, tcoef, U0, j_goal, tol, mode):
+            gh = g.detach().to("cpu", torch.float64).numpy()
+            context.set_permeability(np.asarray(K0, dtype=np.float64) * np.exp(gh))
+            dJ = torch.zeros(context.n_cells, dtype=torch.float64, device=j_goal.device)
+            J = context.adjoint_grad(T, slabs, f_terms, tcoef, U0, j_goal, dJ, tol=tol, mode=mode)
+            fctx.save_for_backward(dJ)
+            return torch.tensor(J, dtype=torch.float64, device=g.device)
+
+        @staticmethod
+        def backward(fctx, gout):
+            (dJ,) = fctx.saved_tensors
+            return (gout * dJ).to(gout.device), None, None, None, None, None, None, None, None, None, None
+
+    return GoalOfLogK
+
+
+_GOAL = None
+
+
+def goal_of_logk(context, g, K0, T, slabs, f_terms, tcoef, U0, j_goal, tol=1e-10, mode=FP64):
+    """Differentiable goal functional J(g) (torch scalar); g: float64 tensor of n_cells."""
+    global _GOAL
+    if _GOAL is None:
+        _GOAL = _goal_function_class()
+    return _GOAL.apply(g, context, K0, T, slabs, f_terms, tcoef, U0, j_goal, tol, mode)
+
+
 def make_mesh(dim, n, u_bc, f_bc, lo=None, hi=None):
     m = Mesh()
     m.dim = dim

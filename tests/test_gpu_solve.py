@@ -98,3 +98,40 @@ def test_adjoint_gradient_matches_oracle():
     g_ref = prob.grad_logk(1.0, slabs, Xs, Zs)
     rel = np.linalg.norm(dJ.cpu().numpy() - g_ref) / np.linalg.norm(g_ref)
     assert rel < 1e-8, rel
+
+
+def test_autograd_goal_gradient_is_the_adjoint_gradient():
+    """torch.autograd through the goal functional returns the adjoint gradient, and J
+    equals the goal weight applied to a forward march; a central difference along one
+    seeded direction agrees to the solver tolerance."""
+    from paper_1801_04984_gb300 import binding as B
+    from paper_1801_04984_gb300.inputs import layered_logk
+    n, r, slabs = (4, 4, 4), 1, 3
+    g0 = layered_logk(n, layer_cells=1, std=1.5, seed=5)
+    ubc, fbc = consolidation_bcs(3)
+    ctx = B.Context(3, n, dict(C2, K=1e-2 * np.exp(g0)), r, ubc, fbc)
+    f = torch.zeros(ctx.n_space, dtype=torch.float64, device="cuda")
+    ctx.load_preset(B.LOAD_TRACTION_TOP, 1.0, f)
+    j = torch.zeros_like(f)
+    ctx.goal_mean_pressure([0.4] * 3, [0.6] * 3, j)
+    U0 = torch.zeros_like(f)
+    g = torch.tensor(g0, device="cuda", requires_grad=True)
+    J = B.goal_of_logk(ctx, g, 1e-2, 1.0, slabs, [f], [[1, 0, 0, 0]], U0, j, tol=1e-13)
+    J.backward()
+    dJ = torch.zeros(ctx.n_cells, dtype=torch.float64, device="cuda")
+    ctx.set_permeability(1e-2 * np.exp(g0))
+    J_ref = ctx.adjoint_grad(1.0, slabs, [f], [[1, 0, 0, 0]], U0, j, dJ, tol=1e-13)
+    assert J.item() == J_ref and torch.equal(g.grad, dJ)
+    U = torch.zeros_like(f)
+    ctx.march(1.0, slabs, [f], [[1, 0, 0, 0]], U0, U, tol=1e-13)
+    assert abs(J_ref - torch.dot(j, U).item()) < 1e-10 * abs(J_ref)
+    d = np.random.default_rng(7).normal(size=ctx.n_cells)
+    eps = 1e-5
+    Jp = B.goal_of_logk(ctx, torch.tensor(g0 + eps * d, device="cuda"), 1e-2, 1.0, slabs, [f], [[1, 0, 0, 0]], U0, j,
+                        tol=1e-13).item()
+    Jm = B.goal_of_logk(ctx, torch.tensor(g0 - eps * d, device="cuda"), 1e-2, 1.0, slabs, [f], [[1, 0, 0, 0]], U0, j,
+                        tol=1e-13).item()
+    fd = (Jp - Jm) / (2 * eps)
+    ad = float(dJ.cpu().numpy() @ d)
+    assert abs(fd - ad) < 1e-6 * abs(ad), (fd, ad)
+    ctx.destroy()
