@@ -184,7 +184,8 @@ def run_batch(args):
     for it in range(args.warmup + args.steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        rc, status, stats = B.solve_batch(inst, workers=args.workers, tol=1e-8, mode=B.MIXED)
+        rc, status, stats = B.solve_batch(inst, workers=args.workers, tol=1e-8, mode=B.MIXED,
+                                          opts=dict(schur_mg=args.schur_mg) if args.schur_mg else None)
         torch.cuda.synchronize()
         if it >= args.warmup:
             times.append(time.perf_counter() - t0)
@@ -223,6 +224,8 @@ def main():
     ap.add_argument("--cheb-degree", type=int, default=0, help="elasticity smoother degree (0: library default)")
     ap.add_argument("--pair-coupling", type=int, default=0, help="0: block Gauss-Seidel on the complex pair, -1: dropped")
     ap.add_argument("--schur-degree", type=int, default=0, help="Schur Chebyshev degree (0: library default)")
+    ap.add_argument("--schur-mg", type=int, default=0,
+                    help="flow-block Schur solve: 0 library choice, 1 multigrid V-cycle, -1 Chebyshev")
     ap.add_argument("--beta-fs", type=float, default=-1.0,
                     help="fixed-stress parameter of the preconditioner (negative: b^2/K_dr)")
     args = ap.parse_args()
@@ -247,7 +250,7 @@ def main():
     ubc, fbc = consolidation_bcs(3)
     ctx = B.Context(3, (n, n, n), dict(COEF, K=K0 * np.exp(g)), r, ubc, fbc,
                     opts=dict(cheb_degree=args.cheb_degree, schur_degree=args.schur_degree,
-                              pair_coupling=args.pair_coupling, beta_fs=args.beta_fs))
+                              pair_coupling=args.pair_coupling, beta_fs=args.beta_fs, schur_mg=args.schur_mg))
     dev = torch.device("cuda", torch.cuda.current_device())
     f = torch.zeros(ctx.n_space, dtype=torch.float64, device=dev)
     ctx.load_preset(B.LOAD_TRACTION_TOP, 1.0, f)

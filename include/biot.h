@@ -112,6 +112,11 @@ typedef struct {
   int pair_coupling;    /* complex eigen-pair of the time matrix (r >= 1): 0 (default) applies one block
                            Gauss-Seidel sweep with the +-beta S coupling; -1 drops the coupling (the
                            paper's diagonal-blockwise L_j preconditioner) */
+  int schur_mg;         /* flux-pressure Schur solve with the lumped Darcy mass: 1 one V-cycle of a
+                           cell-centred multigrid (Gauss points aggregated per cell, then 2^d cells per
+                           coarse cell); -1 Chebyshev-Jacobi of degree schur_degree; 0 (default) chooses:
+                           the V-cycle in 2-D when the Lanczos estimate of cond(Dinv Schur) exceeds 600,
+                           Chebyshev otherwise */
 } biot_opts;
 
 typedef struct {

@@ -39,7 +39,8 @@ class Coeffs(C.Structure):
 
 class Opts(C.Structure):
     _fields_ = [("gmres_restart", C.c_int), ("cheb_degree", C.c_int), ("schur_degree", C.c_int),
-                ("mg_min_cells", C.c_int), ("beta_fs", C.c_double), ("flux_mass_exact", C.c_int), ("pair_coupling", C.c_int)]
+                ("mg_min_cells", C.c_int), ("beta_fs", C.c_double), ("flux_mass_exact", C.c_int), ("pair_coupling", C.c_int),
+                ("schur_mg", C.c_int)]
 
 
 class SolveOpts(C.Structure):
@@ -163,7 +164,7 @@ class Context:
         self.K = np.ascontiguousarray(np.asarray(coeffs["K"], dtype=np.float64))
         co = Coeffs(coeffs["b"], coeffs["invM"], coeffs["K_dr"], coeffs["lam"], coeffs["mu"], coeffs["eta"],
                     self.K.ctypes.data_as(C.POINTER(C.c_double)))
-        o = Opts(0, 0, 0, 0, -1.0, 0, 0)
+        o = Opts(0, 0, 0, 0, -1.0, 0, 0, 0)
         if opts:
             for k, v in opts.items():
                 setattr(o, k, v)
@@ -438,7 +439,7 @@ def solve_batch(instances, workers=0, tol=1e-10, mode=MIXED, inner_tol=1e-5, max
         it.U0 = None
         out = ins.get("U_end")
         it.U_end = out.ctypes.data if out is not None else None
-    o = Opts(0, 0, 0, 0, -1.0, 0, 0)
+    o = Opts(0, 0, 0, 0, -1.0, 0, 0, 0)
     if opts:
         for k, v in opts.items():
             setattr(o, k, v)

@@ -279,6 +279,11 @@ struct PrecWork {
   T *gp = nullptr, *pp = nullptr, *pd = nullptr, *pAx = nullptr, *pxo = nullptr, *pdinv = nullptr;  // nt * Np
   T* scoef = nullptr;  // 16 * Np: lumped Schur stencil for schur_tau
   double schur_tau = -1.0;
+  // cell-centred multigrid of the Schur complement: level l >= 1 stencils (per instance) and
+  // level vectors (per column); pmr0 holds the level-0 residual
+  std::vector<PDims> pml;
+  std::vector<T*> pms, pmb, pmx, pmd, pmt;
+  T* pmr0 = nullptr;
 };
 
 struct GraphKey {
@@ -321,6 +326,7 @@ struct biot_ctx {
   TimeBasis tb;
   biot_opts opts;
   double schur_lmax = 0, schur_lmax_tau = -1, schur_lmin = 0;
+  double schur_kappa = 1;      // Lanczos estimate of cond(Dinv Shat) for schur_lmax_tau
   Krylov<double> k64;
   Krylov<float> k32;
   PrecWork<double> p64;
@@ -789,10 +795,24 @@ double schur_lmax(biot_ctx& c, double tau, cudaStream_t st) {
   double lmin = 0;
   double lm = lanczos_lmax(c, op, w.pdinv, g.Np, g.Np, g.Np, cols, 30, w.gp, w.pp, w.pd, w.pAx, st, &lmin, c.nb);
   c.schur_lmax = lm;
+  c.schur_kappa = lmin > 0 ? lm / lmin : 1e300;
   // Ritz values converge from inside the spectrum: widen the lower end, keep it positive
   c.schur_lmin = std::max(0.7 * lmin, lm / 200.0);
   c.schur_lmax_tau = tau;
   return lm;
+}
+
+// Flow-block solver choice (after schur_lmax for this tau).  Chebyshev(degree) converges
+// at a rate set by sqrt(kappa) of the Jacobi-scaled Schur complement; when the Darcy part
+// dominates the storage part (large tau K / h^2) kappa grows like h^-2 and the multigrid
+// V-cycle wins.  Measured on the 2-D batching workload (kappa 173, 400, 918, 2004 for
+// n = 16, 32, 64, 128): multigrid faster from kappa ~900 on; in 3-D (32^3 dG(1) and
+// 64^3 dG(2)) Chebyshev was faster in every case measured.
+constexpr double PMG_KAPPA_2D = 600.0;
+bool use_schur_mg(const biot_ctx& c) {
+  if (c.opts.schur_mg > 0) return true;
+  if (c.opts.schur_mg < 0 || !c.lumped_flux) return false;
+  return c.g.dim == 2 && c.schur_kappa > PMG_KAPPA_2D;
 }
 
 // Jacobi diagonal of every column and the lumped Schur stencil of every instance for this tau
@@ -806,6 +826,110 @@ void schur_prepare(biot_ctx& c, double tau, cudaStream_t st) {
   launch_schur_dinv<T>(g, c.tab<T>(), c.sb2<T>(), cm_all, tau, w.pdinv, c.nt * c.nb, st);
   for (int b = 0; b < c.nb; ++b)
     launch_schur_stencil<T>(g, c.tab<T>(), c.dmq<T>() + b * nqt, tau, w.scoef + (int64_t)b * 16 * g.Np, st);
+  CKL();
+  if (use_schur_mg(c)) {
+    // Galerkin stencils of the cell levels: 2^d Gauss points -> cell, then 2^d cells -> cell
+    if (w.pml.empty()) {
+      const int cols = c.nt * c.nb;
+      PDims p;
+      for (int d = 0; d < 3; ++d) p.n[d] = g.n[d];
+      p.nc = g.ncells;
+      while (true) {
+        w.pml.push_back(p);
+        w.pms.push_back(dalloc<T>((int64_t)(1 + 2 * g.dim) * p.nc * c.nb));
+        for (auto* v : {&w.pmb, &w.pmx, &w.pmd, &w.pmt}) v->push_back(dalloc<T>(p.nc * cols));
+        bool can = true;
+        for (int d = 0; d < g.dim; ++d)
+          if (p.n[d] % 2 != 0 || p.n[d] / 2 < 2) can = false;
+        if (!can) break;
+        for (int d = 0; d < g.dim; ++d) p.n[d] /= 2;
+        p.nc = 1;
+        for (int d = 0; d < g.dim; ++d) p.nc *= p.n[d];
+      }
+      w.pmr0 = dalloc<T>(g.Np * cols);
+    }
+    launch_pmg_build1<T>(g, w.scoef, w.pms[0], st);
+    for (size_t l = 1; l < w.pml.size(); ++l)
+      launch_pmg_coarsen<T>(g.dim, w.pml[l - 1], w.pml[l], c.nb, w.pms[l - 1], w.pms[l], st);
+    CKL();
+  }
+}
+
+// One V-cycle of the cell-centred multigrid on the lumped Schur complement for the
+// columns k0.. (nk levels x nb instances): right-hand side w.gp, result w.pp.  Chebyshev-
+// Jacobi smoothing on every level (level 0 with the Lanczos bound, cell levels with the
+// Gershgorin bound 2 of the Jacobi-scaled diagonally dominant stencils); coarse corrections
+// are scaled by PMG_ALPHA, which offsets the stiffness that piecewise-constant aggregation
+// gives the Galerkin operators of a Laplacian-type block.
+constexpr int PMG_NU = 2;          // smoothing steps before and after the coarse correction
+constexpr int PMG_COARSE = 8;      // Chebyshev steps on the coarsest level
+constexpr double PMG_ALPHA = 1.6;  // coarse-correction scale (measured best of 1.0, 1.3, 1.6 in 2-D)
+template <typename T>
+void schur_vcycle(biot_ctx& c, double tau, const double* cm, double lmax0, int k0, int nk, cudaStream_t st) {
+  PrecWork<T>& w = c.pw<T>();
+  const Grid& g = c.g;
+  const int cols = nk * c.nb;
+  const int dim = g.dim;
+  const T* dinv = w.pdinv + (int64_t)k0 * c.nb * g.Np;
+  ChebCoef c0 = cheb_coefs(PMG_NU, lmax0 / 6.0, 1.1 * lmax0);
+  ChebCoef cl = cheb_coefs(PMG_NU, 2.2 / 6.0, 2.2);
+  ChebCoef cc = cheb_coefs(PMG_COARSE, 0.02, 2.2);
+  double mp = 1.0;
+  for (int d = 0; d < dim; ++d) mp *= c.t64.wg[d];
+  // level 0 pre-smoothing from zero (w.gp -> w.pp)
+  for (int k = 0; k < PMG_NU; ++k) {
+    launch_schur_cheb_st<T>(g, c.tab<T>(), w.scoef, dinv, cm, c0.c1[k], c0.c2[k], k == 0 ? 1 : 0, w.gp, w.pp, w.pd, w.pxo, cols, st);
+    std::swap(w.pp, w.pxo);
+  }
+  launch_pmg_resid0<T>(g, w.scoef, cm, w.gp, w.pp, w.pmr0, cols, st);
+  const PDims p0 = pdims_points(g);
+  launch_pmg_restrict<T>(dim, p0, w.pml[0], w.pmr0, w.pmb[0], cols, st);
+  CKL();
+  const int L = (int)w.pml.size();
+  double ml = mp * (1 << dim);  // mass of a level-1 cell (Galerkin sum of its points)
+  std::vector<double> mls(L);
+  for (int l = 0; l < L; ++l) {
+    mls[l] = ml;
+    ml *= (1 << dim);
+  }
+  // down: smooth from zero, residual, restrict
+  for (int l = 0; l < L - 1; ++l) {
+    const PDims& pd = w.pml[l];
+    for (int k = 0; k < PMG_NU; ++k) {
+      launch_pmg_step<T>(dim, pd, w.pms[l], cm, mls[l], c.nb, cl.c1[k], cl.c2[k], k == 0 ? 1 : 0, w.pmb[l], w.pmx[l], w.pmd[l],
+                         w.pmt[l], cols, st);
+      std::swap(w.pmx[l], w.pmt[l]);
+    }
+    launch_pmg_step<T>(dim, pd, w.pms[l], cm, mls[l], c.nb, 0.0, 0.0, 2, w.pmb[l], w.pmx[l], w.pmd[l], w.pmt[l], cols, st);
+    launch_pmg_restrict<T>(dim, pd, w.pml[l + 1], w.pmt[l], w.pmb[l + 1], cols, st);
+    CKL();
+  }
+  // coarsest level: Chebyshev from zero
+  {
+    const int l = L - 1;
+    for (int k = 0; k < cc.n; ++k) {
+      launch_pmg_step<T>(dim, w.pml[l], w.pms[l], cm, mls[l], c.nb, cc.c1[k], cc.c2[k], k == 0 ? 1 : 0, w.pmb[l], w.pmx[l],
+                         w.pmd[l], w.pmt[l], cols, st);
+      std::swap(w.pmx[l], w.pmt[l]);
+    }
+    CKL();
+  }
+  // up: prolong the correction, smooth
+  for (int l = L - 2; l >= 0; --l) {
+    const PDims& pd = w.pml[l];
+    launch_pmg_prolong<T>(dim, pd, w.pml[l + 1], w.pmx[l + 1], w.pmx[l], PMG_ALPHA, cols, st);
+    for (int k = 0; k < PMG_NU; ++k) {
+      launch_pmg_step<T>(dim, pd, w.pms[l], cm, mls[l], c.nb, cl.c1[k], cl.c2[k], 0, w.pmb[l], w.pmx[l], w.pmd[l], w.pmt[l], cols,
+                         st);
+      std::swap(w.pmx[l], w.pmt[l]);
+    }
+    CKL();
+  }
+  launch_pmg_prolong<T>(dim, p0, w.pml[0], w.pmx[0], w.pp, PMG_ALPHA, cols, st);
+  for (int k = 0; k < PMG_NU; ++k) {
+    launch_schur_cheb_st<T>(g, c.tab<T>(), w.scoef, dinv, cm, c0.c1[k], c0.c2[k], 0, w.gp, w.pp, w.pd, w.pxo, cols, st);
+    std::swap(w.pp, w.pxo);
+  }
   CKL();
 }
 
@@ -825,6 +949,10 @@ void schur_solve(biot_ctx& c, double tau, cudaStream_t st, int k0, int nk) {
       w.schur_tau = tau;
     }
     const T* dinv = w.pdinv + (int64_t)k0 * c.nb * g.Np;
+    if (use_schur_mg(c) && !w.pml.empty()) {
+      schur_vcycle<T>(c, tau, cm, lmax, k0, nk, st);
+      return;
+    }
     for (int k = 0; k < cc.n; ++k) {
       launch_schur_cheb_st<T>(g, c.tab<T>(), w.scoef, dinv, cm, cc.c1[k], cc.c2[k], k == 0 ? 1 : 0, w.gp, w.pp, w.pd, w.pxo,
                               nk * c.nb, st);
@@ -1794,6 +1922,7 @@ int setup_impl(const biot_mesh* mesh, const biot_coeffs* co, int r, const biot_o
     d.beta_fs = -1;
     d.flux_mass_exact = 0;
     d.pair_coupling = 1;
+    d.schur_mg = 0;
     if (opts) {
       if (opts->gmres_restart > 0) d.gmres_restart = std::min(opts->gmres_restart, 60);
       if (opts->cheb_degree > 0) d.cheb_degree = std::min(opts->cheb_degree, MAX_CHEB);
@@ -1802,6 +1931,7 @@ int setup_impl(const biot_mesh* mesh, const biot_coeffs* co, int r, const biot_o
       d.beta_fs = opts->beta_fs;
       d.flux_mass_exact = opts->flux_mass_exact ? 1 : 0;
       d.pair_coupling = opts->pair_coupling >= 0 ? 1 : 0;
+      d.schur_mg = opts->schur_mg > 0 ? 1 : (opts->schur_mg < 0 ? -1 : 0);
     }
     c->opts = d;
     c->lumped_flux = d.flux_mass_exact ? 0 : 1;
@@ -2310,7 +2440,12 @@ extern "C" void biot_destroy(biot_t c) {
   if (c->ev_in) cudaEventDestroy(c->ev_in);
   if (c->ev_out) cudaEventDestroy(c->ev_out);
   if (c->ws) cudaStreamDestroy(c->ws);
-  auto FP = [&](auto& w) { F(w.tA); F(w.tB); F(w.fq); F(w.tq); F(w.fq2); F(w.gp); F(w.pp); F(w.pd); F(w.pAx); F(w.pxo); F(w.pdinv); F(w.scoef); };
+  auto FP = [&](auto& w) {
+    F(w.tA); F(w.tB); F(w.fq); F(w.tq); F(w.fq2); F(w.gp); F(w.pp); F(w.pd); F(w.pAx); F(w.pxo); F(w.pdinv); F(w.scoef);
+    for (auto* v : {&w.pms, &w.pmb, &w.pmx, &w.pmd, &w.pmt})
+      for (auto p : *v) F(p);
+    F(w.pmr0);
+  };
   FP(c->p64); FP(c->p32);
   for (void* p : c->extra) F(p);
   for (int m = 0; m < 8; ++m) F(c->m_f[m]);

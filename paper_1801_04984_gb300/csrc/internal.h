@@ -170,6 +170,26 @@ void launch_schur_stencil(const Grid& g, const TabT<T>& tb, const T* dmq, double
 template <typename T>
 void launch_schur_cheb_st(const Grid& g, const TabT<T>& tb, const T* coef, const T* dinv, const double* cm, double c1, double c2,
                           int first, const T* b, const T* x, T* d, T* xo, int nrhs, cudaStream_t st);
+// cell-centred multigrid for the lumped Schur complement (mg.cu): grid sizes of one level
+struct PDims {
+  int n[3];
+  int64_t nc;
+};
+PDims pdims_points(const Grid& g);  // the Gauss-point pressure grid (level 0)
+template <typename T>
+void launch_pmg_resid0(const Grid& g, const T* coef, const double* cm, const T* b, const T* x, T* r, int ncols, cudaStream_t st);
+template <typename T>
+void launch_pmg_build1(const Grid& g, const T* coef, T* st1, cudaStream_t st);
+template <typename T>
+void launch_pmg_coarsen(int dim, const PDims& fd, const PDims& cd, int nb, const T* stf, T* stc, cudaStream_t st);
+// mode 0: Chebyshev-Jacobi step, 1: first step from zero, 2: residual b - A x into xo
+template <typename T>
+void launch_pmg_step(int dim, const PDims& pd, const T* stl, const double* cm, double ml, int nb, double c1, double c2, int mode,
+                     const T* b, const T* x, T* d, T* xo, int ncols, cudaStream_t st);
+template <typename T>
+void launch_pmg_restrict(int dim, const PDims& fd, const PDims& cd, const T* rf, T* rc, int ncols, cudaStream_t st);
+template <typename T>
+void launch_pmg_prolong(int dim, const PDims& fd, const PDims& cd, const T* xc, T* xf, double alpha, int ncols, cudaStream_t st);
 template <typename T>
 void launch_dinv_mul(const T* dinv, int64_t dstride, const T* r, T* z, int64_t n, int64_t stride, int nrhs, cudaStream_t st);
 // exact (s Mq)^{-1} by line solves (flux-block arrays); constrained entries untouched

@@ -910,6 +910,35 @@ __global__ void k_schur_stencil(Grid g, TabT<T> tb, const T* __restrict__ dmq, d
     }
 }
 
+// (Shat_r x)_t with the precomputed stencil of one instance (coef) and the mass term of column r
+template <typename T, int DIM>
+__device__ __forceinline__ T schur_stencil_eval(const Grid& g, const T* __restrict__ coef, T mass, const T* __restrict__ xr,
+                                                int64_t t) {
+  const int64_t np = g.Np;
+  const int ng0 = g.ng[0], ng1 = g.ng[1];
+  const int c0 = (int)(t % ng0);
+  const int64_t rr = t / ng0;
+  const int co[3] = {c0, (int)(rr % ng1), (int)(rr / ng1)};
+  const int64_t pst[3] = {1, ng0, (int64_t)ng0 * ng1};
+  T acc = (mass + coef[t]) * xr[t];
+#pragma unroll
+  for (int c = 0; c < DIM; ++c) {
+    const int cc = co[c];
+    const int64_t base = t - (int64_t)cc * pst[c];  // along-c coordinate 0 of this line
+    acc += coef[(1 + c) * np + t] * xr[base + (int64_t)(cc ^ 1) * pst[c]];
+    const int e2 = cc & ~1;  // 2 * cell
+    if (e2 >= 2) {
+      acc += coef[(1 + DIM + 4 * c) * np + t] * xr[base + (int64_t)(e2 - 2) * pst[c]];
+      acc += coef[(1 + DIM + 4 * c + 1) * np + t] * xr[base + (int64_t)(e2 - 1) * pst[c]];
+    }
+    if (e2 + 2 < g.ng[c]) {
+      acc += coef[(1 + DIM + 4 * c + 2) * np + t] * xr[base + (int64_t)(e2 + 2) * pst[c]];
+      acc += coef[(1 + DIM + 4 * c + 3) * np + t] * xr[base + (int64_t)(e2 + 3) * pst[c]];
+    }
+  }
+  return acc;
+}
+
 // Chebyshev-Jacobi step on Shat_r = cm[r] Mp + tau B diag(Mq)^{-1} B^T with the
 // precomputed stencil; dinv per rhs (stride Np).
 template <typename T, int DIM>
@@ -929,35 +958,172 @@ __global__ void __launch_bounds__(256) k_schur_cheb_st(Grid g, const T* __restri
     xo[i] = dn;
     return;
   }
-  const int ng0 = g.ng[0], ng1 = g.ng[1];
-  const int c0 = (int)(t % ng0);
-  const int64_t rr = t / ng0;
-  const int c1i = (int)(rr % ng1);
-  const int c2i = (int)(rr / ng1);
-  const int co[3] = {c0, c1i, c2i};
-  const int64_t pst[3] = {1, ng0, (int64_t)ng0 * ng1};
   const T* xr = x + r * np;
-  const T xs = xr[t];
-  T acc = (T(cm.c[r / g.nb]) * mp + coef[t]) * xs;
-#pragma unroll
-  for (int c = 0; c < DIM; ++c) {
-    const int cc = co[c];
-    const int64_t base = t - (int64_t)cc * pst[c];  // along-c coordinate 0 of this line
-    acc += coef[(1 + c) * np + t] * xr[base + (int64_t)(cc ^ 1) * pst[c]];
-    const int e2 = cc & ~1;  // 2 * cell
-    if (e2 >= 2) {
-      acc += coef[(1 + DIM + 4 * c) * np + t] * xr[base + (int64_t)(e2 - 2) * pst[c]];
-      acc += coef[(1 + DIM + 4 * c + 1) * np + t] * xr[base + (int64_t)(e2 - 1) * pst[c]];
-    }
-    if (e2 + 2 < g.ng[c]) {
-      acc += coef[(1 + DIM + 4 * c + 2) * np + t] * xr[base + (int64_t)(e2 + 2) * pst[c]];
-      acc += coef[(1 + DIM + 4 * c + 3) * np + t] * xr[base + (int64_t)(e2 + 3) * pst[c]];
-    }
-  }
+  const T acc = schur_stencil_eval<T, DIM>(g, coef, T(cm.c[r / g.nb]) * mp, xr, t);
   T dn = c2 * di * (b[i] - acc);
   if (c1 != T(0)) dn += c1 * d[i];
   d[i] = dn;
-  xo[i] = xs + dn;
+  xo[i] = xr[t] + dn;
+}
+
+// ---------------------------------------------------------------------------
+// Cell-centred multigrid for the lumped Schur complement (optional flow-block solver).
+// Level 0 is the Gauss-point pressure grid with the 16-coefficient stencil above.
+// Level 1 aggregates the 2^d points of each cell (piecewise-constant prolongation,
+// restriction = its transpose); further levels aggregate 2^d cells.  Coarse operators
+// are Galerkin products R S P: on the cell grids they are (2d+1)-point stencils stored
+// as [diag | lower_0 | upper_0 | lower_1 | ...] per instance (the K-dependent part; the
+// mass part cm[k] * mp * 2^(d l) is added per column).
+template <typename T, int DIM>
+__global__ void k_pmg_resid0(Grid g, const T* __restrict__ coef, RhsCoef cm, T mp, const T* __restrict__ b,
+                             const T* __restrict__ x, T* __restrict__ r_out, int ncols) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= g.Np) return;
+  const int r = blockIdx.y;
+  const int64_t np = g.Np;
+  const T* cf = coef + (int64_t)(r % g.nb) * 16 * np;
+  const T acc = schur_stencil_eval<T, DIM>(g, cf, T(cm.c[r / g.nb]) * mp, x + r * np, t);
+  r_out[r * np + t] = b[r * np + t] - acc;
+}
+
+// level-1 stencil of every cell from the level-0 point stencil (one instance per grid y)
+template <typename T, int DIM>
+__global__ void k_pmg_build1(Grid g, const T* __restrict__ coef, T* __restrict__ st) {
+  const int64_t cid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (cid >= g.ncells) return;
+  const int b = blockIdx.y;
+  const int64_t np = g.Np, nc = g.ncells;
+  const T* cf = coef + (int64_t)b * 16 * np;
+  T* so = st + (int64_t)b * (1 + 2 * DIM) * nc;
+  const int cx = (int)(cid % g.n[0]);
+  const int64_t rr = cid / g.n[0];
+  const int cy = (int)(rr % g.n[1]), cz = DIM == 3 ? (int)(rr / g.n[1]) : 0;
+  T diag = 0, lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+  for (int q = 0; q < (1 << DIM); ++q) {
+    const int px = 2 * cx + (q & 1), py = 2 * cy + ((q >> 1) & 1), pz = DIM == 3 ? 2 * cz + ((q >> 2) & 1) : 0;
+    const int64_t t = ((int64_t)pz * g.ng[1] + py) * g.ng[0] + px;
+    diag += cf[t];
+    for (int c = 0; c < DIM; ++c) {
+      diag += cf[(1 + c) * np + t];  // partner point of the same cell
+      lo[c] += cf[(1 + DIM + 4 * c) * np + t] + cf[(1 + DIM + 4 * c + 1) * np + t];
+      hi[c] += cf[(1 + DIM + 4 * c + 2) * np + t] + cf[(1 + DIM + 4 * c + 3) * np + t];
+    }
+  }
+  so[cid] = diag;
+  for (int c = 0; c < DIM; ++c) {
+    so[(1 + 2 * c) * nc + cid] = lo[c];
+    so[(2 + 2 * c) * nc + cid] = hi[c];
+  }
+}
+
+// Galerkin stencil of level l+1 (cells cn) from level l (cells fn): aggregate 2^d children
+template <typename T, int DIM>
+__global__ void k_pmg_coarsen(PDims fd, PDims cd, const T* __restrict__ stf, T* __restrict__ stc) {
+  const int64_t cid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (cid >= cd.nc) return;
+  const int b = blockIdx.y;
+  const T* sf = stf + (int64_t)b * (1 + 2 * DIM) * fd.nc;
+  T* sc = stc + (int64_t)b * (1 + 2 * DIM) * cd.nc;
+  const int cx = (int)(cid % cd.n[0]);
+  const int64_t rr = cid / cd.n[0];
+  const int cy = (int)(rr % cd.n[1]), cz = DIM == 3 ? (int)(rr / cd.n[1]) : 0;
+  T diag = 0, lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+  for (int q = 0; q < (1 << DIM); ++q) {
+    const int f[3] = {2 * cx + (q & 1), 2 * cy + ((q >> 1) & 1), DIM == 3 ? 2 * cz + ((q >> 2) & 1) : 0};
+    const int64_t fid = ((int64_t)f[2] * fd.n[1] + f[1]) * fd.n[0] + f[0];
+    diag += sf[fid];
+    for (int c = 0; c < DIM; ++c) {
+      const T l = sf[(1 + 2 * c) * fd.nc + fid], h = sf[(2 + 2 * c) * fd.nc + fid];
+      // a child's lower face is inside the parent when it is the upper child along c
+      if ((f[c] & 1) == 1) diag += l; else lo[c] += l;
+      if ((f[c] & 1) == 0) diag += h; else hi[c] += h;
+    }
+  }
+  sc[cid] = diag;
+  for (int c = 0; c < DIM; ++c) {
+    sc[(1 + 2 * c) * cd.nc + cid] = lo[c];
+    sc[(2 + 2 * c) * cd.nc + cid] = hi[c];
+  }
+}
+
+// (2d+1)-point stencil apply at cell cid of one column (mass m added to the diagonal)
+template <typename T, int DIM>
+__device__ __forceinline__ T pmg_eval(const PDims& pd, const T* __restrict__ st, T m, const T* __restrict__ x, int64_t cid,
+                                      T& diag) {
+  const int cx = (int)(cid % pd.n[0]);
+  const int64_t rr = cid / pd.n[0];
+  const int c3[3] = {cx, (int)(rr % pd.n[1]), DIM == 3 ? (int)(rr / pd.n[1]) : 0};
+  const int64_t str[3] = {1, pd.n[0], (int64_t)pd.n[0] * pd.n[1]};
+  diag = st[cid] + m;
+  T acc = diag * x[cid];
+#pragma unroll
+  for (int c = 0; c < DIM; ++c) {
+    if (c3[c] > 0) acc += st[(1 + 2 * c) * pd.nc + cid] * x[cid - str[c]];
+    if (c3[c] + 1 < pd.n[c]) acc += st[(2 + 2 * c) * pd.nc + cid] * x[cid + str[c]];
+  }
+  return acc;
+}
+
+// Chebyshev-Jacobi step on a cell level (first: from x = 0) or its residual (resid = 1:
+// xo = b - A x); columns on grid y, instance = column % nb
+template <typename T, int DIM>
+__global__ void k_pmg_step(PDims pd, const T* __restrict__ st, RhsCoef cm, T ml, int nb, T c1, T c2, int mode,
+                           const T* __restrict__ b, const T* __restrict__ x, T* __restrict__ d, T* __restrict__ xo) {
+  const int64_t cid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (cid >= pd.nc) return;
+  const int r = blockIdx.y;
+  const int64_t i = r * pd.nc + cid;
+  const T* s = st + (int64_t)(r % nb) * (1 + 2 * DIM) * pd.nc;
+  const T m = T(cm.c[r / nb]) * ml;
+  if (mode == 1) {  // first Chebyshev step from zero
+    const T di = T(1) / (s[cid] + m);
+    const T dn = c2 * di * b[i];
+    d[i] = dn;
+    xo[i] = dn;
+    return;
+  }
+  T diag;
+  const T ax = pmg_eval<T, DIM>(pd, s, m, x + r * pd.nc, cid, diag);
+  if (mode == 2) {  // residual
+    xo[i] = b[i] - ax;
+    return;
+  }
+  T dn = c2 * (b[i] - ax) / diag;
+  if (c1 != T(0)) dn += c1 * d[i];
+  d[i] = dn;
+  xo[i] = x[i] + dn;
+}
+
+// restriction (sum over the 2^d children: points of a cell at level 0 -> 1, or cells)
+template <typename T, int DIM>
+__global__ void k_pmg_restrict(PDims fd, PDims cd, const T* __restrict__ rf, T* __restrict__ rc) {
+  const int64_t cid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (cid >= cd.nc) return;
+  const int r = blockIdx.y;
+  const int cx = (int)(cid % cd.n[0]);
+  const int64_t rr = cid / cd.n[0];
+  const int cy = (int)(rr % cd.n[1]), cz = DIM == 3 ? (int)(rr / cd.n[1]) : 0;
+  const T* src = rf + r * fd.nc;
+  T s = 0;
+  for (int q = 0; q < (1 << DIM); ++q) {
+    const int64_t f = ((int64_t)(DIM == 3 ? 2 * cz + ((q >> 2) & 1) : 0) * fd.n[1] + 2 * cy + ((q >> 1) & 1)) * fd.n[0] + 2 * cx +
+                      (q & 1);
+    s += src[f];
+  }
+  rc[r * cd.nc + cid] = s;
+}
+
+// prolongation: x_f += alpha * x_c(parent), piecewise constant
+template <typename T, int DIM>
+__global__ void k_pmg_prolong(PDims fd, PDims cd, const T* __restrict__ xc, T* __restrict__ xf, T alpha) {
+  const int64_t fid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (fid >= fd.nc) return;
+  const int r = blockIdx.y;
+  const int fx = (int)(fid % fd.n[0]);
+  const int64_t rr = fid / fd.n[0];
+  const int fy = (int)(rr % fd.n[1]), fz = DIM == 3 ? (int)(rr / fd.n[1]) : 0;
+  const int64_t p = ((int64_t)(fz >> 1) * cd.n[1] + (fy >> 1)) * cd.n[0] + (fx >> 1);
+  xf[r * fd.nc + fid] += alpha * xc[r * cd.nc + p];
 }
 
 template <typename T>
@@ -980,6 +1146,59 @@ void launch_schur_cheb_st(const Grid& g, const TabT<T>& tb, const T* coef, const
   else (note_launch(), k_schur_cheb_st<T, 2><<<grid, 256, 0, st>>>(g, coef, dinv, rc, T(mp), T(c1), T(c2), first, b, x, d, xo));
   if (sizeof(T) == 4) prof_end(st, 2);
 }
+PDims pdims_points(const Grid& g) {
+  PDims p;
+  for (int d = 0; d < 3; ++d) p.n[d] = g.ng[d];
+  p.nc = g.Np;
+  return p;
+}
+
+template <typename T>
+void launch_pmg_resid0(const Grid& g, const T* coef, const double* cm, const T* b, const T* x, T* r, int ncols, cudaStream_t st) {
+  RhsCoef rc;
+  const int nlev = (ncols + g.nb - 1) / g.nb;
+  for (int k = 0; k < MAXR; ++k) rc.c[k] = (k < nlev) ? cm[k] : 0.0;
+  double mp = 1.0;
+  for (int d = 0; d < g.dim; ++d) mp *= 0.5 * g.h[d];
+  dim3 grid((unsigned)((g.Np + 255) / 256), ncols);
+  if (g.dim == 3) (note_launch(), k_pmg_resid0<T, 3><<<grid, 256, 0, st>>>(g, coef, rc, T(mp), b, x, r, ncols));
+  else (note_launch(), k_pmg_resid0<T, 2><<<grid, 256, 0, st>>>(g, coef, rc, T(mp), b, x, r, ncols));
+}
+template <typename T>
+void launch_pmg_build1(const Grid& g, const T* coef, T* st1, cudaStream_t st) {
+  dim3 grid((unsigned)((g.ncells + 255) / 256), g.nb);
+  if (g.dim == 3) (note_launch(), k_pmg_build1<T, 3><<<grid, 256, 0, st>>>(g, coef, st1));
+  else (note_launch(), k_pmg_build1<T, 2><<<grid, 256, 0, st>>>(g, coef, st1));
+}
+template <typename T>
+void launch_pmg_coarsen(int dim, const PDims& fd, const PDims& cd, int nb, const T* stf, T* stc, cudaStream_t st) {
+  dim3 grid((unsigned)((cd.nc + 255) / 256), nb);
+  if (dim == 3) (note_launch(), k_pmg_coarsen<T, 3><<<grid, 256, 0, st>>>(fd, cd, stf, stc));
+  else (note_launch(), k_pmg_coarsen<T, 2><<<grid, 256, 0, st>>>(fd, cd, stf, stc));
+}
+template <typename T>
+void launch_pmg_step(int dim, const PDims& pd, const T* stl, const double* cm, double ml, int nb, double c1, double c2, int mode,
+                     const T* b, const T* x, T* d, T* xo, int ncols, cudaStream_t st) {
+  RhsCoef rc;
+  const int nlev = (ncols + nb - 1) / nb;
+  for (int k = 0; k < MAXR; ++k) rc.c[k] = (k < nlev) ? cm[k] : 0.0;
+  dim3 grid((unsigned)((pd.nc + 255) / 256), ncols);
+  if (dim == 3) (note_launch(), k_pmg_step<T, 3><<<grid, 256, 0, st>>>(pd, stl, rc, T(ml), nb, T(c1), T(c2), mode, b, x, d, xo));
+  else (note_launch(), k_pmg_step<T, 2><<<grid, 256, 0, st>>>(pd, stl, rc, T(ml), nb, T(c1), T(c2), mode, b, x, d, xo));
+}
+template <typename T>
+void launch_pmg_restrict(int dim, const PDims& fd, const PDims& cd, const T* rf, T* rc, int ncols, cudaStream_t st) {
+  dim3 grid((unsigned)((cd.nc + 255) / 256), ncols);
+  if (dim == 3) (note_launch(), k_pmg_restrict<T, 3><<<grid, 256, 0, st>>>(fd, cd, rf, rc));
+  else (note_launch(), k_pmg_restrict<T, 2><<<grid, 256, 0, st>>>(fd, cd, rf, rc));
+}
+template <typename T>
+void launch_pmg_prolong(int dim, const PDims& fd, const PDims& cd, const T* xc, T* xf, double alpha, int ncols, cudaStream_t st) {
+  dim3 grid((unsigned)((fd.nc + 255) / 256), ncols);
+  if (dim == 3) (note_launch(), k_pmg_prolong<T, 3><<<grid, 256, 0, st>>>(fd, cd, xc, xf, T(alpha)));
+  else (note_launch(), k_pmg_prolong<T, 2><<<grid, 256, 0, st>>>(fd, cd, xc, xf, T(alpha)));
+}
+
 #define INSTMG(T)                                                                                                   \
   template void launch_prolong_add<T>(const Grid&, const Grid&, const T*, int64_t, T*, int64_t, int, cudaStream_t); \
   template void launch_restrict<T>(const Grid&, const Grid&, const T*, int64_t, T*, int64_t, int, cudaStream_t);    \
@@ -1014,7 +1233,14 @@ void launch_schur_cheb_st(const Grid& g, const TabT<T>& tb, const T* coef, const
   template void launch_cheb_update_r<T>(const T*, const T*, const T*, T*, const T*, T*, double, double, int, int64_t, int, \
                                         cudaStream_t);                                                              \
   template void launch_u_rhs<T>(const Grid&, const TabT<T>&, const T*, int64_t, const T*, int64_t, double, T*, int64_t, \
-                                int, cudaStream_t);
+                                int, cudaStream_t);                                                                 \
+  template void launch_pmg_resid0<T>(const Grid&, const T*, const double*, const T*, const T*, T*, int, cudaStream_t); \
+  template void launch_pmg_build1<T>(const Grid&, const T*, T*, cudaStream_t);                                     \
+  template void launch_pmg_coarsen<T>(int, const PDims&, const PDims&, int, const T*, T*, cudaStream_t);           \
+  template void launch_pmg_step<T>(int, const PDims&, const T*, const double*, double, int, double, double, int,     \
+                                   const T*, const T*, T*, T*, int, cudaStream_t);                                  \
+  template void launch_pmg_restrict<T>(int, const PDims&, const PDims&, const T*, T*, int, cudaStream_t);          \
+  template void launch_pmg_prolong<T>(int, const PDims&, const PDims&, const T*, T*, double, int, cudaStream_t);
 INSTMG(double)
 INSTMG(float)
 

@@ -135,3 +135,24 @@ def test_autograd_goal_gradient_is_the_adjoint_gradient():
     ad = float(dJ.cpu().numpy() @ d)
     assert abs(fd - ad) < 1e-6 * abs(ad), (fd, ad)
     ctx.destroy()
+
+
+@pytest.mark.parametrize("n,r", [((16, 16), 1), ((4, 4, 4), 1), ((32, 16), 0)])
+def test_schur_multigrid_solves_match_direct_solve(n, r):
+    """The flow block solved by one cell-centred multigrid V-cycle (opts schur_mg = 1):
+    FP64 and mixed-precision slab solves still reach the direct solve's solution."""
+    from paper_1801_04984_gb300 import binding as B
+    rng = np.random.default_rng(21)
+    K = 1e-2 * np.exp(rng.normal(0, 1.5, size=int(np.prod(n))))
+    ubc, fbc = consolidation_bcs(len(n))
+    ctx = B.Context(len(n), n, dict(C2, K=K), r, ubc, fbc, opts=dict(schur_mg=1))
+    prob = SlabProblem(Mesh(n), dict(C2, K=K), r, ubc, fbc)
+    tau = 1.0 / 8
+    rhs = prob.mask * rng.normal(size=prob.Nslab)
+    x_ref = prob.factor(tau, "radau").solve(rhs)
+    for mode in (B.FP64, B.MIXED):
+        x = torch.zeros(prob.Nslab, dtype=torch.float64, device="cuda")
+        st = ctx.solve_slab(tau, torch.tensor(rhs, device="cuda"), x, tol=1e-11, mode=mode)
+        rel = np.linalg.norm(x.cpu().numpy() - x_ref) / np.linalg.norm(x_ref)
+        assert rel < 1e-8 and st["rel_residual"] < 1e-11, (mode, rel, st)
+    ctx.destroy()
