@@ -101,6 +101,17 @@ def hbm_peak_measured(root):
         return 6800.0
 
 
+def whole_job_rate(units_per_rank, t_local, world_size, device=None):
+    """Replica runs: every rank processed units_per_rank in t_local seconds; the job took as
+    long as its slowest rank (max over ranks).  Returns (whole-job units/s, job seconds)."""
+    import torch
+    t = torch.tensor([float(t_local)], dtype=torch.float64, device=device)
+    if world_size > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    t_job = float(t.item())
+    return world_size * units_per_rank / t_job, t_job
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -304,13 +315,8 @@ def main():
     sch = ctx.kernel_stats(B.KERNEL_SCHUR_FP32)
     ctx.kernel_stats(B.KERNEL_ELASTICITY_FP64)
     ctx.profile(False)
-    t_step = float(np.mean(times))
-    if ws > 1:
-        tt = torch.tensor([t_step], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_step = tt.item()
     dofs_step = ctx.n_slab * slabs
-    value = ws * dofs_step / t_step
+    value, t_step = whole_job_rate(dofs_step, float(np.mean(times)), ws, dev)
 
     # end-to-end through the C ABI with host buffers
     f_host = f.cpu().numpy().copy()
