@@ -1379,7 +1379,7 @@ int solve_slab_batch(biot_ctx& c, double tau, const double* rhs, double* x, cons
   }
   std::vector<char> done(nb, 0);
   for (int i = 0; i < nb; ++i) done[i] = bn[i] == 0.0;
-  int refs = 0, total = 0;
+  int total = 0;
   while (true) {
     apply_slab_T<double>(c, tau, x, c.r64, o.transpose, st);
     launch_axpby<double>(c.r64, rhs, 1.0, -1.0, n, st);
@@ -1416,7 +1416,6 @@ int solve_slab_batch(biot_ctx& c, double tau, const double* rhs, double* x, cons
     put_scalars(c, rn, 3, st);  // x_b += ||r_b|| d_b (0 for finished instances)
     launch_seg_add_scaled<double, float>(x, c.d32, c.bdev + bslot(c, 3), 1, sg, st);
     CKL();
-    ++refs;
   }
   CK(cudaStreamSynchronize(st));
   int rc = BIOT_OK;
@@ -1432,7 +1431,6 @@ int solve_slab_batch(biot_ctx& c, double tau, const double* rhs, double* x, cons
   s.refinements = refs_max;
   s.rel_residual = worst;
   s.seconds = now_s() - t0;
-  (void)refs;
   return rc;
 }
 
