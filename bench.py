@@ -218,6 +218,48 @@ def run_batch(args):
     return 0
 
 
+def run_apply(args):
+    """One slab-operator apply (FP64 and FP32) of the layered 3-D problem at n^3, dG(r), timed
+    with CUDA events (median of `steps`, L2 flushed before each), against the HBM roofline:
+    algorithmic bytes = read x + write y + one coefficient per cell, (2 N_slab + cells) x word."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_1801_04984_gb300 import binding as B
+    from paper_1801_04984_gb300.inputs import layered_logk, K0
+    n, r = args.n, args.r
+    g = layered_logk((n, n, n), layer_cells=4, std=1.5, seed=1801)
+    ubc, fbc = consolidation_bcs(3)
+    ctx = B.Context(3, (n, n, n), dict(COEF, K=K0 * np.exp(g)), r, ubc, fbc)
+    tau = 1.0 / args.slabs
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    out = {"config": {"workload": "one slab-operator apply: " + WORKLOAD.format(n=n, r=r, slabs=args.slabs),
+                      "n_slab": ctx.n_slab, "l2": "256 MB buffer written before every timed apply"}}
+    for dt, name in ((torch.float64, "fp64"), (torch.float32, "fp32")):
+        x = torch.randn(ctx.n_slab, dtype=dt, device="cuda")
+        y = torch.empty_like(x)
+        for _ in range(max(1, args.warmup)):
+            ctx.apply_slab(tau, x, y)
+        ts = []
+        for _ in range(max(1, args.steps)):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            ctx.apply_slab(tau, x, y)
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1) / 1e3)
+        t = float(np.median(ts))
+        algo = (2 * ctx.n_slab + ctx.n_cells) * x.element_size()
+        out[name] = {"ms": t * 1e3, "algorithmic_MB": algo / 1e6, "achieved_GBs": algo / t / 1e9,
+                     "hbm_peak_GBs": hbm_peak_measured(ROOT), "frac_of_hbm": algo / t / 1e9 / hbm_peak_measured(ROOT),
+                     "slab_dofs_per_s": ctx.n_slab / t}
+    ctx.destroy()
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -230,8 +272,9 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison march")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer run")
-    ap.add_argument("--config", default="march", choices=["march", "batch"],
-                    help="march: the 32^3 dG(1) headline; batch: 256 ragged 2-D instances")
+    ap.add_argument("--config", default="march", choices=["march", "batch", "apply"],
+                    help="march: the 32^3 dG(1) headline; batch: 256 ragged 2-D instances; "
+                         "apply: one slab-operator apply against the HBM roofline")
     ap.add_argument("--instances", type=int, default=256)
     ap.add_argument("--workers", type=int, default=0, help="batch: max instances per batched context (0: library default)")
     ap.add_argument("--cheb-degree", type=int, default=0, help="elasticity smoother degree (0: library default)")
@@ -246,6 +289,8 @@ def main():
         return run_reference(args)
     if args.config == "batch":
         return run_batch(args)
+    if args.config == "apply":
+        return run_apply(args)
 
     import torch
     ws, rank, local = dist_env()
