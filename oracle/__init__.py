@@ -19,6 +19,8 @@ Everything here is plain numpy/scipy in float64, written from the paper
 * `slab`      - the monolithic slab system, loads, constraints, direct solves,
   time marching, the goal functional and its adjoint (§Monolithic Approach).
 * `exact`     - closed forms: manufactured solutions and Terzaghi consolidation.
+* `dwr`       - dual-weighted residual indicators of the dG(r) time error against
+  dG(r+1) for a goal functional (§Abstract: duality-based adaptivity).
 
 Parity status: every function is pinned by `tests/test_oracle_*.py` except the
 Krylov/preconditioner iteration counts, which the oracle does not model

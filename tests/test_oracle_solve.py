@@ -247,3 +247,34 @@ def test_rowwise_apply_matches_assembled_operator(n, r):
     y = prob.operator(0.3, "radau") @ X
     rows = np.arange(prob.Nslab)
     assert np.abs(apply_rows(prob, 0.3, X, rows) - y).max() < 1e-13 * np.abs(y).max()
+
+
+@pytest.mark.parametrize("r", [0, 1])
+def test_dwr_time_indicators_sum_to_the_goal_difference(r):
+    """Dual-weighted residual of the dG(r) solution in the dG(r+1) system: the slab
+    indicators sum to J(U_{r+1}) - J(U_r), computed independently by two direct-solve
+    marches (an identity of the block-bidiagonal slab system), and they are not all of
+    one size: the first slabs, where the sudden load acts, carry most of the error."""
+    from oracle.dwr import dwr_time_indicators
+    n = (6, 4)
+    rng = np.random.default_rng(40 + r)
+    co = dict(C2, K=1e-2 * np.exp(rng.normal(0, 1.0, size=24)))
+    ubc, fbc = consolidation_bcs(2)
+    m = Mesh(n)
+    pr = SlabProblem(m, co, r, ubc, fbc)
+    pr1 = SlabProblem(m, co, r + 1, ubc, fbc)
+
+    def trac(X, t, f):
+        o = np.zeros((len(X), 2))
+        o[:, 1] = -1.0
+        return o
+    F = load_vector(m, 0.0, traction=trac, u_bc=ubc, f_bc=fbc)
+    j = goal_vector_mean_p(m, np.array([0.25, 0.25]), np.array([0.75, 0.75]))
+    eta, J_r = dwr_time_indicators(pr, pr1, 1.0, 5, lambda t: F, j)
+    _, U1 = pr1.march(1.0, 5, lambda t: F)
+    _, U0 = pr.march(1.0, 5, lambda t: F)
+    assert abs(J_r - j @ U0) < 1e-14 * abs(J_r)
+    diff = j @ U1 - j @ U0
+    # identity up to the rounding of the two goal values it is the difference of
+    assert abs(eta.sum() - diff) < 1e-12 * abs(J_r), (eta.sum(), diff, J_r)
+    assert abs(eta[0]) > abs(eta[-1])
