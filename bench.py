@@ -260,6 +260,43 @@ def run_apply(args):
     return 0
 
 
+def run_dwr(args):
+    """Goal-oriented time-error estimate of the layered 3-D march (dG(r) against dG(r+1),
+    J = mean pressure over [0.4, 0.6]^3 at T^-), mixed precision; device time of the
+    whole estimate (forward dG(r) march, backward dG(r+1) dual march, slab residuals)."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_1801_04984_gb300 import binding as B
+    from paper_1801_04984_gb300.inputs import layered_logk, K0
+    n, r, slabs = args.n, args.r, args.slabs
+    g = layered_logk((n, n, n), layer_cells=4, std=1.5, seed=1801)
+    ubc, fbc = consolidation_bcs(3)
+    co = dict(COEF, K=K0 * np.exp(g))
+    ctx = B.Context(3, (n, n, n), co, r, ubc, fbc)
+    ctx1 = B.Context(3, (n, n, n), co, r + 1, ubc, fbc)
+    f = torch.zeros(ctx.n_space, dtype=torch.float64, device="cuda")
+    ctx.load_preset(B.LOAD_TRACTION_TOP, 1.0, f)
+    j = torch.zeros_like(f)
+    ctx.goal_mean_pressure([0.4] * 3, [0.6] * 3, j)
+    U0 = torch.zeros_like(f)
+    times = []
+    for it in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        eta, eta_s, J = ctx.dwr_time_estimate(ctx1, 1.0, slabs, [f], [[1, 0, 0, 0]], U0, j, tol=1e-10, mode=B.MIXED)
+        torch.cuda.synchronize()
+        if it >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    t = float(np.mean(times))
+    line = {"metric": "goal-oriented time-error estimate (dual-weighted residual, dG(r) against dG(r+1))",
+            "value": t, "unit": "s", "higher_is_better": False, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD.format(n=n, r=r, slabs=slabs) + "; J = mean p over [0.4,0.6]^3 at T^-"},
+            "J": J, "eta": eta, "eta_per_slab": eta_s}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -272,9 +309,10 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison march")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer run")
-    ap.add_argument("--config", default="march", choices=["march", "batch", "apply"],
+    ap.add_argument("--config", default="march", choices=["march", "batch", "apply", "dwr"],
                     help="march: the 32^3 dG(1) headline; batch: 256 ragged 2-D instances; "
-                         "apply: one slab-operator apply against the HBM roofline")
+                         "apply: one slab-operator apply against the HBM roofline; "
+                         "dwr: goal-oriented time-error estimate")
     ap.add_argument("--instances", type=int, default=256)
     ap.add_argument("--workers", type=int, default=0, help="batch: max instances per batched context (0: library default)")
     ap.add_argument("--cheb-degree", type=int, default=0, help="elasticity smoother degree (0: library default)")
@@ -291,6 +329,8 @@ def main():
         return run_batch(args)
     if args.config == "apply":
         return run_apply(args)
+    if args.config == "dwr":
+        return run_dwr(args)
 
     import torch
     ws, rank, local = dist_env()

@@ -224,6 +224,22 @@ int biot_adjoint_grad(biot_t ctx, double T, int slabs, int nterms, const double*
                       const double* U0, const double* j_goal, const biot_solve_opts* opts, int recompute, double* J_out,
                       double* dJ_dlogK, void* stream);
 
+/* Goal-oriented estimate of the time-discretisation error (paper §Abstract:
+ * goal-oriented, duality-based adaptivity) of J = j^T U(T^-) for the dG(r)
+ * march of `ctx` against dG(r+1) (`ctx_r1`: same mesh, boundary codes and
+ * coefficients, time order r + 1).  The dG(r) slab solutions are embedded into
+ * the dG(r+1) slab system (a degree-r polynomial is a degree-(r+1) one) and their
+ * residuals are weighted with the dG(r+1) dual solution; eta_slab (HOST, slabs
+ * entries, may be NULL) receives the slab indicators eta_n, eta_out (HOST) their
+ * sum, which equals J(U_{r+1}) - J(U_r) up to the solver tolerances, and J_out
+ * (HOST) J(U_r).  Loads, U0 and j_goal as in biot_adjoint_grad; opts->mode as in
+ * biot_march (the dual solves use the transposed operator).  Allocates its
+ * temporaries (slabs + 1 states and every dG(r) slab solution) per call.  Errors:
+ * EINVAL for batched contexts, mismatched contexts or bad arguments. */
+int biot_dwr_time_estimate(biot_t ctx, biot_t ctx_r1, double T, int slabs, int nterms, const double* const* f_terms,
+                           const double* tcoef, const double* U0, const double* j_goal, const biot_solve_opts* opts,
+                           double* eta_slab, double* eta_out, double* J_out, void* stream);
+
 /* Batched marches: `count` independent instances, each with its own mesh,
  * coefficients (K_cell on the host), time order r, horizon T and slab count, and
  * either a built-in load (load_kind >= 0: one BIOT_LOAD_* preset of magnitude

@@ -95,6 +95,8 @@ def load(path: str = LIB_PATH):
         "biot_adjoint_grad": (C.c_int, [vp, C.c_double, C.c_int, C.c_int, C.POINTER(vp), dp, vp, vp,
                                         C.POINTER(SolveOpts), C.c_int, dp, vp, vp]),
         "biot_goal_mean_pressure": (C.c_int, [vp, dp, dp, vp, vp]),
+        "biot_dwr_time_estimate": (C.c_int, [vp, vp, C.c_double, C.c_int, C.c_int, C.POINTER(vp), dp, vp, vp,
+                                             C.POINTER(SolveOpts), dp, dp, dp, vp]),
         "biot_solve_batch": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(Opts), C.POINTER(SolveOpts), C.c_int, ip,
                                        C.c_void_p]),
         "biot_load_preset": (C.c_int, [vp, C.c_int, C.c_double, vp, vp]),
@@ -322,6 +324,23 @@ class Context:
                                         _stream())
         self._check(rc)
         return J.value
+
+    def dwr_time_estimate(self, ctx_r1, T, slabs, f_terms, tcoef, U0, j_goal, tol=1e-10, max_iters=2000, mode=FP64,
+                          inner_tol=1e-5):
+        """Dual-weighted residual estimate of the dG(r) time error of J = j^T U(T^-) against
+        dG(r+1) (biot_dwr_time_estimate).  Returns (eta, per-slab indicators, J(U_r))."""
+        import torch
+        nterms, arr, tc, keep = self._loads(f_terms, tcoef)
+        o = _solve_opts(tol, max_iters, mode, inner_tol, 0)
+        eta_s = (C.c_double * slabs)()
+        eta, J = C.c_double(), C.c_double()
+        rc = self.lib.biot_dwr_time_estimate(self.h, ctx_r1.h, float(T), int(slabs), nterms, arr,
+                                             tc.ctypes.data_as(C.POINTER(C.c_double)),
+                                             _ptr(U0, torch.float64, self.n_space, "U0"),
+                                             _ptr(j_goal, torch.float64, self.n_space, "j_goal"), C.byref(o), eta_s,
+                                             C.byref(eta), C.byref(J), _stream())
+        self._check(rc)
+        return eta.value, list(eta_s), J.value
 
     def goal_mean_pressure(self, lo, hi, j):
         import torch

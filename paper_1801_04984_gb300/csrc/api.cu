@@ -2169,6 +2169,101 @@ extern "C" int biot_adjoint_grad(biot_t c, double T, int slabs, int nterms, cons
   API_END(c)
 }
 
+// Dual-weighted residual estimate of the dG(r) time error of J = j^T U(T^-) against dG(r+1)
+// (paper §Abstract: goal-oriented, duality-based adaptivity).  The dG(r) slab solution X_n
+// embeds into the dG(r+1) system as Y_n = (Pi (x) I) X_n with Pi[k][l] = phi_l^(r)(s_k^(r+1));
+// with the dG(r+1) dual Z_n, eta_n = Z_n^T (F_n + C Y_{n-1} - calA Y_n) and sum eta_n equals
+// J(U_{r+1}) - J(U_r) up to the solver tolerances.
+extern "C" int biot_dwr_time_estimate(biot_t c, biot_t c1, double T, int slabs, int nterms, const double* const* f_terms,
+                                      const double* tcoef, const double* U0, const double* j_goal, const biot_solve_opts* opts,
+                                      double* eta_slab, double* eta_out, double* J_out, void* stream) {
+  API_BEGIN(c)
+  if (!c1 || !(T > 0) || slabs < 1 || !j_goal) fail(BIOT_EINVAL, "dwr: bad arguments");
+  if (c->nb > 1 || c1->nb > 1) fail(BIOT_EINVAL, "dwr: batched context");
+  if (c1->r != c->r + 1) fail(BIOT_EINVAL, "dwr: the second context must have time order r + 1");
+  const Grid& g = c->g;
+  {
+    const Grid& g1 = c1->g;
+    bool same = g.dim == g1.dim && g.N == g1.N;
+    for (int d = 0; d < 3; ++d) same = same && g.n[d] == g1.n[d] && g.h[d] == g1.h[d];
+    for (int f = 0; f < 6; ++f) same = same && g.ubc[f] == g1.ubc[f] && g.fbc[f] == g1.fbc[f];
+    same = same && c->b == c1->b && c->invM == c1->invM && c->lam == c1->lam && c->mu == c1->mu && c->eta == c1->eta &&
+           c->Kcell == c1->Kcell;
+    if (!same) fail(BIOT_EINVAL, "dwr: the two contexts must share mesh, boundary codes and coefficients");
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  biot_solve_opts o = solve_defaults(opts);
+  o.transpose = 0;
+  const int nt = c->nt, nt1 = c1->nt;
+  const int64_t N = g.N, ns = N * nt, ns1 = N * nt1;
+  const double tau = T / slabs;
+  // forward dG(r) march keeping every slab solution and the end states
+  double* ck = dalloc<double>((int64_t)(slabs + 1) * N);
+  double* Xall = dalloc<double>((int64_t)slabs * ns);
+  biot_stats s;
+  int rc = BIOT_OK;
+  march_impl(*c, T, slabs, nterms, f_terms, tcoef, U0, nullptr, Xall, ck, o, nullptr, s, st, rc);
+  const double J = dev_dot(*c, j_goal, ck + (int64_t)slabs * N, N, st);
+  // embedding of the dG(r) Radau-Lagrange basis into the dG(r+1) nodes
+  double Pi[MAXR * MAXR];
+  {
+    long double xr[MAXR];
+    for (int l = 0; l < nt; ++l) xr[l] = c->tb.nodes[l];
+    for (int k = 0; k < nt1; ++k)
+      for (int l = 0; l < nt; ++l) Pi[k * nt + l] = (double)lagr(xr, nt, l, (long double)c1->tb.nodes[k]);
+  }
+  MarchBufs mb1;
+  march_prepare(*c1, nterms, f_terms, nullptr, mb1, st);
+  double* Z = dalloc<double>(ns1);
+  double* zr = dalloc<double>(ns1);
+  double* Y = dalloc<double>(ns1);
+  double* R = dalloc<double>(ns1);
+  double* tmp = dalloc<double>(N);
+  double* zero = dalloc<double>(N);
+  CK(cudaMemsetAsync(zero, 0, N * sizeof(double), st));
+  CK(cudaMemsetAsync(zr, 0, ns1 * sizeof(double), st));
+  CK(cudaMemcpyAsync(zr + (int64_t)(nt1 - 1) * N, j_goal, N * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  launch_mask<double>(g, zr, N, nt1, st);
+  biot_solve_opts oa = o;
+  oa.transpose = 1;
+  double mp = 1.0;
+  for (int d = 0; d < g.dim; ++d) mp *= c1->t64.wg[d];
+  double eta = 0.0;
+  for (int nsl = slabs - 1; nsl >= 0; --nsl) {
+    // dG(r+1) dual of this slab
+    CK(cudaMemsetAsync(Z, 0, ns1 * sizeof(double), st));
+    biot_stats s3;
+    const int rc3 = solve_slab_impl(*c1, tau, zr, Z, oa, s3, st);
+    if (rc3 != BIOT_OK && rc == BIOT_OK) rc = rc3;
+    // residual of the embedded dG(r) solution in the dG(r+1) slab system
+    launch_time_embed(Xall + (int64_t)nsl * ns, N, nt, Y, N, nt1, Pi, N, st);
+    CK(cudaMemcpyAsync(mb1.U, ck + (int64_t)nsl * N, N * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    build_slab_rhs(*c1, nsl * tau, tau, nterms, tcoef, mb1, st);
+    apply_slab_T<double>(*c1, tau, Y, R, 0, st);
+    launch_axpby<double>(R, mb1.rhs, 1.0, -1.0, ns1, st);  // R = rhs - calA Y
+    CKL();
+    const double en = dev_dot(*c1, Z, R, ns1, st);
+    if (eta_slab) eta_slab[nsl] = en;
+    eta += en;
+    if (nsl > 0) {  // next dual right-hand side: C^T Z (level r+1 = S^T sum_k phi_k(0) Z_k)
+      CK(cudaMemsetAsync(tmp, 0, N * sizeof(double), st));
+      for (int k = 0; k < nt1; ++k) launch_axpby<double>(tmp, Z + k * N, c1->tb.phi0[k], 1.0, N, st);
+      CKL();
+      CK(cudaMemsetAsync(zr, 0, ns1 * sizeof(double), st));
+      double* zl = zr + (int64_t)(nt1 - 1) * N;
+      launch_u_rhs<double>(g, c1->t64, zero, N, tmp + g.offp, N, c1->b, zl, N, 1, st);
+      launch_axpby<double>(zl + g.offp, tmp + g.offp, c1->invM * mp, 0.0, g.Np, st);
+      CKL();
+    }
+  }
+  CK(cudaStreamSynchronize(st));
+  for (double* p : {Z, zr, Y, R, tmp, zero, ck, Xall}) cudaFree(p);
+  if (eta_out) *eta_out = eta;
+  if (J_out) *J_out = J;
+  return rc;
+  API_END(c)
+}
+
 extern "C" int biot_goal_mean_pressure(biot_t c, const double* lo, const double* hi, double* j, void* stream) {
   API_BEGIN(c)
   if (!lo || !hi || !j) fail(BIOT_EINVAL, "goal: NULL argument");

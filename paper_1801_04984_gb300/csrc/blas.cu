@@ -445,6 +445,29 @@ void launch_seg_add_scaled(TX* x, const TD* d, const double* s, int sstride, con
   (note_launch(), k_seg_add_scaled<TX, TD><<<dim3(seg_gx(sg.nb), sg.nb), 256, 0, st>>>(x, d, s, sstride, sg));
 }
 
+// rectangular time map: out[k] = sum_l C[k][l] in[l] for nt_out output and nt_in input
+// levels (the embedding of a dG(r) slab polynomial into the dG(r+1) nodal basis)
+template <typename T>
+__global__ void k_time_embed(const T* __restrict__ in, int64_t sin, int nin, T* __restrict__ out, int64_t sout, int nout,
+                             Mix<T> m, int64_t n) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    T v[MAXR];
+    for (int l = 0; l < nin; ++l) v[l] = in[l * sin + e];
+    for (int k = 0; k < nout; ++k) {
+      T s = 0;
+      for (int l = 0; l < nin; ++l) s += m.c[k][l] * v[l];
+      out[k * sout + e] = s;
+    }
+  }
+}
+void launch_time_embed(const double* in, int64_t sin, int nin, double* out, int64_t sout, int nout, const double* C, int64_t n,
+                       cudaStream_t st) {
+  Mix<double> m;
+  for (int k = 0; k < MAXR; ++k)
+    for (int l = 0; l < MAXR; ++l) m.c[k][l] = (k < nout && l < nin) ? C[k * nin + l] : 0.0;
+  (note_launch(), k_time_embed<double><<<RED_BLOCKS * 2, 256, 0, st>>>(in, sin, nin, out, sout, nout, m, n));
+}
+
 template void launch_multidot<double>(const double* const*, int, const double*, int64_t, double*, double*, cudaStream_t);
 template void launch_multidot<float>(const float* const*, int, const float*, int64_t, double*, double*, cudaStream_t);
 template void launch_multiaxpy_dot<double>(const double* const*, int, const double*, double*, int64_t, int, double*, double*,

@@ -96,6 +96,9 @@ void launch_seg_add_scaled(TX* x, const TD* d, const double* s, int sstride, con
 // y_r = a x_r + b y_r for rows r < rows of length n at stride s
 template <typename T>
 void launch_axpby_rows(T* y, const T* x, double a, double b, int64_t n, int rows, int64_t s, cudaStream_t st);
+// out[k] = sum_l C[k][l] in[l], k < nout, l < nin (C row-major nout x nin, both <= MAXR)
+void launch_time_embed(const double* in, int64_t sin, int nin, double* out, int64_t sout, int nout, const double* C, int64_t n,
+                       cudaStream_t st);
 // time transform: out[k] = sum_l C[k][l] in[l] over nt levels of length n (strided)
 template <typename TI, typename TO>
 void launch_time_mix(const TI* in, int64_t sin, TO* out, int64_t sout, int nt, const double* C, int64_t n, cudaStream_t st);

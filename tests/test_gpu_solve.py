@@ -156,3 +156,39 @@ def test_schur_multigrid_solves_match_direct_solve(n, r):
         rel = np.linalg.norm(x.cpu().numpy() - x_ref) / np.linalg.norm(x_ref)
         assert rel < 1e-8 and st["rel_residual"] < 1e-11, (mode, rel, st)
     ctx.destroy()
+
+
+@pytest.mark.parametrize("n,r", [((6, 4), 0), ((4, 4, 4), 1)])
+def test_dwr_time_estimate_matches_oracle(n, r):
+    """Dual-weighted residual time-error indicators of the dG(r) march against dG(r+1)
+    (C ABI biot_dwr_time_estimate) equal the oracle's slab by slab, and their sum equals
+    the goal difference of two GPU marches (dG(r+1) minus dG(r))."""
+    from paper_1801_04984_gb300 import binding as B
+    from oracle.dwr import dwr_time_indicators
+    rng = np.random.default_rng(50 + r)
+    K = 1e-2 * np.exp(rng.normal(0, 1.0, size=int(np.prod(n))))
+    d = len(n)
+    ubc, fbc = consolidation_bcs(d)
+    ctx = B.Context(d, n, dict(C2, K=K), r, ubc, fbc)
+    ctx1 = B.Context(d, n, dict(C2, K=K), r + 1, ubc, fbc)
+    f = torch.zeros(ctx.n_space, dtype=torch.float64, device="cuda")
+    ctx.load_preset(B.LOAD_TRACTION_TOP, 1.0, f)
+    j = torch.zeros_like(f)
+    lo, hi = [0.25] * d, [0.75] * d
+    ctx.goal_mean_pressure(lo, hi, j)
+    U0 = torch.zeros_like(f)
+    slabs = 5
+    eta, eta_s, J = ctx.dwr_time_estimate(ctx1, 1.0, slabs, [f], [[1, 0, 0, 0]], U0, j, tol=1e-12)
+    pr = SlabProblem(Mesh(n), dict(C2, K=K), r, ubc, fbc)
+    pr1 = SlabProblem(Mesh(n), dict(C2, K=K), r + 1, ubc, fbc)
+    F = f.cpu().numpy()
+    jo = goal_vector_mean_p(pr.mesh, np.array(lo), np.array(hi))
+    eta_o, J_o = dwr_time_indicators(pr, pr1, 1.0, slabs, lambda t: F, jo)
+    assert abs(J - J_o) < 1e-10 * abs(J_o), (J, J_o)
+    assert np.abs(np.array(eta_s) - eta_o).max() < 1e-9 * abs(J_o), (eta_s, eta_o)
+    U1 = torch.zeros_like(f)
+    ctx1.march(1.0, slabs, [f], [[1, 0, 0, 0]], U0, U1, tol=1e-12)
+    diff = torch.dot(j, U1).item() - J
+    assert abs(eta - diff) < 1e-9 * abs(J), (eta, diff)
+    ctx.destroy()
+    ctx1.destroy()
