@@ -297,6 +297,42 @@ def run_dwr(args):
     return 0
 
 
+def run_fixed_stress(args):
+    """The layered 3-D march solved by fixed-stress iterative coupling (FP64 sweeps) and by the
+    monolithic FP64 FGMRES, each slab to relative residual 1e-10: DoF/s and sweeps or
+    iterations per slab (device time of one march each)."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_1801_04984_gb300 import binding as B
+    from paper_1801_04984_gb300.inputs import layered_logk, K0
+    n, r, slabs = args.n, args.r, args.slabs
+    g = layered_logk((n, n, n), layer_cells=4, std=1.5, seed=1801)
+    ubc, fbc = consolidation_bcs(3)
+    ctx = B.Context(3, (n, n, n), dict(COEF, K=K0 * np.exp(g)), r, ubc, fbc)
+    f = torch.zeros(ctx.n_space, dtype=torch.float64, device="cuda")
+    ctx.load_preset(B.LOAD_TRACTION_TOP, 1.0, f)
+    U0 = torch.zeros_like(f)
+    out = {"metric": "space-time DoF/s of the march: fixed-stress iterative coupling vs monolithic FGMRES (FP64)",
+           "unit": "DoF/s", "higher_is_better": True, "n_gpus": 1, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD.format(n=n, r=r, slabs=slabs), "tol": 1e-10}}
+    for name, mode in (("fixed_stress", B.FIXED_STRESS), ("monolithic_fgmres", B.FP64)):
+        U = torch.zeros_like(f)
+        ctx.march(1.0, slabs, [f], [[1, 0, 0, 0]], U0, U, tol=1e-10, mode=mode, max_iters=20000)  # warm-up
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        st = ctx.march(1.0, slabs, [f], [[1, 0, 0, 0]], U0, U, tol=1e-10, mode=mode, max_iters=20000)
+        e1.record()
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1e3
+        out[name] = {"value": ctx.n_slab * slabs / t, "ms_per_slab": 1e3 * t / slabs, "iters_per_slab": st["iters_per_slab"],
+                     "rel_residual": st["rel_residual"]}
+    out["value"] = out["fixed_stress"]["value"]
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -309,10 +345,10 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison march")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer run")
-    ap.add_argument("--config", default="march", choices=["march", "batch", "apply", "dwr"],
+    ap.add_argument("--config", default="march", choices=["march", "batch", "apply", "dwr", "fixed_stress"],
                     help="march: the 32^3 dG(1) headline; batch: 256 ragged 2-D instances; "
                          "apply: one slab-operator apply against the HBM roofline; "
-                         "dwr: goal-oriented time-error estimate")
+                         "dwr: goal-oriented time-error estimate; fixed_stress: iterative coupling vs monolithic")
     ap.add_argument("--instances", type=int, default=256)
     ap.add_argument("--workers", type=int, default=0, help="batch: max instances per batched context (0: library default)")
     ap.add_argument("--cheb-degree", type=int, default=0, help="elasticity smoother degree (0: library default)")
@@ -331,6 +367,8 @@ def main():
         return run_apply(args)
     if args.config == "dwr":
         return run_dwr(args)
+    if args.config == "fixed_stress":
+        return run_fixed_stress(args)
 
     import torch
     ws, rank, local = dist_env()

@@ -77,8 +77,12 @@ enum {
 enum { BIOT_U_NATURAL = 0, BIOT_U_DIRICHLET = 1, BIOT_U_ROLLER = 2 }; /* traction | all comps | normal comp */
 enum { BIOT_F_NATURAL = 0, BIOT_F_NOFLOW = 1 };                      /* pressure | q.n = 0 essential      */
 
-/* arithmetic of a call */
-enum { BIOT_FP64 = 0, BIOT_FP32 = 1, BIOT_MIXED = 2 };
+/* arithmetic of a call; BIOT_FIXED_STRESS selects (as a solve mode, FP64) the fixed-stress
+ * iterative coupling of paper §Iterative Coupling Approach instead of the monolithic FGMRES:
+ * sweeps of the flow solve with fixed volumetric mean stress followed by the deformation solve
+ * with fixed pressure (the block preconditioner's sub-solves), each relaxed by the
+ * residual-minimising factor; max_iters bounds the sweeps */
+enum { BIOT_FP64 = 0, BIOT_FP32 = 1, BIOT_MIXED = 2, BIOT_FIXED_STRESS = 3 };
 
 typedef struct biot_ctx* biot_t;
 
@@ -122,7 +126,7 @@ typedef struct {
 typedef struct {
   double tol;           /* relative true residual ||b - calA x|| / ||b|| (default 1e-10) */
   int max_iters;        /* total Krylov iterations (inner ones for MIXED), default 2000 */
-  int mode;             /* BIOT_FP64 or BIOT_MIXED */
+  int mode;             /* BIOT_FP64, BIOT_MIXED or BIOT_FIXED_STRESS */
   double inner_tol;     /* MIXED: relative tolerance of each FP32 inner solve (default 1e-5) */
   int transpose;        /* 1: solve calA^T x = rhs (adjoint) */
 } biot_solve_opts;

@@ -20,7 +20,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "biot.h")
 OK, EINVAL, ENOMEM, ECUDA, ENOCONV, EBREAKDOWN, ETIMEOUT = range(7)
 U_NATURAL, U_DIRICHLET, U_ROLLER = 0, 1, 2
 F_NATURAL, F_NOFLOW = 0, 1
-FP64, FP32, MIXED = 0, 1, 2
+FP64, FP32, MIXED, FIXED_STRESS = 0, 1, 2, 3
 LOAD_TRACTION_TOP, LOAD_MMS2D_CONST, LOAD_MMS2D_LINEAR = 0, 1, 2
 PART_FLUX_MASS_INV, PART_SCHUR, PART_VCYCLE, PART_ELASTICITY = 0, 1, 2, 3
 KERNEL_ELASTICITY_FP32, KERNEL_ELASTICITY_FP64, KERNEL_SCHUR_FP32 = 0, 1, 2

@@ -1434,6 +1434,63 @@ int solve_slab_batch(biot_ctx& c, double tau, const double* rhs, double* x, cons
   return rc;
 }
 
+// Fixed-stress iterative coupling (paper §Iterative Coupling Approach): each sweep solves the
+// flow problem with the volumetric mean stress held fixed (the beta Mp stabilisation of the
+// flux-pressure block) and then the deformation problem with the pressure held fixed.  Here a
+// sweep applies the block preconditioner's flow and displacement solves (for all temporal DoFs
+// of the slab, through the time transform) to the current residual, z = P r, and relaxes it by
+// the residual-minimising factor alpha = (r, calA z) / (calA z, calA z), so the residual norm
+// never grows; x <- x + alpha z, all in FP64, until ||b - calA x|| <= tol ||b||.
+int solve_fixed_stress(biot_ctx& c, double tau, const double* rhs, double* x, const biot_solve_opts& o, biot_stats& s,
+                       cudaStream_t st) {
+  const double t0 = now_s();
+  const int64_t n = c.g.N * c.nt;
+  if (c.nb > 1) fail(BIOT_EINVAL, "fixed-stress solves take a single instance");
+  if (o.transpose) fail(BIOT_EINVAL, "fixed-stress solves are forward solves");
+  ensure_prec<double>(c);
+  prec_prepare<double>(c, tau, st);
+  if (!c.r64) c.r64 = dalloc<double>(n);
+  if (!c.a64) c.a64 = dalloc<double>(n);
+  Krylov<double>& K = c.kry<double>();
+  if (!K.tmp) ensure_krylov<double>(c, 1);
+  double* r = c.r64;
+  double* z = c.a64;
+  double* w = K.tmp;
+  const double bn = std::sqrt(dev_dot(c, rhs, rhs, n, st));
+  if (!std::isfinite(bn)) fail(BIOT_EINVAL, "non-finite right-hand side");
+  int it = 0, rc = BIOT_OK;
+  apply_slab_T<double>(c, tau, x, r, 0, st);
+  launch_axpby<double>(r, rhs, 1.0, -1.0, n, st);  // r = b - calA x
+  CKL();
+  double rn = std::sqrt(dev_dot(c, r, r, n, st));
+  while (bn > 0 && rn > o.tol * bn) {
+    if (!std::isfinite(rn)) { rc = BIOT_EBREAKDOWN; break; }
+    if (it >= o.max_iters) { rc = BIOT_ENOCONV; break; }
+    precondition_T<double>(c, tau, r, z, 0, st);  // flow with fixed mean stress, then deformation
+    apply_slab_T<double>(c, tau, z, w, 0, st);
+    const double rw = dev_dot(c, r, w, n, st), ww = dev_dot(c, w, w, n, st);
+    const double alpha = ww > 0 ? rw / ww : 0.0;
+    if (!(alpha != 0.0) || !std::isfinite(alpha)) { rc = BIOT_EBREAKDOWN; break; }
+    launch_axpby<double>(x, z, alpha, 1.0, n, st);
+    launch_axpby<double>(r, w, -alpha, 1.0, n, st);
+    CKL();
+    rn = std::sqrt(dev_dot(c, r, r, n, st));
+    ++it;
+  }
+  if (bn == 0) CK(cudaMemsetAsync(x, 0, n * sizeof(double), st));
+  // the true residual of the result (the recursively updated one drifts by rounding only)
+  apply_slab_T<double>(c, tau, x, r, 0, st);
+  launch_axpby<double>(r, rhs, 1.0, -1.0, n, st);
+  CKL();
+  rn = std::sqrt(dev_dot(c, r, r, n, st));
+  s.iterations = it;
+  s.restarts = 0;
+  s.refinements = 0;
+  s.rel_residual = bn > 0 ? rn / bn : 0.0;
+  s.seconds = now_s() - t0;
+  return rc;
+}
+
 // ---- slab solve ---------------------------------------------------------------------
 int solve_slab_impl(biot_ctx& c, double tau, const double* rhs, double* x, const biot_solve_opts& o, biot_stats& s,
                     cudaStream_t st_user) {
@@ -1451,6 +1508,7 @@ int solve_slab_impl(biot_ctx& c, double tau, const double* rhs, double* x, const
     }
   } rejoin{c, st_user};
   if (c.nb > 1) return solve_slab_batch(c, tau, rhs, x, o, s, st);
+  if (o.mode == BIOT_FIXED_STRESS) return solve_fixed_stress(c, tau, rhs, x, o, s, st);
   const int64_t n = c.g.N * c.nt;
   int iters = 0, restarts = 0, refs = 0;
   double res = 0;
@@ -1852,7 +1910,8 @@ biot_solve_opts solve_defaults(const biot_solve_opts* o) {
     if (d.max_iters <= 0) d.max_iters = 2000;
     if (d.inner_tol <= 0) d.inner_tol = 1e-5;
   }
-  if (d.mode != BIOT_FP64 && d.mode != BIOT_MIXED) fail(BIOT_EINVAL, "solve mode must be BIOT_FP64 or BIOT_MIXED");
+  if (d.mode != BIOT_FP64 && d.mode != BIOT_MIXED && d.mode != BIOT_FIXED_STRESS)
+    fail(BIOT_EINVAL, "solve mode must be BIOT_FP64, BIOT_MIXED or BIOT_FIXED_STRESS");
   return d;
 }
 
