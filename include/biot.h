@@ -162,6 +162,17 @@ int biot_setup(const biot_mesh* mesh, const biot_coeffs* coeffs, int r, const bi
  * studies such as permeability sweeps.) */
 int biot_setup_batch(const biot_mesh* mesh, const biot_coeffs* coeffs, int r, const biot_opts* opts, int nb, biot_t* out);
 
+/* Host-side time tables of dG(r) (paper §Discretisation in Time, §Monolithic
+ * Approach), no GPU needed: the r+1 right-Radau nodes on [0,1], the diagonal of
+ * the slab mass M_t (Radau weights), phi_k(0), the jump-augmented derivative matrix
+ * D (row-major), and the real block form of M_t^{-1} D = V Lambda V^{-1} that the
+ * preconditioner uses: V, W = V^{-1} M_t^{-1}, the real part lam of the eigenvalue
+ * owning each transformed component, the first component `pair` of the complex
+ * pair (-1: none) and its imaginary part pair_beta (block [[a, b], [-b, a]]).
+ * Any output may be NULL.  Errors: EINVAL for r outside 0..2. */
+int biot_time_tables(int r, double* nodes, double* w, double* phi0, double* D, double* V, double* W, double* lam, int* pair,
+                     double* pair_beta);
+
 /* Sizes: DoFs per temporal level and per slab, number of cells (per instance). */
 int biot_sizes(biot_t ctx, int64_t* n_space, int64_t* n_slab, int64_t* n_cells);
 

@@ -86,6 +86,7 @@ def load(path: str = LIB_PATH):
         "biot_march_batch": (C.c_int, [vp, C.c_double, C.c_int, C.c_int, C.POINTER(vp), dp, C.POINTER(vp), C.POINTER(vp),
                                        C.POINTER(SolveOpts), ip, C.c_void_p, ip, vp]),
         "biot_sizes": (C.c_int, [vp, i64p, i64p, i64p]),
+        "biot_time_tables": (C.c_int, [C.c_int, dp, dp, dp, dp, dp, dp, dp, ip, dp]),
         "biot_set_permeability": (C.c_int, [vp, dp]),
         "biot_apply_slab": (C.c_int, [vp, C.c_double, vp, vp, C.c_int, C.c_int, vp]),
         "biot_precondition": (C.c_int, [vp, C.c_double, vp, vp, C.c_int, C.c_int, vp]),
@@ -418,6 +419,22 @@ def goal_of_logk(context, g, K0, T, slabs, f_terms, tcoef, U0, j_goal, tol=1e-10
     if _GOAL is None:
         _GOAL = _goal_function_class()
     return _GOAL.apply(g, context, K0, T, slabs, f_terms, tcoef, U0, j_goal, tol, mode)
+
+
+def time_tables(r):
+    """Host time tables of dG(r) (biot_time_tables): dict of numpy arrays."""
+    lib = load()
+    nt = r + 1
+    out = {k: np.zeros(nt) for k in ("nodes", "w", "phi0", "lam")}
+    out.update({k: np.zeros((nt, nt)) for k in ("D", "V", "W")})
+    pair, beta = C.c_int(), C.c_double()
+    dptr = lambda a: a.ctypes.data_as(C.POINTER(C.c_double))  # noqa: E731
+    rc = lib.biot_time_tables(int(r), dptr(out["nodes"]), dptr(out["w"]), dptr(out["phi0"]), dptr(out["D"]), dptr(out["V"]),
+                              dptr(out["W"]), dptr(out["lam"]), C.byref(pair), C.byref(beta))
+    if rc != OK:
+        raise BiotError(rc, "biot_time_tables")
+    out["pair"], out["pair_beta"] = pair.value, beta.value
+    return out
 
 
 def make_mesh(dim, n, u_bc, f_bc, lo=None, hi=None):

@@ -2036,6 +2036,27 @@ int setup_impl(const biot_mesh* mesh, const biot_coeffs* co, int r, const biot_o
 }
 }  // namespace
 
+extern "C" int biot_time_tables(int r, double* nodes, double* w, double* phi0, double* D, double* V, double* W, double* lam,
+                                int* pair, double* pair_beta) {
+  if (r < 0 || r > 2) return BIOT_EINVAL;
+  const TimeBasis tb = make_time_basis(r);
+  const int nt = r + 1;
+  for (int k = 0; k < nt; ++k) {
+    if (nodes) nodes[k] = tb.nodes[k];
+    if (w) w[k] = tb.w[k];
+    if (phi0) phi0[k] = tb.phi0[k];
+    if (lam) lam[k] = tb.lam[k];
+    for (int l = 0; l < nt; ++l) {
+      if (D) D[k * nt + l] = tb.D[k][l];
+      if (V) V[k * nt + l] = tb.V[k][l];
+      if (W) W[k * nt + l] = tb.W[k][l];
+    }
+  }
+  if (pair) *pair = tb.pair;
+  if (pair_beta) *pair_beta = tb.pair_beta;
+  return BIOT_OK;
+}
+
 extern "C" int biot_setup(const biot_mesh* mesh, const biot_coeffs* co, int r, const biot_opts* opts, biot_t* out) {
   return setup_impl(mesh, co, r, opts, 1, out);
 }

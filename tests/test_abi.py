@@ -31,3 +31,26 @@ def test_product_path_does_not_import_the_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
                 txt = open(os.path.join(root, f)).read()
                 assert not re.search(r"^\s*(from|import)\s+oracle", txt, re.M), f
+
+
+def test_library_time_tables_match_the_oracle():
+    """The CUDA path's host-side dG(r) tables (Radau nodes and weights, D, and the real block
+    form of the time operator used by the preconditioner) agree with the oracle's exact
+    change of basis from the Legendre matrices, and V Lambda V^{-1} reproduces M_t^{-1} D."""
+    import numpy as np
+    from oracle import timebasis as tb
+    for r in (0, 1, 2):
+        t = B.time_tables(r)
+        Mt, D = tb.radau_matrices(r)
+        assert np.allclose(t["nodes"], tb.radau_right_nodes(r), atol=1e-15)
+        assert np.allclose(t["w"], np.diag(Mt), atol=1e-14) and np.allclose(Mt, np.diag(np.diag(Mt)), atol=1e-13)
+        assert np.allclose(t["D"], D, atol=1e-12)
+        assert np.allclose(t["phi0"], tb.basis_values(np.array([0.0]), r, "radau")[:, 0], atol=1e-13)
+        Lam = np.diag(t["lam"])
+        p = t["pair"]
+        if p >= 0:
+            Lam[p, p + 1], Lam[p + 1, p] = t["pair_beta"], -t["pair_beta"]
+        T = np.linalg.solve(Mt, D)
+        assert np.allclose(t["V"] @ Lam @ np.linalg.inv(t["V"]), T, atol=1e-11), r
+        assert np.allclose(t["W"], np.linalg.inv(t["V"]) @ np.linalg.inv(Mt), atol=1e-10)
+        assert (p >= 0) == (r >= 1)  # dG(1) and dG(2) have one complex pair
