@@ -132,7 +132,7 @@ typedef struct {
 } biot_solve_opts;
 
 typedef struct {
-  int iterations;       /* Krylov iterations (all inner iterations for MIXED) */
+  int iterations;       /* Krylov iterations (all inner iterations for MIXED; sweeps for BIOT_FIXED_STRESS) */
   int refinements;      /* MIXED: outer refinement steps */
   int restarts;
   double rel_residual;  /* final true relative residual (FP64) */
