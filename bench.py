@@ -1,7 +1,8 @@
 """Benchmark: space-time DoF/s of the monolithic Biot slab march on one GB300.
 
-Workload (one "step"): 3-D Biot on the unit cube, 32^3 hexes, Q2 / RT1 / DGQ1,
-dG(1) in time, T = 1 in 16 slabs; layered log-normal permeability
+Workload (one "step", the precision configuration): 3-D Biot on the unit cube,
+64^3 hexes, Q2 / RT1 / DGQ1, dG(2) in time, T = 1 in 8 slabs (44.6 M unknowns per
+slab; `--n 32 --r 1 --slabs 16` gives the 32^3 dG(1) workload); layered log-normal permeability
 K = exp(g) 1e-2 (g ~ N(0, 1.5^2) per 4-cell z-layer, seed 1801); lambda = mu = 1,
 b = 0.8, 1/M = 0.05; unit compressive load on the drained top face, roller /
 no-flow elsewhere.  Every slab is solved to relative residual 1e-10 (FP64) by
@@ -343,14 +344,14 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n", type=int, default=32)
-    ap.add_argument("--r", type=int, default=1)
-    ap.add_argument("--slabs", type=int, default=16)
+    ap.add_argument("--n", type=int, default=64)
+    ap.add_argument("--r", type=int, default=2)
+    ap.add_argument("--slabs", type=int, default=8)
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison march")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer run")
     ap.add_argument("--config", default="march", choices=["march", "batch", "apply", "dwr", "fixed_stress"],
-                    help="march: the 32^3 dG(1) headline; batch: 256 ragged 2-D instances; "
+                    help="march: the layered 3-D march (default 64^3 dG(2), 8 slabs); batch: 256 ragged 2-D instances; "
                          "apply: one slab-operator apply against the HBM roofline; "
                          "dwr: goal-oriented time-error estimate; fixed_stress: iterative coupling vs monolithic")
     ap.add_argument("--instances", type=int, default=256)
@@ -442,7 +443,7 @@ def main():
     t_prof = e0.elapsed_time(e1) / 1e3
     el = ctx.kernel_stats(B.KERNEL_ELASTICITY_FP32)
     sch = ctx.kernel_stats(B.KERNEL_SCHUR_FP32)
-    ctx.kernel_stats(B.KERNEL_ELASTICITY_FP64)
+    el64 = ctx.kernel_stats(B.KERNEL_ELASTICITY_FP64)
     ctx.profile(False)
     dofs_step = ctx.n_slab * slabs
     value, t_step = whole_job_rate(dofs_step, float(np.mean(times)), ws, dev)
@@ -482,29 +483,41 @@ def main():
     # sum-factorised Kronecker apply: 180 FMA = 360 flop per Q2 node and right-hand side (z pass
     # 12 outputs x 4 taps, y pass 21 terms x 4, x pass 12 x 4; 5-tap vertex / 3-tap mid rows);
     # algorithmic bytes: the displacement block read once and written once, 3 x 2 x 4 B per node.
-    # The per-level working sets fit in L2, so the kernel is issue/shared-memory bound: it is
-    # reported against the FP32 CUDA-core peak (152 SMs x 128 lanes x 2 flop x SM clock).
+    # The kernel is bound by FP32 FMA issue, not HBM: it is reported against the FP32 FMA
+    # throughput that biot_fma_peak measures on this GPU in this run.  The FP64 elasticity
+    # launches of the same march (the true residuals of the refinement) are reported against
+    # the measured FP64 FMA throughput.
+    peak32, _ = B.fma_peak(B.FP32)
+    peak64, _ = B.fma_peak(B.FP64)
     el_n, el_ms, el_units = el
-    clk = (clocks or {}).get("sm_mhz") or 2070.0
-    fp32_peak = 152 * 128 * 2 * clk * 1e6 / 1e12
     achieved = 360.0 * el_units / (el_ms / 1e3) / 1e12 if el_ms > 0 else None
-    traffic = None
+    traffic, traffic_src = None, None
+    prof_path = os.path.join(ROOT, "profiles", "elasticity_fp32_%dcube.txt" % n)
     try:
-        prof_txt = open(os.path.join(ROOT, "profiles", "elasticity_fp32_32cube.txt")).read()
-        for line in prof_txt.splitlines():
+        for line in open(prof_path).read().splitlines():
             if line.startswith("dram_bytes_per_node_rhs:"):
                 traffic = float(line.split(":")[1]) * el_units / max(1, el_n)
-    except Exception:
+                traffic_src = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one fine-level launch (%s), per node "
+                               "x right-hand side, times the average units of one launch of this march"
+                               % os.path.relpath(prof_path, ROOT))
+    except OSError:
         traffic = None
     roofline = {"bound": "alu", "kernel": "k_apply_u3_col<float> (FP32 elasticity operator)",
-                "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": (achieved / fp32_peak) if achieved else None,
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x median sampled SM clock",
-                "traffic": traffic,
+                "achieved": achieved, "peak": peak32, "unit": "TFLOP/s",
+                "frac": (achieved / peak32) if achieved else None,
+                "peak_source": "measured in this run: biot_fma_peak(FP32), independent FMA chains on every SM",
+                "traffic": traffic, "traffic_source": traffic_src,
                 "launches_per_step": el_n, "avg_launch_us": 1e3 * el_ms / max(1, el_n),
                 "share_of_step": (el_ms / 1e3) / t_prof if t_prof > 0 else None,
                 "algorithmic_gbs": 24.0 * el_units / (el_ms / 1e3) / 1e9 if el_ms > 0 else None,
                 "hbm_peak_gbs": hbm_peak_measured(ROOT)}
+    e64_n, e64_ms, e64_units = el64
+    ach64 = 360.0 * e64_units / (e64_ms / 1e3) / 1e12 if e64_ms > 0 else None
+    fp64_roofline = {"bound": "alu", "kernel": "k_apply_u3_col<double> (FP64 elasticity operator: the true residuals)",
+                     "achieved": ach64, "peak": peak64, "unit": "TFLOP/s", "frac": (ach64 / peak64) if ach64 else None,
+                     "peak_source": "measured in this run: biot_fma_peak(FP64)",
+                     "launches_per_step": e64_n, "avg_launch_us": 1e3 * e64_ms / max(1, e64_n),
+                     "share_of_step": (e64_ms / 1e3) / t_prof if t_prof > 0 else None}
     schur = {"kernel": "k_schur_cheb_st<float> (one Chebyshev step, flux-pressure Schur)", "launches_per_step": sch[0],
              "avg_launch_us": 1e3 * sch[1] / max(1, sch[0]), "share_of_step": (sch[1] / 1e3) / t_prof if t_prof > 0 else None}
     s_mean = stats[-1]
@@ -526,6 +539,7 @@ def main():
         "e2e": e2e,
         "gpu_launches": int((launches1 - launches0) / max(1, args.steps)),
         "roofline": roofline,
+        "fp64_roofline": fp64_roofline,
         "second_kernel": schur,
         "clocks": clocks,
         "cpu_baseline": cpu,

@@ -333,7 +333,9 @@ int biot_apply_part(biot_t ctx, int part, double tau, const void* in, void* out,
  * driver also materialises the array at that moment); make that first call before
  * any stream capture.  All calls share the array: calls that overlap on the GPU (other
  * streams or devices' threads racing on one device) race on it.  The context must
- * have been created by biot_setup; this call itself allocates nothing. */
+ * have been created by biot_setup (EINVAL for batched contexts of biot_setup_batch) with
+ * the default lumped Darcy mass (EINVAL when opts->flux_mass_exact = 1); this call itself
+ * allocates nothing. */
 int biot_schur_apply_noalloc(biot_t ctx, double tau, const double* in, double* out, void* stream);
 
 /* Tracing.  biot_profile(ctx, 1) makes every launch of the displacement-row
@@ -358,6 +360,15 @@ int biot_counters(biot_t ctx, int64_t* launches, int64_t* op_launches, double* o
  * them.  With profiling on, CUDA graphs are not used. */
 enum { BIOT_KERNEL_ELASTICITY_FP32 = 0, BIOT_KERNEL_ELASTICITY_FP64 = 1, BIOT_KERNEL_SCHUR_FP32 = 2 };
 int biot_kernel_stats(biot_t ctx, int kind, int64_t* launches, double* ms, double* units);
+
+/* Measured arithmetic peak of the CUDA cores on the current device: a kernel of
+ * independent fused multiply-add chains (prec = BIOT_FP32 or BIOT_FP64) over every SM,
+ * calibrated to run about 60 ms and timed with CUDA events on `stream`.  tflops
+ * (HOST, may be NULL) receives the achieved TFLOP/s (2 flop per FMA), ms the duration of
+ * the timed launch.  The paper has no counterpart: this is the denominator against which
+ * the operator kernels' FP32 and FP64 arithmetic rates are reported.  No context needed;
+ * allocates nothing.  Errors: EINVAL for another prec, ECUDA. */
+int biot_fma_peak(int prec, double* tflops, double* ms, void* stream);
 
 const char* biot_last_error(biot_t ctx);
 void biot_destroy(biot_t ctx);

@@ -186,11 +186,35 @@ def goal_vector_mean_p(mesh: Mesh, box_lo, box_hi) -> np.ndarray:
     return j
 
 
-def apply_rows(prob: SlabProblem, tau: float, X: np.ndarray, rows, basis: str = "radau") -> np.ndarray:
+class CellwiseSlab:
+    """What `apply_rows` needs of a slab problem, without any global assembly: the
+    local-to-global maps, the reference element matrices, the per-cell Darcy factor
+    eta/K_c, the constraint mask of one time level and the time matrices.  Used at
+    sizes where the assembled slab matrix of `SlabProblem` does not fit in memory
+    (paper §Monolithic Approach: the same slab operator, evaluated row by row)."""
+
+    def __init__(self, mesh: Mesh, coeffs: dict, r: int, u_bc, f_bc):
+        from types import SimpleNamespace
+        self.mesh = mesh
+        self.coeffs = coeffs
+        self.r = int(r)
+        cells, Lu, Lq, Lp = mesh.l2g()
+        A, E, Mq, B, Mp = mesh.element_matrices(coeffs["lam"], coeffs["mu"])
+        kscale = coeffs["eta"] / np.asarray(coeffs["K"], dtype=np.float64)
+        self.blocks = SimpleNamespace(Lu=Lu, Lq=Lq, Lp=Lp, Ae=A, Ee=E, Mqe=Mq, Be=B, Mpe=Mp, kscale=kscale)
+        self.mask1 = constraint_mask(mesh, u_bc, f_bc)
+        self.N = mesh.N
+        self.Nslab = mesh.N * (self.r + 1)
+
+    def time_mats(self, basis):
+        return tb.legendre_matrices(self.r) if basis == "legendre" else tb.radau_matrices(self.r)
+
+
+def apply_rows(prob, tau: float, X: np.ndarray, rows, basis: str = "radau") -> np.ndarray:
     """Selected entries of calA_c X computed cell by cell from the element matrices
     (no global assembly), for parity checks at sizes where the sparse slab matrix
     does not fit: y_(k,i) = sum_l D_kl (S X_l)_i + tau (M_t)_kl (A_s X_l)_i on free
-    rows, y = X on constrained rows."""
+    rows, y = X on constrained rows.  `prob` is a SlabProblem or a CellwiseSlab."""
     from .space import dofs_of_cell_rows
     m = prob.mesh
     blk = prob.blocks
@@ -198,7 +222,7 @@ def apply_rows(prob: SlabProblem, tau: float, X: np.ndarray, rows, basis: str = 
     Mt, D = prob.time_mats(basis)
     N = m.N
     nu, nq, npl = blk.Lu.shape[1], blk.Lq.shape[1], blk.Lp.shape[1]
-    Xm = (prob.mask * X).reshape(prob.r + 1, N)
+    Xm = X.reshape(prob.r + 1, N) * prob.mask1[None, :]
     out = np.zeros(len(rows))
     for ri, row in enumerate(rows):
         k, i = divmod(int(row), N)

@@ -106,6 +106,7 @@ def load(path: str = LIB_PATH):
         "biot_profile": (C.c_int, [vp, C.c_int]),
         "biot_kernel_stats": (C.c_int, [vp, C.c_int, i64p, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
         "biot_counters": (C.c_int, [vp, i64p, i64p, C.POINTER(C.c_double)]),
+        "biot_fma_peak": (C.c_int, [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), vp]),
         "biot_last_error": (C.c_char_p, [vp]),
         "biot_destroy": (None, [vp]),
     }
@@ -419,6 +420,17 @@ def goal_of_logk(context, g, K0, T, slabs, f_terms, tcoef, U0, j_goal, tol=1e-10
     if _GOAL is None:
         _GOAL = _goal_function_class()
     return _GOAL.apply(g, context, K0, T, slabs, f_terms, tcoef, U0, j_goal, tol, mode)
+
+
+def fma_peak(prec=FP32):
+    """Measured CUDA-core FMA throughput of the current device (biot_fma_peak):
+    (TFLOP/s, ms of the timed launch)."""
+    lib = load()
+    tf, ms = C.c_double(), C.c_double()
+    rc = lib.biot_fma_peak(int(prec), C.byref(tf), C.byref(ms), _stream())
+    if rc != OK:
+        raise BiotError(rc, "biot_fma_peak failed")
+    return tf.value, ms.value
 
 
 def time_tables(r):

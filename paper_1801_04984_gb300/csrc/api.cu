@@ -2567,6 +2567,8 @@ struct CtxView {
   const TabT<double>* t64;
   const double* dmq64;
   double invM, beta;
+  int nb;           // batched instances (1: a context of biot_setup)
+  int lumped_flux;  // 1: the Schur complement uses the diagonal of the Darcy mass
 };
 bool ctx_view(biot_t c, CtxView* v) {
   if (!c || !v) return false;
@@ -2575,6 +2577,8 @@ bool ctx_view(biot_t c, CtxView* v) {
   v->dmq64 = c->dmq64;
   v->invM = c->invM;
   v->beta = c->beta;
+  v->nb = c->nb;
+  v->lumped_flux = c->lumped_flux;
   return true;
 }
 void ctx_set_error(biot_t c, const char* msg) {

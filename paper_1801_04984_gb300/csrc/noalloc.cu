@@ -34,6 +34,8 @@ struct CtxView {
   const TabT<double>* t64;
   const double* dmq64;
   double invM, beta;
+  int nb;
+  int lumped_flux;
 };
 bool ctx_view(biot_t ctx, CtxView* v);
 void ctx_set_error(biot_t ctx, const char* msg);
@@ -43,6 +45,15 @@ extern "C" int biot_schur_apply_noalloc(biot_t ctx, double tau, const double* in
   using namespace biot;
   CtxView v;
   if (!ctx_view(ctx, &v)) return BIOT_EINVAL;
+  if (v.nb != 1) {
+    ctx_set_error(ctx, "schur_apply_noalloc: batched contexts (biot_setup_batch) are not supported; use a context of biot_setup");
+    return BIOT_EINVAL;
+  }
+  if (!v.lumped_flux) {
+    ctx_set_error(ctx, "schur_apply_noalloc: the context inverts the Darcy mass exactly (flux_mass_exact = 1); this entry "
+                       "point applies only the lumped-Darcy-mass Schur complement");
+    return BIOT_EINVAL;
+  }
   if (!in || !out || !(tau > 0)) {
     ctx_set_error(ctx, "schur_apply_noalloc: NULL vector or tau <= 0");
     return BIOT_EINVAL;

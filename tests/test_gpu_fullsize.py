@@ -1,0 +1,222 @@
+"""Parity at the benchmarked sizes: the 3-D layered consolidation problem at 32^3 dG(1)
+(16 slabs) and 64^3 dG(2) (8 slabs, 44.6 M unknowns per slab).
+
+* Slab operator (paper §Monolithic Approach): the GPU apply (FP64 and FP32) of a seeded
+  random slab vector against the oracle's row-by-row evaluation from the element
+  matrices (`oracle.slab.apply_rows` on a `CellwiseSlab`, no global assembly), on
+  more than 2,000 sampled rows per case: every block (u_c, q_c, p), every temporal
+  level, every face of every block grid, the seams of the operator's 8-node tiles and
+  the interior.
+* March (paper §Discretisation in Time): with the permeability constant in horizontal
+  layers, roller / no-flow side and bottom faces and a uniform top load, the discrete
+  solution depends on z only (the oracle pins this: a layered 3-D march equals the
+  2-D one).  The GPU march of the full 3-D problem, FP64 and mixed FP32/FP64, is
+  compared on every column of the grid and at the end of every slab with the oracle's
+  direct-solve march of one (1, 1, n) column with the same layers.
+"""
+import numpy as np
+import pytest
+
+from gpu_common import C2, consolidation_bcs
+from oracle.slab import CellwiseSlab, SlabProblem, apply_rows
+from oracle.space import Mesh, load_vector
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+CASES = [(32, 1, 16), (64, 2, 8)]
+
+
+def _coeffs(n):
+    from paper_1801_04984_gb300.inputs import K0, layered_logk
+    g = layered_logk((n, n, n), layer_cells=4, std=1.5, seed=1801)
+    return dict(C2, K=K0 * np.exp(g)), g
+
+
+_CTX = {}
+
+
+@pytest.fixture(scope="module")
+def contexts():
+    yield _CTX
+    for c in _CTX.values():
+        c.destroy()
+    _CTX.clear()
+    torch.cuda.empty_cache()
+
+
+def _context(cache, n, r):
+    from paper_1801_04984_gb300 import binding as B
+    if (n, r) not in cache:
+        for key in list(cache):  # one full-size context on the device at a time
+            cache.pop(key).destroy()
+        torch.cuda.empty_cache()
+        co, _ = _coeffs(n)
+        ubc, fbc = consolidation_bcs(3)
+        cache[(n, r)] = B.Context(3, (n, n, n), co, r, ubc, fbc)
+    return cache[(n, r)]
+
+
+def _grids(m: Mesh):
+    """(offset, shape x-fastest) of every block grid of one temporal level."""
+    out = [(m.off_u[c], m.u_shape) for c in range(m.dim)]
+    out += [(m.off_q[c], m.q_shapes[c]) for c in range(m.dim)]
+    out.append((m.off_p, m.p_shape))
+    return out
+
+
+def sample_rows(m: Mesh, r: int, seed: int, per_face=12, interior=80, seams=20):
+    """Row indices of the slab vector: for every temporal level and block grid, points on
+    each face of the grid, points whose coordinates sit on the seams of 8-node tiles, and
+    uniform interior points."""
+    rng = np.random.default_rng(seed)
+    rows = []
+    for k in range(r + 1):
+        for off, shp in _grids(m):
+            shp = np.array(shp)
+            pts = []
+            for axis in range(m.dim):
+                for side in (0, 1):
+                    p = rng.integers(0, shp, size=(per_face, m.dim))
+                    p[:, axis] = 0 if side == 0 else shp[axis] - 1
+                    pts.append(p)
+            seam_vals = np.array([7, 8, 15, 16, 23, 24])
+            p = np.stack([rng.choice(seam_vals[seam_vals < s], size=seams) for s in shp], axis=1)
+            pts.append(p)
+            pts.append(rng.integers(0, shp, size=(interior, m.dim)))
+            P = np.concatenate(pts)
+            lin = P[:, 0] + shp[0] * (P[:, 1] + shp[1] * P[:, 2])
+            rows.append(k * m.N + off + lin)
+    return np.unique(np.concatenate(rows))
+
+
+def _block_of(m: Mesh, rows):
+    """Block label per row (0..d-1 u_c, d..2d-1 q_c, 2d p) of one temporal level."""
+    i = rows % m.N
+    lab = np.zeros(len(rows), dtype=np.int64)
+    bounds = [m.off_u[c] for c in range(m.dim)] + [m.off_q[c] for c in range(m.dim)] + [m.off_p]
+    for b, start in enumerate(bounds):
+        lab[i >= start] = b
+    return lab
+
+
+def _check_blocks(m, rows, y, yo, tol):
+    lab = _block_of(m, rows)
+    for b in np.unique(lab):
+        s = lab == b
+        scale = np.abs(yo[s]).max()
+        assert scale > 0
+        err = np.abs(y[s] - yo[s]).max() / scale
+        assert err < tol, ("block", int(b), err)
+    rel = np.linalg.norm(y - yo) / np.linalg.norm(yo)
+    assert rel < tol, rel
+    return rel
+
+
+@pytest.mark.parametrize("n,r,slabs", CASES)
+def test_fullsize_apply_fp64_sampled_rows_match_oracle(contexts, n, r, slabs):
+    from paper_1801_04984_gb300.inputs import random_vector
+    ctx = _context(contexts, n, r)
+    co, _ = _coeffs(n)
+    ubc, fbc = consolidation_bcs(3)
+    m = Mesh((n, n, n))
+    light = CellwiseSlab(m, co, r, ubc, fbc)
+    tau = 1.0 / slabs
+    x = random_vector(ctx.n_slab, seed=1000 + n + r)
+    rows = sample_rows(m, r, seed=n * 10 + r)
+    assert len(rows) >= 2000
+    xd = torch.tensor(x, device="cuda")
+    yd = torch.full_like(xd, float("nan"))
+    ctx.apply_slab(tau, xd, yd)
+    y = yd[torch.tensor(rows, device="cuda")].cpu().numpy()
+    del xd, yd
+    yo = apply_rows(light, tau, x, rows)
+    _check_blocks(m, rows, y, yo, 1e-12)
+
+
+@pytest.mark.parametrize("n,r,slabs", CASES)
+def test_fullsize_apply_fp32_sampled_rows_match_oracle_to_rounding(contexts, n, r, slabs):
+    from paper_1801_04984_gb300.inputs import random_vector
+    ctx = _context(contexts, n, r)
+    co, _ = _coeffs(n)
+    ubc, fbc = consolidation_bcs(3)
+    m = Mesh((n, n, n))
+    light = CellwiseSlab(m, co, r, ubc, fbc)
+    tau = 1.0 / slabs
+    x32 = random_vector(ctx.n_slab, seed=2000 + n + r).astype(np.float32)
+    rows = sample_rows(m, r, seed=n * 10 + r + 1)
+    xd = torch.tensor(x32, device="cuda")
+    yd = torch.full_like(xd, float("nan"))
+    ctx.apply_slab(tau, xd, yd)
+    y = yd[torch.tensor(rows, device="cuda")].double().cpu().numpy()
+    del xd, yd
+    # the oracle applied to the same (rounded) input: only the kernel's FP32 arithmetic differs
+    yo = apply_rows(light, tau, x32.astype(np.float64), rows)
+    _check_blocks(m, rows, y, yo, 2e-5)
+
+
+def _column_march(n, r, slabs, g):
+    """Oracle march of one (1, 1, n) column with the layers of g (K per z-cell)."""
+    from paper_1801_04984_gb300.inputs import K0
+    gz = g.reshape(n, n, n)[:, 0, 0]
+    co = dict(C2, K=K0 * np.exp(gz))
+    ubc, fbc = consolidation_bcs(3)
+    m = Mesh((1, 1, n))
+    prob = SlabProblem(m, co, r, ubc, fbc)
+
+    def trac(X, t, f):
+        o = np.zeros((len(X), 3))
+        o[:, 2] = -1.0
+        return o
+    F = load_vector(m, 0.0, traction=trac, u_bc=ubc, f_bc=fbc)
+    Xs, _ = prob.march(1.0, slabs, lambda t: F)
+    return m, [prob.end_value(X) for X in Xs]
+
+
+def _fields(m: Mesh, U):
+    """u_c, q_c and p of one temporal level as arrays indexed [z, y, x]."""
+    out = {}
+    for c in range(3):
+        out["u%d" % c] = U[m.off_u[c]:m.off_u[c] + m.nu_nodes].reshape(m.u_shape[::-1])
+        out["q%d" % c] = U[m.off_q[c]:m.off_q[c] + m.Nq_c[c]].reshape(m.q_shapes[c][::-1])
+    out["p"] = U[m.off_p:].reshape(m.p_shape[::-1])
+    return out
+
+
+@pytest.mark.parametrize("mode", ["fp64", "mixed"])
+@pytest.mark.parametrize("n,r,slabs", CASES)
+def test_fullsize_layered_march_matches_column_oracle(contexts, n, r, slabs, mode):
+    from paper_1801_04984_gb300 import binding as B
+    ctx = _context(contexts, n, r)
+    _, g = _coeffs(n)
+    mc, ends = _column_march(n, r, slabs, g)
+    f = torch.zeros(ctx.n_space, dtype=torch.float64, device="cuda")
+    ctx.load_preset(B.LOAD_TRACTION_TOP, 1.0, f)
+    U0 = torch.zeros_like(f)
+    U = torch.zeros_like(f)
+    X_all = torch.empty(slabs * ctx.n_slab, dtype=torch.float64, device="cuda")
+    ctx.march(1.0, slabs, [f], [[1.0, 0, 0, 0]], U0, U, X_all=X_all, tol=1e-10,
+              mode=B.MIXED if mode == "mixed" else B.FP64)
+    m = Mesh((n, n, n))
+    worst = 0.0
+    for s in range(slabs):
+        last = X_all[s * ctx.n_slab + r * ctx.n_space:s * ctx.n_slab + (r + 1) * ctx.n_space]
+        G = _fields(m, last.cpu().numpy())
+        O = _fields(mc, ends[s])
+        # the column's z profiles, broadcast over every (x, y) column of the 3-D grid
+        for name in ("u2", "q2", "p"):
+            col = O[name][:, 0, 0]
+            # the direct-solve column itself is constant across its 3 x 3 nodes up to rounding
+            assert np.abs(O[name] - col[:, None, None]).max() <= 1e-10 * np.abs(col).max()
+            ref = np.broadcast_to(col[:, None, None], G[name].shape)
+            scale = np.abs(ref).max()
+            err = np.abs(G[name] - ref).max() / scale
+            rel = np.linalg.norm(G[name] - ref) / np.linalg.norm(ref)
+            worst = max(worst, err, rel)
+            assert err < 1e-8 and rel < 1e-8, (s, name, err, rel)
+        # horizontal displacement and flux vanish
+        for name, ref in (("u0", "u2"), ("u1", "u2"), ("q0", "q2"), ("q1", "q2")):
+            assert np.abs(G[name]).max() < 1e-8 * np.abs(O[ref]).max(), (s, name)
+    assert np.allclose(U.cpu().numpy(), X_all[(slabs - 1) * ctx.n_slab + r * ctx.n_space:slabs * ctx.n_slab].cpu().numpy(),
+                       rtol=0, atol=0)
+    print("n=%d r=%d %s: worst relative difference to the column oracle %.2e" % (n, r, mode, worst))

@@ -115,3 +115,16 @@ def test_lumped_schur(n, bcs):
     beta = C2["b"] ** 2 / C2["K_dr"]
     ref = (C2["invM"] + beta) * (blk.Mp @ p) + tau * (Bf @ ((Bf.T @ p) / Mq.diagonal()))
     assert np.abs(yd.cpu().numpy()[m.off_p:] - ref).max() < 1e-11 * np.abs(ref).max()
+
+
+def test_fma_peak_is_measured_and_plausible():
+    """biot_fma_peak: the FP32 and FP64 CUDA-core FMA throughput of this GPU (the ALU
+    roofline denominators).  FP32 lies within the nominal 152 SMs x 128 lanes x 2 flop x
+    clock (80.5 TFLOP/s at 2070 MHz) and is well above FP64 on this part."""
+    from paper_1801_04984_gb300 import binding as B
+    f32, ms32 = B.fma_peak(B.FP32)
+    f64, ms64 = B.fma_peak(B.FP64)
+    assert 20.0 < f32 < 85.0, f32
+    assert 0.05 < f64 < f32, f64
+    assert ms32 > 10.0 and ms64 > 10.0
+    print("FMA peak: FP32 %.1f TFLOP/s, FP64 %.2f TFLOP/s" % (f32, f64))

@@ -239,7 +239,7 @@ def test_adjoint_gradient_matches_finite_differences():
 
 @pytest.mark.parametrize("n,r", [((3, 2), 1), ((2, 3, 2), 2)])
 def test_rowwise_apply_matches_assembled_operator(n, r):
-    from oracle.slab import apply_rows
+    from oracle.slab import CellwiseSlab, apply_rows
     m = Mesh(n)
     ubc, fbc = consolidation_bcs(m.dim)
     prob = SlabProblem(m, dict(C2, K=np.linspace(0.01, 0.1, m.ncells)), r, ubc, fbc)
@@ -247,6 +247,9 @@ def test_rowwise_apply_matches_assembled_operator(n, r):
     y = prob.operator(0.3, "radau") @ X
     rows = np.arange(prob.Nslab)
     assert np.abs(apply_rows(prob, 0.3, X, rows) - y).max() < 1e-13 * np.abs(y).max()
+    # the assembly-free form used for full-size parity gives the same rows
+    light = CellwiseSlab(m, dict(C2, K=np.linspace(0.01, 0.1, m.ncells)), r, ubc, fbc)
+    assert np.abs(apply_rows(light, 0.3, X, rows) - y).max() < 1e-13 * np.abs(y).max()
 
 
 @pytest.mark.parametrize("r", [0, 1])
