@@ -189,10 +189,13 @@ int biot_apply_slab(biot_t ctx, double tau, const void* x, void* y, int prec, in
  * z = P r.  prec as in biot_apply_slab. */
 int biot_precondition(biot_t ctx, double tau, const void* r, void* z, int prec, int transpose, void* stream);
 
-/* Solve calA x = rhs (or calA^T x = rhs) for one slab.  rhs, x: double*,
- * n_slab; x holds the initial guess on entry and the solution on exit.
- * opts/stats may be NULL.  Returns ENOCONV (x = best iterate) if max_iters
- * is reached first, EBREAKDOWN on non-finite values. */
+/* Solve calA x = rhs (or calA^T x = rhs) for one slab (paper §Monolithic Approach: the
+ * coupled system of all r+1 temporal DoFs solved at once; §Preconditioning technology:
+ * GMRES, right-preconditioned by the time-spectral block-triangular fixed-stress
+ * preconditioner).  rhs, x: double*, n_slab; x holds the initial guess on entry and the
+ * solution on exit.  opts/stats may be NULL.  Returns EINVAL for a non-finite right-hand
+ * side, ENOCONV (x = best iterate, finite) if max_iters is reached first, EBREAKDOWN on
+ * non-finite values inside the iteration. */
 int biot_solve_slab(biot_t ctx, double tau, const double* rhs, double* x, const biot_solve_opts* opts, biot_stats* stats,
                     void* stream);
 
@@ -211,6 +214,18 @@ int biot_solve_slab(biot_t ctx, double tau, const double* rhs, double* x, const 
 int biot_march(biot_t ctx, double T, int slabs, int nterms, const double* const* f_terms, const double* tcoef,
                const double* U0, double* U_end, double* X_all, const biot_solve_opts* opts, int* iters_per_slab,
                biot_stats* stats, void* stream);
+
+/* Resumable march: slabs first .. first + count - 1 of the partition of (0, T] into `slabs`
+ * slabs of length tau = T / slabs (paper §Discretisation in Time: the state carried from
+ * one slab to the next is U(t_n^-) alone, so a march can stop after any slab and restart
+ * from that state).  U_first (n_space, HOST or DEVICE) is U(t_first^-), U_end receives
+ * U(t_{first+count}^-); loads, X_all (count * n_slab) and iters_per_slab (count) as in
+ * biot_march, whose result equals, bitwise, a sequence of biot_march_resume calls that
+ * covers the same slabs on the same context.  Errors: EINVAL unless
+ * 0 <= first < first + count <= slabs, and for batched contexts. */
+int biot_march_resume(biot_t ctx, double T, int slabs, int first, int count, int nterms, const double* const* f_terms,
+                      const double* tcoef, const double* U_first, double* U_end, double* X_all, const biot_solve_opts* opts,
+                      int* iters_per_slab, biot_stats* stats, void* stream);
 
 /* Marches every instance of a batched context (biot_setup_batch) over the same
  * `slabs` slabs of (0, T] (paper §Discretisation in Time), all instances in
@@ -314,8 +329,13 @@ int biot_load_preset(biot_t ctx, int kind, double value, double* f, void* stream
  *                            flux-pressure Schur complement of the dG(0)-type block
  *                            with lambda = 1 and the fixed-stress term beta Mp;
  *   BIOT_PART_VCYCLE:       out_u = one multigrid V-cycle for tau A x = in_u from x = 0;
- *   BIOT_PART_ELASTICITY:   out_u = tau A in_u (constrained rows identity). */
-enum { BIOT_PART_FLUX_MASS_INV = 0, BIOT_PART_SCHUR = 1, BIOT_PART_VCYCLE = 2, BIOT_PART_ELASTICITY = 3 };
+ *   BIOT_PART_ELASTICITY:   out_u = tau A in_u (constrained rows identity);
+ *   BIOT_PART_SCHUR_STEP:   out_p = in_p - diag(Shat)^{-1} Shat in_p with Shat the lumped-Darcy-mass
+ *                            BIOT_PART_SCHUR operator: one step of the flux-pressure Chebyshev-Jacobi
+ *                            kernel the solver runs (weights 0 and 1, zero right-hand side); EINVAL for
+ *                            batched contexts and flux_mass_exact = 1. */
+enum { BIOT_PART_FLUX_MASS_INV = 0, BIOT_PART_SCHUR = 1, BIOT_PART_VCYCLE = 2, BIOT_PART_ELASTICITY = 3,
+       BIOT_PART_SCHUR_STEP = 4 };
 int biot_apply_part(biot_t ctx, int part, double tau, const void* in, void* out, int prec, void* stream);
 
 /* Allocation-free flux-pressure Schur apply, for callers that cannot call

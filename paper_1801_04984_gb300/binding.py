@@ -22,7 +22,7 @@ U_NATURAL, U_DIRICHLET, U_ROLLER = 0, 1, 2
 F_NATURAL, F_NOFLOW = 0, 1
 FP64, FP32, MIXED, FIXED_STRESS = 0, 1, 2, 3
 LOAD_TRACTION_TOP, LOAD_MMS2D_CONST, LOAD_MMS2D_LINEAR = 0, 1, 2
-PART_FLUX_MASS_INV, PART_SCHUR, PART_VCYCLE, PART_ELASTICITY = 0, 1, 2, 3
+PART_FLUX_MASS_INV, PART_SCHUR, PART_VCYCLE, PART_ELASTICITY, PART_SCHUR_STEP = 0, 1, 2, 3, 4
 KERNEL_ELASTICITY_FP32, KERNEL_ELASTICITY_FP64, KERNEL_SCHUR_FP32 = 0, 1, 2
 ERR_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOCONV", 5: "EBREAKDOWN", 6: "ETIMEOUT"}
 
@@ -93,6 +93,8 @@ def load(path: str = LIB_PATH):
         "biot_solve_slab": (C.c_int, [vp, C.c_double, vp, vp, C.POINTER(SolveOpts), C.POINTER(Stats), vp]),
         "biot_march": (C.c_int, [vp, C.c_double, C.c_int, C.c_int, C.POINTER(vp), dp, vp, vp, vp,
                                  C.POINTER(SolveOpts), ip, C.POINTER(Stats), vp]),
+        "biot_march_resume": (C.c_int, [vp, C.c_double, C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(vp), dp, vp, vp, vp,
+                                        C.POINTER(SolveOpts), ip, C.POINTER(Stats), vp]),
         "biot_adjoint_grad": (C.c_int, [vp, C.c_double, C.c_int, C.c_int, C.POINTER(vp), dp, vp, vp,
                                         C.POINTER(SolveOpts), C.c_int, dp, vp, vp]),
         "biot_goal_mean_pressure": (C.c_int, [vp, dp, dp, vp, vp]),
@@ -270,6 +272,29 @@ class Context:
         rc = self.lib.biot_march(self.h, float(T), int(slabs), nterms, arr, tc.ctypes.data_as(C.POINTER(C.c_double)),
                                  anyptr(U0, "U0"), anyptr(U_end, "U_end"),
                                  _ptr(X_all, None, None, "X_all"), C.byref(o), its, C.byref(st), _stream())
+        self._check(rc, allow=(ENOCONV,) if allow_noconv else ())
+        d = st.as_dict()
+        d["iters_per_slab"] = list(its)
+        return d
+
+    def march_resume(self, T, slabs, first, count, f_terms, tcoef, U_first, U_end, X_all=None, tol=1e-10, max_iters=2000,
+                     mode=FP64, inner_tol=1e-5, allow_noconv=False):
+        """Slabs first .. first+count-1 of the partition of (0, T] into `slabs` slabs, from
+        U_first = U(t_first^-) (biot_march_resume)."""
+        nterms, arr, tc, keep = self._loads(f_terms, tcoef)
+        o = _solve_opts(tol, max_iters, mode, inner_tol, 0)
+        st = Stats()
+        its = (C.c_int * count)()
+
+        def anyptr(t, name):
+            if isinstance(t, np.ndarray):
+                assert t.dtype == np.float64 and t.flags.c_contiguous and t.size == self.n_space, name
+                return C.c_void_p(t.ctypes.data)
+            return _ptr(t, None, self.n_space, name)
+        rc = self.lib.biot_march_resume(self.h, float(T), int(slabs), int(first), int(count), nterms, arr,
+                                        tc.ctypes.data_as(C.POINTER(C.c_double)), anyptr(U_first, "U_first"),
+                                        anyptr(U_end, "U_end"), _ptr(X_all, None, None, "X_all"), C.byref(o), its,
+                                        C.byref(st), _stream())
         self._check(rc, allow=(ENOCONV,) if allow_noconv else ())
         d = st.as_dict()
         d["iters_per_slab"] = list(its)

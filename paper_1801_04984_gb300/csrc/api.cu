@@ -18,10 +18,23 @@
 #include <map>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/biot.h"
 #include "internal.h"
 
 using namespace biot;
+
+namespace {
+// NVTX range of one phase (march, slab, slab solve, inner FP32 solve) for timeline tools;
+// without an attached tool the calls return at once
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+}  // namespace
 
 // ---------------------------------------------------------------------------
 // helpers
@@ -277,7 +290,8 @@ struct PrecWork {
   T *tA = nullptr, *tB = nullptr;  // slab
   T *fq = nullptr, *tq = nullptr, *fq2 = nullptr;  // nt * Nq
   T *gp = nullptr, *pp = nullptr, *pd = nullptr, *pAx = nullptr, *pxo = nullptr, *pdinv = nullptr;  // nt * Np
-  T* scoef = nullptr;  // 16 * Np: lumped Schur stencil for schur_tau
+  T* scoef = nullptr;  // 16 * Np per instance: lumped Schur stencil for schur_tau (multigrid path only)
+  T* wq = nullptr;     // nqt per instance: flux weights tau wt^2 / Mq_ff of the matrix-free Schur step
   double schur_tau = -1.0;
   // cell-centred multigrid of the Schur complement: level l >= 1 stencils (per instance) and
   // level vectors (per column); pmr0 holds the level-0 residual
@@ -480,6 +494,7 @@ void ensure_prec(biot_ctx& c) {
   w.pxo = dalloc<T>(nt * g.Np);
   w.pdinv = dalloc<T>(nt * g.Np);
   w.scoef = dalloc<T>(16 * g.Np * c.nb);
+  w.wq = dalloc<T>(nqt * c.nb);
   for (Level& L : c.lv) {
     LevelWork<T>& lw = lwork<T>(L);
     int64_t n = (int64_t)nt * L.g.Nu;
@@ -515,10 +530,8 @@ void ensure_krylov(biot_ctx& c, int m) {
 }
 
 double dev_dot(biot_ctx& c, const double* a, const double* b, int64_t n, cudaStream_t st) {
-  // the pointer goes through pinned host memory so the copy is stream ordered
-  c.hptr[0] = (void*)a;
-  CK(cudaMemcpyAsync(c.ptrbuf, c.hptr, sizeof(void*), cudaMemcpyHostToDevice, st));
-  launch_multidot<double>(reinterpret_cast<const double* const*>(c.ptrbuf), 1, b, n, c.partial, c.hdev + 100, st);
+  const double* va[1] = {a};  // host array of vector pointers (passed to the kernel by value)
+  launch_multidot<double>(va, 1, b, n, c.partial, c.hdev + 100, st);
   CKL();
   CK(cudaMemcpyAsync(c.hhost + 100, c.hdev + 100, sizeof(double), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
@@ -824,8 +837,13 @@ void schur_prepare(biot_ctx& c, double tau, cudaStream_t st) {
   double cm_all[MAXR];
   schur_cm(c, cm_all);
   launch_schur_dinv<T>(g, c.tab<T>(), c.sb2<T>(), cm_all, tau, w.pdinv, c.nt * c.nb, st);
-  for (int b = 0; b < c.nb; ++b)
-    launch_schur_stencil<T>(g, c.tab<T>(), c.dmq<T>() + b * nqt, tau, w.scoef + (int64_t)b * 16 * g.Np, st);
+  for (int b = 0; b < c.nb; ++b) {
+    // FP32 runs the matrix-free step; FP64 (a small share of the work, on the slow FP64 pipe)
+    // keeps the precomputed stencil, which needs no divisions
+    if (sizeof(T) == 4) launch_schur_wq<T>(g, c.tab<T>(), c.dmq<T>() + b * nqt, tau, w.wq + (int64_t)b * nqt, st);
+    if (use_schur_mg(c) || sizeof(T) == 8)
+      launch_schur_stencil<T>(g, c.tab<T>(), c.dmq<T>() + b * nqt, tau, w.scoef + (int64_t)b * 16 * g.Np, st);
+  }
   CKL();
   if (use_schur_mg(c)) {
     // Galerkin stencils of the cell levels: 2^d Gauss points -> cell, then 2^d cells -> cell
@@ -954,8 +972,11 @@ void schur_solve(biot_ctx& c, double tau, cudaStream_t st, int k0, int nk) {
       return;
     }
     for (int k = 0; k < cc.n; ++k) {
-      launch_schur_cheb_st<T>(g, c.tab<T>(), w.scoef, dinv, cm, cc.c1[k], cc.c2[k], k == 0 ? 1 : 0, w.gp, w.pp, w.pd, w.pxo,
-                              nk * c.nb, st);
+      if (sizeof(T) == 4)
+        launch_schur_cheb_mf<T>(g, c.tab<T>(), w.wq, cm, cc.c1[k], cc.c2[k], k == 0 ? 1 : 0, w.gp, w.pp, w.pd, w.pxo, nk, st);
+      else
+        launch_schur_cheb_st<T>(g, c.tab<T>(), w.scoef, dinv, cm, cc.c1[k], cc.c2[k], k == 0 ? 1 : 0, w.gp, w.pp, w.pd, w.pxo,
+                                nk * c.nb, st);
       CKL();
       std::swap(w.pp, w.pxo);
     }
@@ -1086,9 +1107,10 @@ void arnoldi_step_body(biot_ctx& c, double tau, int transpose, int j, cudaStream
     CKL();
     return;
   }
-  launch_multidot<T>(K.dV, j + 1, w, n, c.partial, hd, st);
-  launch_multiaxpy_dot<T>(K.dV, j + 1, hd, w, n, 1, c.partial, hd + 64, st);
-  launch_multiaxpy_dot<T>(K.dV, j + 1, hd + 64, w, n, 2, c.partial, hd + 128, st);
+  const T* const* Vh = K.V.data();  // host array of basis pointers (kernel parameters)
+  launch_multidot<T>(Vh, j + 1, w, n, c.partial, hd, st);
+  launch_multiaxpy_dot<T>(Vh, j + 1, hd, w, n, 1, c.partial, hd + 64, st);
+  launch_multiaxpy_dot<T>(Vh, j + 1, hd + 64, w, n, 2, c.partial, hd + 128, st);
   launch_scale_into<T>(w, w, hd + 129, 0, n, st);  // hd[129] = 1/||w|| from the norm reduction
   CKL();
 }
@@ -1156,7 +1178,8 @@ int gmres(biot_ctx& c, double tau, int transpose, const T* b, T* x, double tol_a
   std::vector<double> H((m + 1) * m), cs(m), sn(m), gv(m + 1), y(m);
   double* hd = c.hdev;
   auto norm2 = [&](T* v) -> double {
-    launch_multidot<T>(K.dV, 1, v, n, c.partial, hd + 128, st);  // K.dV[0] == V_0 == v
+    const T* vp[1] = {v};
+    launch_multidot<T>(vp, 1, v, n, c.partial, hd + 128, st);
     CKL();
     CK(cudaMemcpyAsync(c.hhost + 128, hd + 128, sizeof(double), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
@@ -1507,6 +1530,7 @@ int solve_slab_impl(biot_ctx& c, double tau, const double* rhs, double* x, const
       cudaStreamWaitEvent(su, c.ev_out, 0);
     }
   } rejoin{c, st_user};
+  NvtxRange range_solve("biot solve_slab");
   if (c.nb > 1) return solve_slab_batch(c, tau, rhs, x, o, s, st);
   if (o.mode == BIOT_FIXED_STRESS) return solve_fixed_stress(c, tau, rhs, x, o, s, st);
   const int64_t n = c.g.N * c.nt;
@@ -1536,6 +1560,7 @@ int solve_slab_impl(biot_ctx& c, double tau, const double* rhs, double* x, const
       if (!std::isfinite(rn)) { rc = BIOT_EBREAKDOWN; break; }
       if (rn <= o.tol * bn) { rc = BIOT_OK; break; }
       if (iters >= o.max_iters || refs >= 50) { rc = BIOT_ENOCONV; break; }
+      NvtxRange range_ref("biot FP32 inner solve");
       launch_axpby<double>(c.r64, c.r64, 0.0, 1.0 / rn, n, st);
       launch_convert<double, float>(c.r64, c.r32, n, st);
       CK(cudaMemsetAsync(c.d32, 0, n * sizeof(float), st));
@@ -1781,19 +1806,24 @@ void build_slab_rhs(biot_ctx& c, double t0, double tau, int nterms, const double
   CKL();
 }
 
+// Slabs first .. first + count - 1 of the uniform partition of (0, T] into `slabs` slabs, from
+// the state U0 = U(t_first^-).  X_all, ckpt and iters are indexed from the first marched slab.
 void march_impl(biot_ctx& c, double T, int slabs, int nterms, const double* const* f_terms, const double* tcoef,
                 const double* U0, double* U_end, double* X_all, double* ckpt, const biot_solve_opts& o, int* iters,
-                biot_stats& st_out, cudaStream_t st, int& rc_out) {
+                biot_stats& st_out, cudaStream_t st, int& rc_out, int first = 0, int count = -1) {
   double t_start = now_s();
   const Grid& g = c.g;
+  NvtxRange range_march("biot march");
   MarchBufs mb;
   march_prepare(c, nterms, f_terms, U0, mb, st);
   const double tau = T / slabs;
+  if (count < 0) count = slabs - first;
   biot_stats tot{0, 0, 0, 0.0, 0.0};
   rc_out = BIOT_OK;
-  for (int nsl = 0; nsl < slabs; ++nsl) {
+  for (int nsl = 0; nsl < count; ++nsl) {
+    NvtxRange range_slab("biot slab");
     if (ckpt) CK(cudaMemcpyAsync(ckpt + (int64_t)nsl * g.N, mb.U, g.N * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    build_slab_rhs(c, nsl * tau, tau, nterms, tcoef, mb, st);
+    build_slab_rhs(c, (first + nsl) * tau, tau, nterms, tcoef, mb, st);
     for (int k = 0; k < c.nt; ++k) CK(cudaMemcpyAsync(mb.X + k * g.N, mb.U, g.N * sizeof(double), cudaMemcpyDeviceToDevice, st));
     biot_stats s;
     int rc = solve_slab_impl(c, tau, mb.rhs, mb.X, o, s, st);
@@ -1806,7 +1836,7 @@ void march_impl(biot_ctx& c, double T, int slabs, int nterms, const double* cons
     if (X_all) CK(cudaMemcpyAsync(X_all + (int64_t)nsl * g.N * c.nt, mb.X, g.N * c.nt * sizeof(double), cudaMemcpyDeviceToDevice, st));
     CK(cudaMemcpyAsync(mb.U, mb.X + (int64_t)(c.nt - 1) * g.N, g.N * sizeof(double), cudaMemcpyDeviceToDevice, st));
   }
-  if (ckpt) CK(cudaMemcpyAsync(ckpt + (int64_t)slabs * g.N, mb.U, g.N * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  if (ckpt) CK(cudaMemcpyAsync(ckpt + (int64_t)count * g.N, mb.U, g.N * sizeof(double), cudaMemcpyDeviceToDevice, st));
   if (U_end) CK(cudaMemcpyAsync(U_end, mb.U, g.N * sizeof(double), is_device_ptr(U_end) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   tot.seconds = now_s() - t_start;
@@ -1956,6 +1986,20 @@ int setup_impl(const biot_mesh* mesh, const biot_coeffs* co, int r, const biot_o
     if (!(co->invM >= 0) || !(co->K_dr > 0) || !(co->mu > 0) || !(co->lambda >= 0) || !(co->eta > 0))
       fail(BIOT_EINVAL, "coefficients out of range");
     if (!co->K_cell) fail(BIOT_EINVAL, "K_cell is NULL");
+    for (double v : {co->b, co->invM, co->K_dr, co->lambda, co->mu, co->eta})
+      if (!std::isfinite(v)) fail(BIOT_EINVAL, "coefficients must be finite");
+    {
+      // every permeability is checked on the host before the first CUDA call
+      int64_t ncell_all = nb;
+      for (int d = 0; d < mesh->dim; ++d) ncell_all *= mesh->n[d];
+      for (int64_t i = 0; i < ncell_all; ++i)
+        if (!(co->K_cell[i] > 0.0) || !std::isfinite(co->K_cell[i])) {
+          char buf[128];
+          snprintf(buf, sizeof(buf), "K_cell[%lld] = %g: permeabilities must be positive and finite", (long long)i,
+                   co->K_cell[i]);
+          fail(BIOT_EINVAL, buf);
+        }
+    }
     apply_init_attributes();
     {
       const char* ng = std::getenv("BIOT_NO_GRAPHS");
@@ -1963,6 +2007,8 @@ int setup_impl(const biot_mesh* mesh, const biot_coeffs* co, int r, const biot_o
     }
     c->g = make_grid(mesh->dim, mesh->n, mesh->lo, mesh->hi, mesh->u_bc, mesh->f_bc);
     c->g.nb = nb;
+    // the kernels index one temporal level of one instance with 32-bit integers
+    if (c->g.N >= (int64_t)1 << 31) fail(BIOT_EINVAL, "mesh too large: 2^31 or more unknowns per temporal level");
     c->r = r;
     c->nt = r + 1;
     c->b = co->b;
@@ -2016,7 +2062,7 @@ int setup_impl(const biot_mesh* mesh, const biot_coeffs* co, int r, const biot_o
     CK(cudaMallocHost((void**)&c->hhost, ((int64_t)HS * nb + 256) * sizeof(double)));
     CK(cudaMallocHost((void**)&c->bhost, bdev_doubles(c->nt, nb) * sizeof(double)));
     c->partial = dalloc<double>(
-        std::max<int64_t>(RED_BLOCKS * 16, std::max(seg_partial_doubles(c->nt * nb), seg_partial_doubles(nb))));
+        std::max<int64_t>(RED_BLOCKS * 32, std::max(seg_partial_doubles(c->nt * nb), seg_partial_doubles(nb))));
     c->lvl64 = dalloc<double>(g.N);
     c->lvl64b = dalloc<double>(g.N);
     cudaStream_t st = 0;  // set-up runs on the legacy stream, ordered with its synchronous copies
@@ -2133,6 +2179,24 @@ extern "C" int biot_march(biot_t c, double T, int slabs, int nterms, const doubl
   biot_stats s{0, 0, 0, 0.0, 0.0};
   int rc = BIOT_OK;
   march_impl(*c, T, slabs, nterms, f_terms, tcoef, U0, U_end, X_all, nullptr, o, iters_per_slab, s, (cudaStream_t)stream, rc);
+  if (stats) *stats = s;
+  return rc;
+  API_END(c)
+}
+
+extern "C" int biot_march_resume(biot_t c, double T, int slabs, int first, int count, int nterms, const double* const* f_terms,
+                                 const double* tcoef, const double* U_first, double* U_end, double* X_all,
+                                 const biot_solve_opts* opts, int* iters_per_slab, biot_stats* stats, void* stream) {
+  API_BEGIN(c)
+  if (!(T > 0) || slabs < 1) fail(BIOT_EINVAL, "march_resume: T must be > 0 and slabs >= 1");
+  if (first < 0 || count < 1 || first + count > slabs) fail(BIOT_EINVAL, "march_resume: need 0 <= first < first + count <= slabs");
+  if (nterms > 0 && (!f_terms || !tcoef)) fail(BIOT_EINVAL, "march_resume: load terms missing");
+  if (c->nb > 1) fail(BIOT_EINVAL, "march_resume: batched context");
+  biot_solve_opts o = solve_defaults(opts);
+  biot_stats s{0, 0, 0, 0.0, 0.0};
+  int rc = BIOT_OK;
+  march_impl(*c, T, slabs, nterms, f_terms, tcoef, U_first, U_end, X_all, nullptr, o, iters_per_slab, s, (cudaStream_t)stream, rc,
+             first, count);
   if (stats) *stats = s;
   return rc;
   API_END(c)
@@ -2513,6 +2577,20 @@ void apply_part_T(biot_ctx& c, int part, double tau, const T* in, T* out, cudaSt
     CK(cudaMemcpyAsync(out, lw.x, g.Nu * sizeof(T), cudaMemcpyDeviceToDevice, st));
   } else if (part == BIOT_PART_ELASTICITY) {
     apply_A<T>(c.lv[0], c.lam, c.mu, tau, in, out, 1, st);
+  } else if (part == BIOT_PART_SCHUR_STEP) {
+    if (!c.lumped_flux || c.nb != 1) fail(BIOT_EINVAL, "apply_part: BIOT_PART_SCHUR_STEP needs a lumped, unbatched context");
+    prec_prepare<T>(c, tau, st);
+    double cm[1] = {c.invM + c.beta};
+    // one step of the kernel the solver runs in this precision, with c1 = 0, c2 = 1 and b = 0:
+    // out_p = in_p - diag(Shat)^{-1} Shat in_p
+    CK(cudaMemsetAsync(w.gp, 0, g.Np * sizeof(T), st));
+    if (sizeof(T) == 4) {
+      launch_schur_cheb_mf<T>(g, c.tab<T>(), w.wq, cm, 0.0, 1.0, 0, w.gp, in + g.offp, w.pd, out + g.offp, 1, st);
+    } else {
+      launch_schur_dinv<T>(g, c.tab<T>(), c.sb2<T>(), cm, tau, w.pdinv, 1, st);
+      launch_schur_cheb_st<T>(g, c.tab<T>(), w.scoef, w.pdinv, cm, 0.0, 1.0, 0, w.gp, in + g.offp, w.pd, out + g.offp, 1, st);
+      w.schur_tau = -1;  // the solver's diagonals of this tau were overwritten
+    }
   } else {
     fail(BIOT_EINVAL, "unknown part");
   }
@@ -2618,7 +2696,7 @@ extern "C" void biot_destroy(biot_t c) {
   if (c->ev_out) cudaEventDestroy(c->ev_out);
   if (c->ws) cudaStreamDestroy(c->ws);
   auto FP = [&](auto& w) {
-    F(w.tA); F(w.tB); F(w.fq); F(w.tq); F(w.fq2); F(w.gp); F(w.pp); F(w.pd); F(w.pAx); F(w.pxo); F(w.pdinv); F(w.scoef);
+    F(w.tA); F(w.tB); F(w.fq); F(w.tq); F(w.fq2); F(w.gp); F(w.pp); F(w.pd); F(w.pAx); F(w.pxo); F(w.pdinv); F(w.scoef); F(w.wq);
     for (auto* v : {&w.pms, &w.pmb, &w.pmx, &w.pmd, &w.pmt})
       for (auto p : *v) F(p);
     F(w.pmr0);

@@ -86,10 +86,9 @@ __global__ void __launch_bounds__(256) k_add_Ep(Grid g, TabT<T> tb, SlabCoef sc,
                                                 T* __restrict__ y, int64_t sy) {
   const int64_t node = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (node >= g.nnode) return;
-  const int ix = (int)(node % g.nu[0]);
-  const int64_t rr = node / g.nu[0];
-  const int iy = (int)(rr % g.nu[1]);
-  const int iz = DIM == 3 ? (int)(rr / g.nu[1]) : 0;
+  int ix, iy, iz;
+  unlex3(node, g.nu[0], g.nu[1], ix, iy, iz);
+  if (DIM == 2) iz = 0;
   const EpNode<T, DIM> en(g, tb, ix, iy, iz);
   const int b = blockIdx.y, nb = g.nb;  // instance of a batched grid
   T s[MAXR][DIM];  // s[k][c] = sum_l ep[k][l] (E_c p_l)
@@ -441,10 +440,7 @@ __global__ void k_apply_q(Grid g, TabT<T> tb, SlabCoef sc, const T* __restrict__
   // grid coordinates of this component's DoF grid
   int sh[3], co[3];
   for (int d = 0; d < 3; ++d) sh[d] = (d < DIM) ? ((d == c) ? g.nu[d] : g.ng[d]) : 1;
-  co[0] = (int)(r % sh[0]);
-  int64_t rr = r / sh[0];
-  co[1] = (int)(rr % sh[1]);
-  co[2] = (int)(rr / sh[1]);
+  unlex3(r, sh[0], sh[1], co[0], co[1], co[2]);
   const int64_t qoff = g.offq[c];
   const int64_t gidx = qoff + r;
   const int ia = co[c];
@@ -511,10 +507,7 @@ __global__ void __launch_bounds__(256) k_apply_p(Grid g, TabT<T> tb, SlabCoef sc
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= g.Np) return;
   int co[3];
-  co[0] = (int)(t % g.ng[0]);
-  int64_t rr = t / g.ng[0];
-  co[1] = (int)(rr % g.ng[1]);
-  co[2] = (int)(rr / g.ng[1]);
+  unlex3(t, g.ng[0], g.ng[1], co[0], co[1], co[2]);
   int cell[3], gq[3];
   for (int d = 0; d < 3; ++d) { cell[d] = (d < DIM) ? co[d] >> 1 : 0; gq[d] = (d < DIM) ? (co[d] & 1) : 0; }
   T mp = T(1);
@@ -559,15 +552,169 @@ __global__ void __launch_bounds__(256) k_apply_p(Grid g, TabT<T> tb, SlabCoef sc
 }
 
 // ---------------------------------------------------------------------------
+// pressure rows, one thread per cell and instance: the cell's 2^DIM Gauss points for every
+// temporal output level.  E^T u is sum-factorised over the cell's 3^DIM nodes per component
+// (x, then y, then z contraction), B q gathers the cell's flux DoFs line by line; every value
+// of the cell is loaded once for all of its points.  Same arithmetic as k_apply_p:
+//   Y^p_k = pq[k] B q_k + sum_l (pu[k][l] E^T u_l + pp[k][l] Mp p_l).
+template <typename T, int DIM>
+__global__ void __launch_bounds__(128) k_apply_p_cell(Grid g, TabT<T> tb, SlabCoef sc, const T* __restrict__ x, int64_t sx,
+                                                      T* __restrict__ y, int64_t sy) {
+  constexpr int NP = 1 << DIM;        // points per cell
+  constexpr int NL = 1 << (DIM - 1);  // lines per cell and direction
+  constexpr int NA = DIM == 3 ? 3 : 1;
+  const int cid = blockIdx.x * blockDim.x + threadIdx.x;
+  if (cid >= (int)g.ncells) return;
+  const int bi = blockIdx.y, nb = g.nb;
+  int cx, cy, cz;
+  unlex3(cid, g.n[0], g.n[1], cx, cy, cz);
+  if (DIM == 2) cz = 0;
+  const int cc[3] = {cx, cy, cz};
+  const int nx = g.nu[0], ny = g.nu[1], nz = g.nu[2];
+  const int pst[3] = {1, g.ng[0], g.ng[0] * g.ng[1]};
+  const int pbase = 2 * cx + pst[1] * 2 * cy + pst[2] * 2 * cz;
+  bool interior = cx > 0 && cx < g.n[0] - 1 && cy > 0 && cy < g.n[1] - 1;
+  if (DIM == 3) interior = interior && cz > 0 && cz < g.n[2] - 1;
+  T mp = T(1);
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) mp *= tb.wg[d];
+  int fm[DIM];
+#pragma unroll
+  for (int c = 0; c < DIM; ++c) fm[c] = u_face_mask(g, c);
+  T out[MAXR][NP];
+#pragma unroll
+  for (int k = 0; k < MAXR; ++k)
+#pragma unroll
+    for (int p = 0; p < NP; ++p) out[k][p] = T(0);
+#pragma unroll
+  for (int l = 0; l < MAXR; ++l) {
+    if (l >= sc.nt) break;
+    const T* xl = x + (int64_t)(l * nb + bi) * sx;
+    // ---- E^T u at the cell's points
+    T eu[NP];
+#pragma unroll
+    for (int p = 0; p < NP; ++p) eu[p] = T(0);
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) {
+      // 1-D factors of component c: derivative along c, value across
+      T fx[3][2], fy[3][2], fz[3][2];
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          fx[a][q] = (c == 0) ? tb.bd[0][a][q] : tb.bv[0][a][q];
+          fy[a][q] = (c == 1) ? tb.bd[1][a][q] : tb.bv[1][a][q];
+          fz[a][q] = (DIM == 3) ? ((c == 2) ? tb.bd[2][a][q] : tb.bv[2][a][q]) : T(a == 0 ? 1 : 0);
+        }
+      const T* uc = xl + c * g.nnode;
+      T t2[NA][2][2];  // [az][gy][gx]
+#pragma unroll
+      for (int az = 0; az < NA; ++az)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) t2[az][q >> 1][q & 1] = T(0);
+#pragma unroll
+      for (int az = 0; az < NA; ++az) {
+        const int iz = 2 * cz + az;
+#pragma unroll
+        for (int ay = 0; ay < 3; ++ay) {
+          const int iy = 2 * cy + ay;
+          const T* row = uc + ((int64_t)iz * ny + iy) * nx + 2 * cx;
+          T v[3];
+#pragma unroll
+          for (int ax = 0; ax < 3; ++ax)
+            v[ax] = (interior || u_free_mask(fm[c], 2 * cx + ax, iy, iz, nx, ny, nz)) ? __ldg(row + ax) : T(0);
+#pragma unroll
+          for (int gx = 0; gx < 2; ++gx) {
+            const T t1 = fx[0][gx] * v[0] + fx[1][gx] * v[1] + fx[2][gx] * v[2];
+#pragma unroll
+            for (int gy = 0; gy < 2; ++gy) t2[az][gy][gx] += fy[ay][gy] * t1;
+          }
+        }
+      }
+#pragma unroll
+      for (int p = 0; p < NP; ++p) {
+        const int gx = p & 1, gy = (p >> 1) & 1, gz = (p >> 2) & 1;
+        T a = 0;
+#pragma unroll
+        for (int az = 0; az < NA; ++az) a += fz[az][gz] * t2[az][gy][gx];
+        eu[p] += a;
+      }
+    }
+    // ---- B q at the cell's points
+    T bq[NP];
+#pragma unroll
+    for (int p = 0; p < NP; ++p) bq[p] = T(0);
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) {
+      int mul = 1, stride_c = 1;
+      int64_t base = g.offq[c];
+      T wt = T(1);
+#pragma unroll
+      for (int k2 = 0; k2 < DIM; ++k2) {
+        if (k2 == c) stride_c = mul;
+        else wt *= tb.wg[k2];
+        mul *= (k2 == c) ? g.nu[k2] : g.ng[k2];
+      }
+      bool fr[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) fr[a] = q_free(g, c, 2 * cc[c] + a);
+#pragma unroll
+      for (int l2 = 0; l2 < NL; ++l2) {
+        // transverse Gauss-line coordinates of line l2, the point with along-c bit 0
+        int64_t off = base + (int64_t)(2 * cc[c]) * stride_c;
+        int p0 = 0, bit = 0, m2 = 1;
+#pragma unroll
+        for (int k2 = 0; k2 < DIM; ++k2) {
+          if (k2 != c) {
+            const int b = (l2 >> bit) & 1;
+            off += (int64_t)(2 * cc[k2] + b) * m2;
+            p0 |= b << k2;
+            ++bit;
+          }
+          m2 *= (k2 == c) ? g.nu[k2] : g.ng[k2];
+        }
+        T qa[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) qa[a] = fr[a] ? xl[off + (int64_t)a * stride_c] : T(0);
+#pragma unroll
+        for (int gq = 0; gq < 2; ++gq)
+          bq[p0 | (gq << c)] += wt * (tb.bd[c][0][gq] * qa[0] + tb.bd[c][1][gq] * qa[1] + tb.bd[c][2][gq] * qa[2]);
+      }
+    }
+    // ---- pressure values and the level's contributions to every output level
+    const T* pl = xl + g.offp + pbase;
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+      const int gx = p & 1, gy = (p >> 1) & 1, gz = (p >> 2) & 1;
+      const T pv = pl[gx + gy * pst[1] + gz * pst[2]];
+#pragma unroll
+      for (int k = 0; k < MAXR; ++k) {
+        if (k >= sc.nt) break;
+        out[k][p] += T(sc.pu[k][l]) * eu[p] + T(sc.pp[k][l]) * mp * pv;
+        if (k == l) out[k][p] += T(sc.pq[k]) * bq[p];
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < MAXR; ++k) {
+    if (k >= sc.nt) break;
+    T* yk = y + (int64_t)(k * nb + bi) * sy + g.offp + pbase;
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+      const int gx = p & 1, gy = (p >> 1) & 1, gz = (p >> 2) & 1;
+      yk[gx + gy * pst[1] + gz * pst[2]] = out[k][p];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // diagonal of the elasticity block A (unit tau) per node and component
 template <typename T, int DIM>
 __global__ void k_diag_A(Grid g, TabT<T> tb, double lam, double mu, T* __restrict__ d) {
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= g.nnode) return;
-  int ix = (int)(t % g.nu[0]);
-  int64_t rr = t / g.nu[0];
-  int iy = (int)(rr % g.nu[1]);
-  int iz = (int)(rr / g.nu[1]);
+  int ix, iy, iz;
+  unlex3(t, g.nu[0], g.nu[1], ix, iy, iz);
   int rt[3] = {rowtype(ix, g.nu[0]), rowtype(iy, g.nu[1]), DIM == 3 ? rowtype(iz, g.nu[2]) : 0};
   T Mc[3], Kc[3];
   for (int e = 0; e < DIM; ++e) { Mc[e] = tb.q2[e][0][rt[e]][2]; Kc[e] = tb.q2[e][1][rt[e]][2]; }
@@ -595,7 +742,12 @@ void launch_apply_u(const Grid& g, const TabT<T>& tb, const SlabCoef& sc, const 
   if (scu.ucols <= 0) { scu.ucols = sc.nt * g.nb; scu.udiv = g.nb; }
   if (scu.udiv <= 0) scu.udiv = 1;
   const int cols = scu.ucols;
-  if (g.dim == 3) {
+  if (g.dim == 3 && sizeof(T) == 4 && g.nnode >= ELAST3_MIN_NODES) {
+    // FP32 on the fine multigrid levels: the z-marching kernel (elast3.cu); the coarse levels,
+    // where a serial march over the planes would be latency-bound, keep the 8^3-tile kernel
+    launch_elast3_f32(g, *reinterpret_cast<const TabT<float>*>(&tb), scu, cols, reinterpret_cast<const float*>(u), su,
+                      reinterpret_cast<float*>(y), sy, st, reinterpret_cast<const UEpi<float>*>(&ep));
+  } else if (g.dim == 3) {
     constexpr bool ALLJ = sizeof(T) == 4;
     dim3 grid((g.nu[0] + T3 - 1) / T3, (g.nu[1] + T3 - 1) / T3, ((g.nu[2] + T3 - 1) / T3) * cols);
     size_t smem = sizeof(T) * (3 * H3 * H3 * H3 + (ALLJ ? 12 : 4) * H3 * H3 * T3 + 12 * H3 * T3 * T3);
@@ -634,9 +786,9 @@ void launch_apply_q(const Grid& g, const TabT<T>& tb, const SlabCoef& sc, const 
 template <typename T>
 void launch_apply_p(const Grid& g, const TabT<T>& tb, const SlabCoef& sc, const T* x, int64_t sx, T* y, int64_t sy,
                     cudaStream_t st) {
-  const dim3 blocks((unsigned)((g.Np + 255) / 256), g.nb);
-  if (g.dim == 3) (note_launch(), k_apply_p<T, 3><<<blocks, 256, 0, st>>>(g, tb, sc, x, sx, y, sy));
-  else (note_launch(), k_apply_p<T, 2><<<blocks, 256, 0, st>>>(g, tb, sc, x, sx, y, sy));
+  const dim3 blocks((unsigned)((g.ncells + 127) / 128), g.nb);
+  if (g.dim == 3) (note_launch(), k_apply_p_cell<T, 3><<<blocks, 128, 0, st>>>(g, tb, sc, x, sx, y, sy));
+  else (note_launch(), k_apply_p_cell<T, 2><<<blocks, 128, 0, st>>>(g, tb, sc, x, sx, y, sy));
 }
 
 template <typename T>
@@ -650,6 +802,7 @@ void launch_diag_A(const Grid& g, const TabT<T>& tb, double lam, double mu, T* d
 void apply_init_attributes() {
   static std::once_flag once;
   std::call_once(once, [] {
+  elast3_init_attributes();
   cudaFuncSetAttribute(k_apply_u3_col<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)(sizeof(float) * (3 * H3 * H3 * H3 + 12 * H3 * H3 * T3 + 12 * H3 * T3 * T3)));
   cudaFuncSetAttribute(k_apply_u3_col<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,

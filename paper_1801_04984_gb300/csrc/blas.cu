@@ -39,6 +39,7 @@ struct DotAcc<double> {
   double s;
   __device__ void init() { s = 0.0; }
   __device__ void add(double x, double y) { s = fma(x, y, s); }
+  __device__ void add_plain(double x) { s += x; }
   __device__ double get() const { return s; }
 };
 template <>
@@ -46,6 +47,7 @@ struct DotAcc<float> {
   Acc a;
   __device__ void init() { a.hi = 0.f; a.lo = 0.f; }
   __device__ void add(float x, float y) { acc_fma(a, x, y); }
+  __device__ void add_plain(float x) { a.hi += x; }  // uncompensated
   __device__ double get() const { return (double)a.hi + (double)a.lo; }
 };
 
@@ -66,23 +68,87 @@ __device__ inline void block_reduce_store(double* vals, int cnt, double* partial
   }
 }
 
+// Basis pointers travel as a kernel parameter (constant bank): no pointer loads per element,
+// and a CUDA graph that captures the launch keeps them.
 template <typename TV>
-__global__ void __launch_bounds__(256) k_multidot(const TV* const* __restrict__ V, int nv, const TV* __restrict__ w, int64_t n,
-                                                  double* __restrict__ partial) {
-  DotAcc<TV> acc[NV];
+struct PtrPack {
+  const TV* p[MAXDOT];
+};
+// 16-byte vectors of the element type
+template <typename TV>
+struct Vec16;
+template <>
+struct Vec16<float> {
+  using T = float4;
+  static constexpr int W = 4;
+  __device__ static void get(const T& v, float (&o)[4]) { o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w; }
+  __device__ static T make(const float (&o)[4]) { return make_float4(o[0], o[1], o[2], o[3]); }
+};
+template <>
+struct Vec16<double> {
+  using T = double2;
+  static constexpr int W = 2;
+  __device__ static void get(const T& v, double (&o)[2]) { o[0] = v.x; o[1] = v.y; }
+  __device__ static T make(const double (&o)[2]) { return make_double2(o[0], o[1]); }
+};
+
+// block-reduce `cnt` (<= NVM) doubles per thread, write to partial[bid * stride + i]
+template <int NVM>
+__device__ inline void block_reduce_store_n(const double* vals, int cnt, double* partial, int stride, int64_t bid) {
+  __shared__ double sh[NVM][8];  // 256 threads = 8 warps
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
-  for (int i = 0; i < NV; ++i) acc[i].init();
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += stride) {
-    TV we = w[e];
-#pragma unroll
-    for (int i = 0; i < NV; ++i)
-      if (i < nv) acc[i].add(V[i][e], we);
+  for (int i = 0; i < NVM; ++i) {
+    if (i >= cnt) break;
+    double v = vals[i];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) sh[i][warp] = v;
   }
-  double vals[NV];
+  __syncthreads();
+  if (threadIdx.x < cnt) {
+    double s = 0;
+    for (int w = 0; w < nw; ++w) s += sh[threadIdx.x][w];
+    partial[bid * stride + threadIdx.x] = s;
+  }
+}
+
+// dots V_i^T w, i < nv <= NVM, in one pass over w: 16-byte loads, per-thread compensated
+// FP32 (or plain FP64) accumulation, partials per block
+template <typename TV, int NVM, bool VEC>
+__global__ void __launch_bounds__(256) k_multidot(const __grid_constant__ PtrPack<TV> V, int nv, const TV* __restrict__ w, int64_t n,
+                                                  double* __restrict__ partial) {
+  using VT = typename Vec16<TV>::T;
+  constexpr int W = Vec16<TV>::W;
+  DotAcc<TV> acc[NVM];
 #pragma unroll
-  for (int i = 0; i < NV; ++i) vals[i] = acc[i].get();
-  block_reduce_store(vals, nv, partial, NV + 1, blockIdx.x);
+  for (int i = 0; i < NVM; ++i) acc[i].init();
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t nvec = VEC ? n / W : 0;
+  for (int64_t e = t0; e < nvec; e += stride) {
+    TV wv[W];
+    Vec16<TV>::get(reinterpret_cast<const VT*>(w)[e], wv);
+#pragma unroll
+    for (int i = 0; i < NVM; ++i) {
+      if (i >= nv) break;
+      TV vv[W];
+      Vec16<TV>::get(__ldg(reinterpret_cast<const VT*>(V.p[i]) + e), vv);
+#pragma unroll
+      for (int q = 0; q < W; ++q) acc[i].add(vv[q], wv[q]);
+    }
+  }
+  for (int64_t e = nvec * W + t0; e < n; e += stride) {  // tail
+    const TV we = w[e];
+#pragma unroll
+    for (int i = 0; i < NVM; ++i) {
+      if (i >= nv) break;
+      acc[i].add(V.p[i][e], we);
+    }
+  }
+  double vals[NVM];
+#pragma unroll
+  for (int i = 0; i < NVM; ++i) vals[i] = acc[i].get();
+  block_reduce_store_n<NVM>(vals, nv, partial, NVM, blockIdx.x);
 }
 
 // sum partial[b][i] over blocks b (fixed order) -> out[i]
@@ -107,67 +173,145 @@ __global__ void k_final_reduce(const double* __restrict__ partial, int nblocks, 
   }
 }
 
+constexpr int DOT_PASS = 32;  // vectors per pass of the multi-dot / multi-axpy
+
+template <typename TV>
+bool aligned16(const TV* p) {
+  return (reinterpret_cast<uintptr_t>(p) & 15) == 0;
+}
+
+// V: HOST array of nv device pointers (every vector 16-byte aligned)
 template <typename TV>
 void launch_multidot(const TV* const* V, int nv, const TV* w, int64_t n, double* partial, double* out, cudaStream_t st) {
-  for (int c0 = 0; c0 < nv; c0 += NV) {
-    int cnt = (nv - c0 < NV) ? nv - c0 : NV;
-    (note_launch(), k_multidot<TV><<<RED_BLOCKS, 256, 0, st>>>(V + c0, cnt, w, n, partial));
-    (note_launch(), k_final_reduce<<<1, 256, 0, st>>>(partial, RED_BLOCKS, cnt, NV + 1, out + c0));
+  for (int c0 = 0; c0 < nv; c0 += DOT_PASS) {
+    const int cnt = (nv - c0 < DOT_PASS) ? nv - c0 : DOT_PASS;
+    PtrPack<TV> pk;
+    bool vec = aligned16(w);
+    for (int i = 0; i < MAXDOT; ++i) {
+      pk.p[i] = (i < cnt) ? V[c0 + i] : nullptr;
+      if (i < cnt) vec = vec && aligned16(pk.p[i]);
+    }
+    // 16-byte loads when every vector allows them (library buffers always do; caller
+    // vectors at an offset may not)
+    if (vec) {
+      if (cnt <= 8) (note_launch(), k_multidot<TV, 8, true><<<RED_BLOCKS, 256, 0, st>>>(pk, cnt, w, n, partial));
+      else if (cnt <= 16) (note_launch(), k_multidot<TV, 16, true><<<RED_BLOCKS, 256, 0, st>>>(pk, cnt, w, n, partial));
+      else (note_launch(), k_multidot<TV, 32, true><<<RED_BLOCKS, 256, 0, st>>>(pk, cnt, w, n, partial));
+    } else {
+      if (cnt <= 8) (note_launch(), k_multidot<TV, 8, false><<<RED_BLOCKS, 256, 0, st>>>(pk, cnt, w, n, partial));
+      else if (cnt <= 16) (note_launch(), k_multidot<TV, 16, false><<<RED_BLOCKS, 256, 0, st>>>(pk, cnt, w, n, partial));
+      else (note_launch(), k_multidot<TV, 32, false><<<RED_BLOCKS, 256, 0, st>>>(pk, cnt, w, n, partial));
+    }
+    const int stride = cnt <= 8 ? 8 : (cnt <= 16 ? 16 : 32);
+    (note_launch(), k_final_reduce<<<1, 256, 0, st>>>(partial, RED_BLOCKS, cnt, stride, out + c0));
   }
 }
 
-// mode 0: w -= V h ; mode 1: also partial dots V^T w_new ; mode 2: also ||w_new||^2
-template <typename TV>
-__global__ void __launch_bounds__(256) k_multiaxpy(const TV* const* __restrict__ V, int nv, const double* __restrict__ h,
+// mode 0: w -= V h ; mode 1: also dots V^T w_new ; mode 2: also ||w_new||^2.  The update runs
+// in the vectors' precision; mode 1 reads the basis a second time right after (cache hits).
+template <typename TV, int NVM, bool VEC>
+__global__ void __launch_bounds__(256) k_multiaxpy(const __grid_constant__ PtrPack<TV> V, int nv, const double* __restrict__ h,
                                                    TV* __restrict__ w, int64_t n, int mode, double* __restrict__ partial) {
-  TV hv[NV];
+  using VT = typename Vec16<TV>::T;
+  constexpr int W = Vec16<TV>::W;
+  __shared__ TV hs[NVM];
+  if (threadIdx.x < NVM) hs[threadIdx.x] = (threadIdx.x < nv) ? (TV)h[threadIdx.x] : TV(0);
+  __syncthreads();
+  DotAcc<TV> acc[NVM];
 #pragma unroll
-  for (int i = 0; i < NV; ++i) hv[i] = (i < nv) ? (TV)h[i] : TV(0);
-  DotAcc<TV> acc[NV];
-#pragma unroll
-  for (int i = 0; i < NV; ++i) acc[i].init();
+  for (int i = 0; i < NVM; ++i) acc[i].init();
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += stride) {
-    TV v[NV];
+  const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t nvec = VEC ? n / W : 0;
+  for (int64_t e = t0; e < nvec; e += stride) {
+    TV wv[W];
+    Vec16<TV>::get(reinterpret_cast<const VT*>(w)[e], wv);
+#pragma unroll
+    for (int i = 0; i < NVM; ++i) {
+      if (i >= nv) break;
+      TV vv[W];
+      Vec16<TV>::get(__ldg(reinterpret_cast<const VT*>(V.p[i]) + e), vv);
+      const TV hi = hs[i];
+#pragma unroll
+      for (int q = 0; q < W; ++q) wv[q] -= hi * vv[q];
+    }
+    reinterpret_cast<VT*>(w)[e] = Vec16<TV>::make(wv);
+    if (mode == 1) {
+      // second Gram-Schmidt coefficients: w is already orthogonal to the basis up to the
+      // first pass's rounding, so these dots only need accuracy relative to ||v|| ||w||;
+      // plain per-thread accumulation (then FP64 across threads) is enough
+#pragma unroll
+      for (int i = 0; i < NVM; ++i) {
+        if (i >= nv) break;
+        TV vv[W];
+        Vec16<TV>::get(__ldg(reinterpret_cast<const VT*>(V.p[i]) + e), vv);
+        TV sdot = TV(0);
+#pragma unroll
+        for (int q = 0; q < W; ++q) sdot = fma(vv[q], wv[q], sdot);
+        acc[i].add_plain(sdot);
+      }
+    } else if (mode == 2) {
+#pragma unroll
+      for (int q = 0; q < W; ++q) acc[0].add(wv[q], wv[q]);
+    }
+  }
+  for (int64_t e = nvec * W + t0; e < n; e += stride) {  // tail
     TV we = w[e];
 #pragma unroll
-    for (int i = 0; i < NV; ++i)
-      if (i < nv) { v[i] = V[i][e]; we -= hv[i] * v[i]; }
+    for (int i = 0; i < NVM; ++i) {
+      if (i >= nv) break;
+      we -= hs[i] * V.p[i][e];
+    }
     w[e] = we;
     if (mode == 1) {
 #pragma unroll
-      for (int i = 0; i < NV; ++i)
-        if (i < nv) acc[i].add(v[i], we);
+      for (int i = 0; i < NVM; ++i) {
+        if (i >= nv) break;
+        acc[i].add(V.p[i][e], we);
+      }
     } else if (mode == 2) {
       acc[0].add(we, we);
     }
   }
   if (mode == 0) return;
-  double vals[NV];
+  double vals[NVM];
 #pragma unroll
-  for (int i = 0; i < NV; ++i) vals[i] = acc[i].get();
-  block_reduce_store(vals, mode == 1 ? nv : 1, partial, NV + 1, blockIdx.x);
+  for (int i = 0; i < NVM; ++i) vals[i] = acc[i].get();
+  block_reduce_store_n<NVM>(vals, mode == 1 ? nv : 1, partial, NVM, blockIdx.x);
 }
 
 template <typename TV>
 void launch_multiaxpy_dot(const TV* const* V, int nv, const double* h, TV* w, int64_t n, int mode, double* partial,
                           double* out, cudaStream_t st) {
-  // mode 1 needs every chunk's dots against the final w: apply all axpys first
-  // chunk by chunk, then dot in a separate pass when more than one chunk.
-  if (nv <= NV) {
-    (note_launch(), k_multiaxpy<TV><<<RED_BLOCKS, 256, 0, st>>>(V, nv, h, w, n, mode, partial));
-    if (mode == 1) (note_launch(), k_final_reduce<<<1, 256, 0, st>>>(partial, RED_BLOCKS, nv, NV + 1, out));
-    if (mode == 2) (note_launch(), k_final_reduce<<<1, 256, 0, st>>>(partial, RED_BLOCKS, 1, NV + 1, out, out + 1));
-    return;
+  // mode 1 needs every pass's dots against the final w: with more than one pass apply all
+  // updates first, then dot in a separate pass
+  const int npass = (nv + DOT_PASS - 1) / DOT_PASS;
+  for (int c0 = 0; c0 < nv; c0 += DOT_PASS) {
+    const int cnt = (nv - c0 < DOT_PASS) ? nv - c0 : DOT_PASS;
+    const bool last = c0 + DOT_PASS >= nv;
+    const int m = (mode == 2 && last) ? 2 : ((mode == 1 && npass == 1) ? 1 : 0);
+    PtrPack<TV> pk;
+    bool vec = aligned16(w);
+    for (int i = 0; i < MAXDOT; ++i) {
+      pk.p[i] = (i < cnt) ? V[c0 + i] : nullptr;
+      if (i < cnt) vec = vec && aligned16(pk.p[i]);
+    }
+    const int nvm = cnt <= 8 ? 8 : (cnt <= 16 ? 16 : 32);
+#define BIOT_MAXPY(NVM, VEC) (note_launch(), k_multiaxpy<TV, NVM, VEC><<<RED_BLOCKS, 256, 0, st>>>(pk, cnt, h + c0, w, n, m, partial))
+    if (vec) {
+      if (nvm == 8) BIOT_MAXPY(8, true);
+      else if (nvm == 16) BIOT_MAXPY(16, true);
+      else BIOT_MAXPY(32, true);
+    } else {
+      if (nvm == 8) BIOT_MAXPY(8, false);
+      else if (nvm == 16) BIOT_MAXPY(16, false);
+      else BIOT_MAXPY(32, false);
+    }
+#undef BIOT_MAXPY
+    if (m == 1) (note_launch(), k_final_reduce<<<1, 256, 0, st>>>(partial, RED_BLOCKS, cnt, nvm, out));
+    if (m == 2) (note_launch(), k_final_reduce<<<1, 256, 0, st>>>(partial, RED_BLOCKS, 1, nvm, out, out + 1));
   }
-  for (int c0 = 0; c0 < nv; c0 += NV) {
-    int cnt = (nv - c0 < NV) ? nv - c0 : NV;
-    bool last = c0 + NV >= nv;
-    int m = (last && mode == 2) ? 2 : 0;
-    (note_launch(), k_multiaxpy<TV><<<RED_BLOCKS, 256, 0, st>>>(V + c0, cnt, h + c0, w, n, m, partial));
-    if (m == 2) (note_launch(), k_final_reduce<<<1, 256, 0, st>>>(partial, RED_BLOCKS, 1, NV + 1, out, out + 1));
-  }
-  if (mode == 1) launch_multidot<TV>(V, nv, w, n, partial, out, st);
+  if (mode == 1 && npass > 1) launch_multidot<TV>(V, nv, w, n, partial, out, st);
 }
 
 template <typename TA, typename TB>

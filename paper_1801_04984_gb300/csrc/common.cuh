@@ -41,6 +41,16 @@ struct Grid {
                    // (k * nb + b) * N; per-instance coefficient arrays are instance-major.
 };
 
+// Coordinates (i0, i1, i2) of the lexicographic index t (first coordinate fastest) on an
+// n0 x n1 x * grid.  One temporal level of one instance has fewer than 2^31 entries
+// (checked at set-up), so the division runs in 32-bit arithmetic.
+__host__ __device__ __forceinline__ void unlex3(int64_t t, int n0, int n1, int& i0, int& i1, int& i2) {
+  const unsigned u = (unsigned)t, q = u / (unsigned)n0;
+  i0 = (int)(u - q * (unsigned)n0);
+  i1 = (int)(q % (unsigned)n1);
+  i2 = (int)(q / (unsigned)n1);
+}
+
 // 1-D operator taps.  Row types of a Q2 node row: 0 interior vertex, 1 mid
 // node, 2 lower boundary vertex, 3 upper boundary vertex.  Taps are offsets
 // -2..+2 in node index; out-of-range input nodes are zero-padded, so boundary

@@ -117,13 +117,16 @@ struct EtPoint {
   int cell[3];
   T f[DIM][3][3];
   int fm[3];
+  bool interior;  // no node of the cell lies on the domain boundary: no constraint to test
 
   __device__ __forceinline__ EtPoint(const Grid& g, const TabT<T>& tb, const int (&co)[3]) {
     int gq[3];
+    interior = true;
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       cell[d] = (d < DIM) ? co[d] >> 1 : 0;
       gq[d] = (d < DIM) ? (co[d] & 1) : 0;
+      if (d < DIM) interior = interior && cell[d] > 0 && cell[d] < g.n[d] - 1;
     }
 #pragma unroll
     for (int c = 0; c < DIM; ++c) {
@@ -154,7 +157,7 @@ struct EtPoint {
 #pragma unroll
           for (int ax = 0; ax < 3; ++ax) {
             const int ix = 2 * cell[0] + ax;
-            if (u_free_mask(fm[c], ix, iy, iz, nx, ny, nz)) s += f[c][0][ax] * __ldg(row + ix);
+            if (interior || u_free_mask(fm[c], ix, iy, iz, nx, ny, nz)) s += f[c][0][ax] * __ldg(row + ix);
           }
           acc += f[c][2][az] * f[c][1][ay] * s;
         }

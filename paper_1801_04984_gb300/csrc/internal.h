@@ -44,6 +44,12 @@ template <typename T>
 void launch_apply_p(const Grid& g, const TabT<T>& tb, const SlabCoef& sc, const T* x, int64_t sx, T* y, int64_t sy,
                     cudaStream_t st);
 void apply_init_attributes();
+// FP32 3-D elasticity rows, z-marching sum-factorised kernel (elast3.cu), used on grids of at
+// least ELAST3_MIN_NODES nodes per component (65^3 and finer)
+constexpr int64_t ELAST3_MIN_NODES = 100000;
+void elast3_init_attributes();
+void launch_elast3_f32(const Grid& g, const TabT<float>& tb, const SlabCoef& sc, int cols, const float* u, int64_t su, float* y,
+                       int64_t sy, cudaStream_t st, const UEpi<float>* epi);
 template <typename T>
 void launch_diag_A(const Grid& g, const TabT<T>& tb, double lam, double mu, T* d, cudaStream_t st);
 
@@ -53,6 +59,8 @@ void launch_diag_A(const Grid& g, const TabT<T>& tb, double lam, double mu, T* d
 constexpr int RED_BLOCKS = 608;  // 4 x 152 SMs
 constexpr int MAXDOT = 64;       // max vectors in one multi-dot
 
+// V: HOST array of nv device pointers, every vector 16-byte aligned (the pointers are passed
+// to the kernel by value, so a captured graph keeps them)
 template <typename TV>
 void launch_multidot(const TV* const* V, int nv, const TV* w, int64_t n, double* partial, double* out, cudaStream_t st);
 // w = w - sum_i V_i h_i  (h in device memory, double); optionally the dots
@@ -173,6 +181,14 @@ void launch_schur_stencil(const Grid& g, const TabT<T>& tb, const T* dmq, double
 template <typename T>
 void launch_schur_cheb_st(const Grid& g, const TabT<T>& tb, const T* coef, const T* dinv, const double* cm, double c1, double c2,
                           int first, const T* b, const T* x, T* d, T* xo, int nrhs, cudaStream_t st);
+// matrix-free form of the same step: per-flux-DoF weights tau wt^2 / Mq_ff (0 on no-flow DoFs,
+// instance-major like dmq) and one Chebyshev-Jacobi step for nk levels x nb instances
+// (columns level-major, stride Np; cm indexed by level) with the Jacobi diagonal formed on the fly
+template <typename T>
+void launch_schur_wq(const Grid& g, const TabT<T>& tb, const T* dmq, double tau, T* wq, cudaStream_t st);
+template <typename T>
+void launch_schur_cheb_mf(const Grid& g, const TabT<T>& tb, const T* wq, const double* cm, double c1, double c2, int first,
+                          const T* b, const T* x, T* d, T* xo, int nk, cudaStream_t st);
 // cell-centred multigrid for the lumped Schur complement (mg.cu): grid sizes of one level
 struct PDims {
   int n[3];

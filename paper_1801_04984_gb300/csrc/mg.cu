@@ -54,10 +54,7 @@ __global__ void k_prolong_add(Grid gf, Grid gc, const T* __restrict__ xc, int64_
   if (t >= gf.nnode) return;
   const int c = blockIdx.y % gf.dim, r = blockIdx.y / gf.dim;
   int f[3];
-  f[0] = (int)(t % gf.nu[0]);
-  int64_t rr = t / gf.nu[0];
-  f[1] = (int)(rr % gf.nu[1]);
-  f[2] = (int)(rr / gf.nu[1]);
+  unlex3(t, gf.nu[0], gf.nu[1], f[0], f[1], f[2]);
   if (!u_free(gf, c, f[0], f[1], f[2])) return;
   // the coarse correction is zero on constrained coarse nodes (identity rows with zero data)
   int ci[3][3], cnt[3];
@@ -84,10 +81,7 @@ __global__ void k_restrict(Grid gf, Grid gc, const T* __restrict__ rf, int64_t s
   if (t >= gc.nnode) return;
   const int c = blockIdx.y % gf.dim, r = blockIdx.y / gf.dim;
   int cidx[3];
-  cidx[0] = (int)(t % gc.nu[0]);
-  int64_t rr = t / gc.nu[0];
-  cidx[1] = (int)(rr % gc.nu[1]);
-  cidx[2] = (int)(rr / gc.nu[1]);
+  unlex3(t, gc.nu[0], gc.nu[1], cidx[0], cidx[1], cidx[2]);
   T acc = 0;
   // the fine residual is zero on constrained fine nodes (identity rows, x = b there)
   if (u_free(gc, c, cidx[0], cidx[1], cidx[2])) {
@@ -198,10 +192,7 @@ __device__ inline bool decode_q(const Grid& g, const T* wg, int64_t t, QIdx<T>& 
   while (r >= g.nq[c]) { r -= g.nq[c]; ++c; }
   int sh[3];
   for (int d = 0; d < 3; ++d) sh[d] = (d < DIM) ? ((d == c) ? g.nu[d] : g.ng[d]) : 1;
-  q.co[0] = (int)(r % sh[0]);
-  int64_t rr = r / sh[0];
-  q.co[1] = (int)(rr % sh[1]);
-  q.co[2] = (int)(rr / sh[1]);
+  unlex3(r, sh[0], sh[1], q.co[0], q.co[1], q.co[2]);
   q.c = c;
   q.r = r;
   q.ia = q.co[c];
@@ -236,10 +227,7 @@ __device__ inline T gather_BTp(const Grid& g, const TabT<T>& tb, const QIdx<T>& 
 template <typename T, int DIM>
 __device__ inline T gather_Bq(const Grid& g, const TabT<T>& tb, int64_t t, const T* q, const T* dscale) {
   int co[3];
-  co[0] = (int)(t % g.ng[0]);
-  int64_t rr = t / g.ng[0];
-  co[1] = (int)(rr % g.ng[1]);
-  co[2] = (int)(rr / g.ng[1]);
+  unlex3(t, g.ng[0], g.ng[1], co[0], co[1], co[2]);
   T acc = 0;
   for (int c = 0; c < DIM; ++c) {
     int sh[3];
@@ -292,10 +280,7 @@ __global__ void k_diag_BDBt(Grid g, TabT<T> tb, const T* __restrict__ dmq, T* __
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= g.Np) return;
   int co[3];
-  co[0] = (int)(t % g.ng[0]);
-  int64_t rr = t / g.ng[0];
-  co[1] = (int)(rr % g.ng[1]);
-  co[2] = (int)(rr / g.ng[1]);
+  unlex3(t, g.ng[0], g.ng[1], co[0], co[1], co[2]);
   double acc = 0;
   for (int c = 0; c < DIM; ++c) {
     int sh[3];
@@ -402,10 +387,9 @@ __global__ void __launch_bounds__(256) k_u_rhs(Grid g, TabT<T> tb, const T* __re
                                                int64_t sbu, int nrhs) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= g.nnode) return;
-  const int ix = (int)(t % g.nu[0]);
-  const int64_t rr = t / g.nu[0];
-  const int iy = (int)(rr % g.nu[1]);
-  const int iz = DIM == 3 ? (int)(rr / g.nu[1]) : 0;
+  int ix, iy, iz;
+  unlex3(t, g.nu[0], g.nu[1], ix, iy, iz);
+  if (DIM == 2) iz = 0;
   const EpNode<T, DIM> en(g, tb, ix, iy, iz);
   bool fr[DIM];
 #pragma unroll
@@ -492,10 +476,7 @@ __global__ void __launch_bounds__(256) k_p_plus_ETu(Grid g, TabT<T> tb, const T*
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= g.Np) return;
   int co[3];
-  co[0] = (int)(t % g.ng[0]);
-  const int64_t rr = t / g.ng[0];
-  co[1] = (int)(rr % g.ng[1]);
-  co[2] = (int)(rr / g.ng[1]);
+  unlex3(t, g.ng[0], g.ng[1], co[0], co[1], co[2]);
   const EtPoint<T, DIM> et(g, tb, co);
   for (int r = 0; r < nrhs; ++r) out[r * so + t] = rp[r * srp + t] + T(alpha) * et.eval(g, u + r * su);
 }
@@ -867,10 +848,7 @@ __global__ void k_schur_stencil(Grid g, TabT<T> tb, const T* __restrict__ dmq, d
   if (t >= g.Np) return;
   const int64_t np = g.Np;
   int co[3];
-  co[0] = (int)(t % g.ng[0]);
-  int64_t rr = t / g.ng[0];
-  co[1] = (int)(rr % g.ng[1]);
-  co[2] = (int)(rr / g.ng[1]);
+  unlex3(t, g.ng[0], g.ng[1], co[0], co[1], co[2]);
   double self = 0, part[3] = {0, 0, 0}, lo[3][2] = {{0, 0}, {0, 0}, {0, 0}}, hi[3][2] = {{0, 0}, {0, 0}, {0, 0}};
   for (int c = 0; c < DIM; ++c) {
     int sh[3];
@@ -964,6 +942,159 @@ __global__ void __launch_bounds__(256) k_schur_cheb_st(Grid g, const T* __restri
   if (c1 != T(0)) dn += c1 * d[i];
   d[i] = dn;
   xo[i] = xr[t] + dn;
+}
+
+// ---------------------------------------------------------------------------
+// Matrix-free form of the same lumped Schur complement.  Per flux DoF f one weight
+//   wq_f = tau wt_f^2 / (Mq)_ff   (0 on no-flow DoFs),
+// wt_f the transverse Gauss weight of f's line, so that
+//   (Shat x)_p = cm mp x_p + sum_f B_pf/wt_f wq_f (B^T x)_f / wt_f
+// with the 1-D divergence weights bd only.  A step then streams x, b, d and one flux-grid
+// weight array shared by every column of the launch (about 3 values per point) instead of
+// the 16 stencil coefficients per point and column, and forms the Jacobi diagonal
+// sum_f wq_f bd^2 + cm mp on the fly.
+template <typename T, int DIM>
+__global__ void k_schur_wq(Grid g, TabT<T> tb, const T* __restrict__ dmq, double tau, T* __restrict__ wq) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  QIdx<double> q;
+  double wg[3] = {(double)tb.wg[0], (double)tb.wg[1], (double)tb.wg[2]};
+  if (!decode_q<DIM>(g, wg, t, q)) return;
+  wq[t] = q_free(g, q.c, q.ia) ? (T)(tau * q.wt * q.wt / (double)dmq[t]) : T(0);
+}
+
+// One Chebyshev-Jacobi step on Shat for the nk temporal levels of one instance (grid y; column
+// of level k = k * nb + instance, stride Np).  One thread owns one cell and its 2^DIM Gauss
+// points: along each direction the cell holds 2^(DIM-1) lines of two points, and each line
+// couples through its three flux DoFs (lower face, mid, upper face) to the two points of the
+// neighbouring cells on the same line.  The cell's values and weights are loaded once for all
+// of its points.  All index arithmetic is 32-bit (one level of one instance has fewer than
+// 2^31 entries, checked at set-up).
+template <typename T, int DIM>
+__global__ void __launch_bounds__(256, 3) k_schur_cheb_mf(Grid g, TabT<T> tb, const T* __restrict__ wq, RhsCoef cm, T mp, T c1,
+                                                       T c2, int first, int nk, const T* __restrict__ b,
+                                                       const T* __restrict__ x, T* __restrict__ d, T* __restrict__ xo) {
+  constexpr int NP = 1 << DIM;        // points per cell
+  constexpr int NL = 1 << (DIM - 1);  // lines per cell and direction
+  const int cid = blockIdx.x * blockDim.x + threadIdx.x;
+  if (cid >= (int)g.ncells) return;
+  const int inst = blockIdx.y, nb = g.nb;
+  const int64_t np = g.Np;
+  wq += (int64_t)inst * (g.nq[0] + g.nq[1] + g.nq[2]);
+  int cx, cy, cz;
+  unlex3(cid, g.n[0], g.n[1], cx, cy, cz);
+  if (DIM == 2) cz = 0;
+  const int cc[3] = {cx, cy, cz};
+  const int pst[3] = {1, g.ng[0], g.ng[0] * g.ng[1]};
+  const int pbase = 2 * cx + pst[1] * 2 * cy + pst[2] * 2 * cz;  // the cell's first point
+  // point p of the cell (bits gx, gy, gz) at pbase + poff[p]
+  int poff[NP];
+#pragma unroll
+  for (int p = 0; p < NP; ++p) poff[p] = (p & 1) + ((p >> 1) & 1) * pst[1] + ((p >> 2) & 1) * pst[2];
+  // diagonal of the flux part per point
+  T self[NP];
+#pragma unroll
+  for (int p = 0; p < NP; ++p) self[p] = 0;
+  // flux-grid offset of line l of direction c at along-index 2 cc[c] (its lower face DoF), stride along c
+  int qline[DIM][NL], qstr[DIM];
+#pragma unroll
+  for (int c = 0; c < DIM; ++c) {
+    int mul = 1, stride_c = 1, base = (int)(g.offq[c] - g.Nu);
+#pragma unroll
+    for (int k2 = 0; k2 < DIM; ++k2) {
+      if (k2 == c) stride_c = mul;
+      mul *= (k2 == c) ? g.nu[k2] : g.ng[k2];
+    }
+    qstr[c] = stride_c;
+#pragma unroll
+    for (int l = 0; l < NL; ++l) {
+      // transverse Gauss-line coordinates of line l: the bits of l over the other directions
+      int off = base + 2 * cc[c] * stride_c, bit = 0, m2 = 1;
+#pragma unroll
+      for (int k2 = 0; k2 < DIM; ++k2) {
+        const int ext = (k2 == c) ? g.nu[k2] : g.ng[k2];
+        if (k2 != c) {
+          off += (2 * cc[k2] + ((l >> bit) & 1)) * m2;
+          ++bit;
+        }
+        m2 *= ext;
+      }
+      qline[c][l] = off;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const T wa = wq[off + a * stride_c];
+#pragma unroll
+        for (int gq = 0; gq < 2; ++gq) {
+          // point of line l with along-c bit gq
+          int p = 0, bb = 0;
+#pragma unroll
+          for (int k2 = 0; k2 < DIM; ++k2) {
+            const int bitv = (k2 == c) ? gq : ((l >> bb) & 1);
+            if (k2 != c) ++bb;
+            p |= bitv << k2;
+          }
+          self[p] += wa * tb.bd[c][a][gq] * tb.bd[c][a][gq];
+        }
+      }
+    }
+  }
+  // neighbour cells present below / above along each direction (bit c)
+  const int has_lo = (cx >= 1 ? 1 : 0) | (cy >= 1 ? 2 : 0) | (DIM == 3 && cz >= 1 ? 4 : 0);
+  const int has_hi = (cx + 1 < g.n[0] ? 1 : 0) | (cy + 1 < g.n[1] ? 2 : 0) | (DIM == 3 && cz + 1 < g.n[2] ? 4 : 0);
+  for (int k = 0; k < nk; ++k) {
+    const int64_t col = (int64_t)(k * nb + inst) * np;
+    const T mass = T(cm.c[k]) * mp;
+    const T* xr = x + col + pbase;
+    if (first) {
+#pragma unroll
+      for (int p = 0; p < NP; ++p) {
+        const int64_t i = col + pbase + poff[p];
+        const T dn = c2 / (mass + self[p]) * b[i];
+        d[i] = dn;
+        xo[i] = dn;
+      }
+      continue;
+    }
+    T xv[NP], acc[NP];
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+      xv[p] = xr[poff[p]];
+      acc[p] = mass * xv[p];
+    }
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) {
+#pragma unroll
+      for (int l = 0; l < NL; ++l) {
+        int p0 = 0, bb = 0;  // the line's point with along-c bit 0
+#pragma unroll
+        for (int k2 = 0; k2 < DIM; ++k2) {
+          const int bitv = (k2 == c) ? 0 : ((l >> bb) & 1);
+          if (k2 != c) ++bb;
+          p0 |= bitv << k2;
+        }
+        const int p1 = p0 | (1 << c);
+        const T x0 = xv[p0], x1 = xv[p1];
+        const T* xl = xr + poff[p0];
+        T s0 = tb.bd[c][0][0] * x0 + tb.bd[c][0][1] * x1;
+        const T s1 = tb.bd[c][1][0] * x0 + tb.bd[c][1][1] * x1;
+        T s2 = tb.bd[c][2][0] * x0 + tb.bd[c][2][1] * x1;
+        if ((has_lo >> c) & 1) s0 += tb.bd[c][2][0] * xl[-2 * pst[c]] + tb.bd[c][2][1] * xl[-pst[c]];
+        if ((has_hi >> c) & 1) s2 += tb.bd[c][0][0] * xl[2 * pst[c]] + tb.bd[c][0][1] * xl[3 * pst[c]];
+        const T w0 = wq[qline[c][l]], w1 = wq[qline[c][l] + qstr[c]], w2 = wq[qline[c][l] + 2 * qstr[c]];
+        const T t0 = w0 * s0, t1 = w1 * s1, t2 = w2 * s2;
+        acc[p0] += tb.bd[c][0][0] * t0 + tb.bd[c][1][0] * t1 + tb.bd[c][2][0] * t2;
+        acc[p1] += tb.bd[c][0][1] * t0 + tb.bd[c][1][1] * t1 + tb.bd[c][2][1] * t2;
+      }
+    }
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+      const int64_t i = col + pbase + poff[p];
+      const T dinv = T(1) / (mass + self[p]);
+      T dn = c2 * dinv * (b[i] - acc[p]);
+      if (c1 != T(0)) dn += c1 * d[i];
+      d[i] = dn;
+      xo[i] = xv[p] + dn;
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -1146,6 +1277,28 @@ void launch_schur_cheb_st(const Grid& g, const TabT<T>& tb, const T* coef, const
   else (note_launch(), k_schur_cheb_st<T, 2><<<grid, 256, 0, st>>>(g, coef, dinv, rc, T(mp), T(c1), T(c2), first, b, x, d, xo));
   if (sizeof(T) == 4) prof_end(st, 2);
 }
+template <typename T>
+void launch_schur_wq(const Grid& g, const TabT<T>& tb, const T* dmq, double tau, T* wq, cudaStream_t st) {
+  const int64_t n = g.nq[0] + g.nq[1] + g.nq[2];
+  const int blocks = (int)((n + 255) / 256);
+  if (g.dim == 3) (note_launch(), k_schur_wq<T, 3><<<blocks, 256, 0, st>>>(g, tb, dmq, tau, wq));
+  else (note_launch(), k_schur_wq<T, 2><<<blocks, 256, 0, st>>>(g, tb, dmq, tau, wq));
+}
+template <typename T>
+void launch_schur_cheb_mf(const Grid& g, const TabT<T>& tb, const T* wq, const double* cm, double c1, double c2, int first,
+                          const T* b, const T* x, T* d, T* xo, int nk, cudaStream_t st) {
+  RhsCoef rc;
+  for (int r = 0; r < MAXR; ++r) rc.c[r] = (r < nk) ? cm[r] : 0.0;
+  double mp = 1.0;
+  for (int k = 0; k < g.dim; ++k) mp *= (double)tb.wg[k];
+  dim3 grid((unsigned)((g.ncells + 255) / 256), g.nb);
+  if (sizeof(T) == 4) prof_begin(st, 2, (double)g.Np * nk * g.nb);
+  if (g.dim == 3)
+    (note_launch(), k_schur_cheb_mf<T, 3><<<grid, 256, 0, st>>>(g, tb, wq, rc, T(mp), T(c1), T(c2), first, nk, b, x, d, xo));
+  else
+    (note_launch(), k_schur_cheb_mf<T, 2><<<grid, 256, 0, st>>>(g, tb, wq, rc, T(mp), T(c1), T(c2), first, nk, b, x, d, xo));
+  if (sizeof(T) == 4) prof_end(st, 2);
+}
 PDims pdims_points(const Grid& g) {
   PDims p;
   for (int d = 0; d < 3; ++d) p.n[d] = g.ng[d];
@@ -1222,6 +1375,9 @@ void launch_pmg_prolong(int dim, const PDims& fd, const PDims& cd, const T* xc, 
   template void launch_schur_stencil<T>(const Grid&, const TabT<T>&, const T*, double, T*, cudaStream_t);          \
   template void launch_schur_cheb_st<T>(const Grid&, const TabT<T>&, const T*, const T*, const double*, double, double, \
                                         int, const T*, const T*, T*, T*, int, cudaStream_t);                        \
+  template void launch_schur_wq<T>(const Grid&, const TabT<T>&, const T*, double, T*, cudaStream_t);                \
+  template void launch_schur_cheb_mf<T>(const Grid&, const TabT<T>&, const T*, const double*, double, double, int,   \
+                                        const T*, const T*, T*, T*, int, cudaStream_t);                              \
   template void launch_mq_line_solve<T>(const Grid&, const TabT<T>&, const T*, const T*, int64_t, T*, int64_t, double, int, \
                                         cudaStream_t);                                                              \
   template void launch_BTp<T>(const Grid&, const TabT<T>&, const T*, int64_t, const T*, int64_t, T*, int64_t, double, \

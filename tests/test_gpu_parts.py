@@ -128,3 +128,33 @@ def test_fma_peak_is_measured_and_plausible():
     assert 0.05 < f64 < f32, f64
     assert ms32 > 10.0 and ms64 > 10.0
     print("FMA peak: FP32 %.1f TFLOP/s, FP64 %.2f TFLOP/s" % (f32, f64))
+
+
+@pytest.mark.parametrize("n,bcs", CASES)
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_schur_chebyshev_step_kernel(n, bcs, prec):
+    """The matrix-free flux-pressure step the solver runs (weights per flux DoF, Jacobi
+    diagonal formed on the fly): out = x - diag(Shat)^{-1} Shat x against the oracle's
+    assembled lumped Schur complement Shat = (1/M + beta) Mp + tau B_f diag(Mq_ff)^{-1} B_f^T."""
+    from paper_1801_04984_gb300 import binding as B
+    rng = np.random.default_rng(29)
+    K = 1e-2 * np.exp(rng.normal(0, 1.5, size=int(np.prod(n))))
+    ctx = _ctx(n, bcs, K, exact=0)
+    m = Mesh(n)
+    blk = SpatialBlocks(m, dict(C2, K=K))
+    fq = constraint_mask(m, *bcs)[m.Nu:m.off_p] == 1.0
+    Mq = blk.Mq.tocsr()[fq][:, fq]
+    Bf = blk.B.tocsr()[:, fq]
+    beta = C2["b"] ** 2 / C2["K_dr"]
+    tau = 0.07
+    S = ((C2["invM"] + beta) * blk.Mp + tau * (Bf @ sp.diags(1.0 / Mq.diagonal()) @ Bf.T)).tocsr()
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    x = rng.normal(size=m.N)
+    xd = torch.tensor(x, device="cuda", dtype=dt)
+    yd = torch.full_like(xd, float("nan"))
+    ctx.apply_part(B.PART_SCHUR_STEP, tau, xd, yd)
+    p = xd.double().cpu().numpy()[m.off_p:]
+    ref = p - (S @ p) / S.diagonal()
+    got = yd.double().cpu().numpy()[m.off_p:]
+    tol = 1e-12 if prec == "fp64" else 2e-6
+    assert np.abs(got - ref).max() < tol * np.abs(ref).max(), np.abs(got - ref).max() / np.abs(ref).max()
