@@ -22,8 +22,10 @@
  *        S   = [[0, 0, 0], [0, 0, 0], [b E^T, 0, (1/M) Mp]];
  *   solver (paper §Monolithic Approach, §Preconditioning technology):
  *   restarted flexible GMRES, right-preconditioned by the time-spectral
- *   decomposition of M_t^{-1} D with the complex-pair couplings dropped
- *   ("diagonal blockwise L_j") and a block-triangular fixed-stress
+ *   decomposition of M_t^{-1} D (real block form; the +-beta S couplings of a
+ *   complex eigenvalue pair are kept through one block Gauss-Seidel sweep by
+ *   default, or dropped as in the paper's "diagonal blockwise L_j" with
+ *   opts.pair_coupling = -1) and a block-triangular fixed-stress
  *   preconditioner per block: flux-pressure block first with the
  *   displacement coupling replaced by (b^2/K_dr) Mp, then the displacement
  *   block by a geometric-multigrid V-cycle with Chebyshev-Jacobi smoothing.
@@ -178,6 +180,12 @@ int biot_sizes(biot_t ctx, int64_t* n_space, int64_t* n_slab, int64_t* n_cells);
 
 /* Replace the cellwise permeability (HOST array, n_cells, > 0). */
 int biot_set_permeability(biot_t ctx, const double* K_cell);
+
+/* Replace the cellwise permeability by its log-parametrisation K_c = K0 exp(g_c) (paper
+ * §Poroelasticity: Darcy's law with the permeability K; the log field g is the variable of
+ * biot_adjoint_grad's gradient).  g: HOST array, n_cells; EINVAL for K0 <= 0 or any
+ * non-finite K_c. */
+int biot_set_log_permeability(biot_t ctx, const double* g, double K0);
 
 /* y = calA x (transpose = 0) or calA^T x (transpose = 1) for one slab of
  * length tau > 0 (paper §Monolithic Approach block system, applied matrix-free

@@ -88,6 +88,7 @@ def load(path: str = LIB_PATH):
         "biot_sizes": (C.c_int, [vp, i64p, i64p, i64p]),
         "biot_time_tables": (C.c_int, [C.c_int, dp, dp, dp, dp, dp, dp, dp, ip, dp]),
         "biot_set_permeability": (C.c_int, [vp, dp]),
+        "biot_set_log_permeability": (C.c_int, [vp, dp, C.c_double]),
         "biot_apply_slab": (C.c_int, [vp, C.c_double, vp, vp, C.c_int, C.c_int, vp]),
         "biot_precondition": (C.c_int, [vp, C.c_double, vp, vp, C.c_int, C.c_int, vp]),
         "biot_solve_slab": (C.c_int, [vp, C.c_double, vp, vp, C.POINTER(SolveOpts), C.POINTER(Stats), vp]),
@@ -212,6 +213,13 @@ class Context:
         self.K = np.ascontiguousarray(np.asarray(K, dtype=np.float64))
         assert self.K.size == self.n_cells
         return self._check(self.lib.biot_set_permeability(self.h, self.K.ctypes.data_as(C.POINTER(C.c_double))))
+
+    def set_log_permeability(self, g, K0):
+        """K = K0 exp(g) per cell, formed by the library (biot_set_log_permeability)."""
+        g = np.ascontiguousarray(np.asarray(g, dtype=np.float64))
+        assert g.size == self.n_cells * self.nb
+        rc = self._check(self.lib.biot_set_log_permeability(self.h, g.ctypes.data_as(C.POINTER(C.c_double)), float(K0)))
+        return rc
 
     def apply_slab(self, tau, x, y, transpose=False):
         import torch
@@ -421,8 +429,8 @@ def _goal_function_class():
 
         @staticmethod
         def forward(fctx, g, context, K0, T, slabs, f_terms, tcoef, U0, j_goal, tol, mode):
-            gh = g.detach().to("cpu", torch.float64).numpy()
-            context.set_permeability(np.asarray(K0, dtype=np.float64) * np.exp(gh))
+            gh = np.ascontiguousarray(g.detach().to("cpu", torch.float64).numpy())
+            context.set_log_permeability(gh, K0)
             dJ = torch.zeros(context.n_cells, dtype=torch.float64, device=j_goal.device)
             J = context.adjoint_grad(T, slabs, f_terms, tcoef, U0, j_goal, dJ, tol=tol, mode=mode)
             fctx.save_for_backward(dJ)

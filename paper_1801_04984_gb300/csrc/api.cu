@@ -2128,6 +2128,18 @@ extern "C" int biot_set_permeability(biot_t c, const double* K) {
   API_END(c)
 }
 
+extern "C" int biot_set_log_permeability(biot_t c, const double* g, double K0) {
+  API_BEGIN(c)
+  if (!g) fail(BIOT_EINVAL, "log-permeability is NULL");
+  if (!(K0 > 0) || !std::isfinite(K0)) fail(BIOT_EINVAL, "K0 must be positive and finite");
+  const int64_t nc = c->g.ncells * c->nb;
+  std::vector<double> K(nc);
+  for (int64_t i = 0; i < nc; ++i) K[i] = K0 * std::exp(g[i]);  // non-finite results are rejected below
+  set_permeability(*c, K.data(), 0);
+  return BIOT_OK;
+  API_END(c)
+}
+
 extern "C" int biot_apply_slab(biot_t c, double tau, const void* x, void* y, int prec, int transpose, void* stream) {
   API_BEGIN(c)
   if (!x || !y || !(tau > 0)) fail(BIOT_EINVAL, "apply_slab: NULL vector or tau <= 0");

@@ -592,54 +592,7 @@ __global__ void __launch_bounds__(128) k_apply_p_cell(Grid g, TabT<T> tb, SlabCo
     const T* xl = x + (int64_t)(l * nb + bi) * sx;
     // ---- E^T u at the cell's points
     T eu[NP];
-#pragma unroll
-    for (int p = 0; p < NP; ++p) eu[p] = T(0);
-#pragma unroll
-    for (int c = 0; c < DIM; ++c) {
-      // 1-D factors of component c: derivative along c, value across
-      T fx[3][2], fy[3][2], fz[3][2];
-#pragma unroll
-      for (int a = 0; a < 3; ++a)
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-          fx[a][q] = (c == 0) ? tb.bd[0][a][q] : tb.bv[0][a][q];
-          fy[a][q] = (c == 1) ? tb.bd[1][a][q] : tb.bv[1][a][q];
-          fz[a][q] = (DIM == 3) ? ((c == 2) ? tb.bd[2][a][q] : tb.bv[2][a][q]) : T(a == 0 ? 1 : 0);
-        }
-      const T* uc = xl + c * g.nnode;
-      T t2[NA][2][2];  // [az][gy][gx]
-#pragma unroll
-      for (int az = 0; az < NA; ++az)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) t2[az][q >> 1][q & 1] = T(0);
-#pragma unroll
-      for (int az = 0; az < NA; ++az) {
-        const int iz = 2 * cz + az;
-#pragma unroll
-        for (int ay = 0; ay < 3; ++ay) {
-          const int iy = 2 * cy + ay;
-          const T* row = uc + ((int64_t)iz * ny + iy) * nx + 2 * cx;
-          T v[3];
-#pragma unroll
-          for (int ax = 0; ax < 3; ++ax)
-            v[ax] = (interior || u_free_mask(fm[c], 2 * cx + ax, iy, iz, nx, ny, nz)) ? __ldg(row + ax) : T(0);
-#pragma unroll
-          for (int gx = 0; gx < 2; ++gx) {
-            const T t1 = fx[0][gx] * v[0] + fx[1][gx] * v[1] + fx[2][gx] * v[2];
-#pragma unroll
-            for (int gy = 0; gy < 2; ++gy) t2[az][gy][gx] += fy[ay][gy] * t1;
-          }
-        }
-      }
-#pragma unroll
-      for (int p = 0; p < NP; ++p) {
-        const int gx = p & 1, gy = (p >> 1) & 1, gz = (p >> 2) & 1;
-        T a = 0;
-#pragma unroll
-        for (int az = 0; az < NA; ++az) a += fz[az][gz] * t2[az][gy][gx];
-        eu[p] += a;
-      }
-    }
+    cell_ETu<T, DIM>(g, tb, xl, cx, cy, cz, interior, fm, eu);
     // ---- B q at the cell's points
     T bq[NP];
 #pragma unroll

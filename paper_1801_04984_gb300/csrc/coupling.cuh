@@ -60,12 +60,16 @@ template <typename T, int DIM>
 struct EpNode {
   int ox[4], oy[4], oz[4];  // clamped pressure-grid coordinates of the window slots
   T vx[4], dx[4], vy[4], dy[4], vz[4], dz[4];
+  int nsy, nsz;             // slots with nonzero weights along y and z: 2 unless a vertex between two cells
 
   __device__ __forceinline__ EpNode(const Grid& g, const TabT<T>& tb, int ix, int iy, int iz) {
     int sx, sy, sz = 0;
     ep_window<T>(tb, 0, ix, g.n[0], sx, vx, dx);
     ep_window<T>(tb, 1, iy, g.n[1], sy, vy, dy);
     if (DIM == 3) ep_window<T>(tb, 2, iz, g.n[2], sz, vz, dz);
+    // (neighbouring threads share y and z, so these bounds are uniform across most warps)
+    nsy = ((iy & 1) || iy == 0 || iy == 2 * g.n[1]) ? 2 : 4;
+    nsz = DIM == 3 ? (((iz & 1) || iz == 0 || iz == 2 * g.n[2]) ? 2 : 4) : 1;
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
       ox[e] = min(sx + e, g.ng[0] - 1);
@@ -80,9 +84,11 @@ struct EpNode {
     T a0 = 0, a1 = 0, a2 = 0;
 #pragma unroll
     for (int c2 = 0; c2 < NZ; ++c2) {
+      if (c2 >= nsz) break;
       T b0 = 0, b1 = 0, b2 = 0;  // y-contracted partial sums
 #pragma unroll
       for (int c1 = 0; c1 < 4; ++c1) {
+        if (c1 >= nsy) break;
         const T* row = p + ((int64_t)oz[c2] * g.ng[1] + oy[c1]) * g.ng[0];
         T sv = 0, sd = 0;
 #pragma unroll
@@ -165,5 +171,66 @@ struct EtPoint {
     return acc;
   }
 };
+
+// E^T u at the 2^DIM Gauss points of cell (cx, cy, cz) from the cell's 3^DIM nodes per
+// component, sum-factorised (x, then y, then z contraction); u = one displacement level
+// [u_0|u_1|u_2] (stride nnode); constrained displacement entries count as zero (`interior`:
+// no node of the cell is on the domain boundary, nothing to test; fm: face masks per component).
+// eu[p], p = gx + 2 gy + 4 gz.
+template <typename T, int DIM>
+__device__ __forceinline__ void cell_ETu(const Grid& g, const TabT<T>& tb, const T* __restrict__ u, int cx, int cy, int cz,
+                                         bool interior, const int (&fm)[DIM], T (&eu)[1 << DIM]) {
+  constexpr int NP = 1 << DIM;
+  constexpr int NA = DIM == 3 ? 3 : 1;
+  const int nx = g.nu[0], ny = g.nu[1], nz = g.nu[2];
+#pragma unroll
+  for (int p = 0; p < NP; ++p) eu[p] = T(0);
+#pragma unroll
+  for (int c = 0; c < DIM; ++c) {
+    // 1-D factors of component c: derivative along c, value across
+    T fx[3][2], fy[3][2], fz[3][2];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        fx[a][q] = (c == 0) ? tb.bd[0][a][q] : tb.bv[0][a][q];
+        fy[a][q] = (c == 1) ? tb.bd[1][a][q] : tb.bv[1][a][q];
+        fz[a][q] = (DIM == 3) ? ((c == 2) ? tb.bd[2][a][q] : tb.bv[2][a][q]) : T(a == 0 ? 1 : 0);
+      }
+    const T* uc = u + c * g.nnode;
+    T t2[NA][2][2];  // [az][gy][gx]
+#pragma unroll
+    for (int az = 0; az < NA; ++az)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) t2[az][q >> 1][q & 1] = T(0);
+#pragma unroll
+    for (int az = 0; az < NA; ++az) {
+      const int iz = 2 * cz + az;
+#pragma unroll
+      for (int ay = 0; ay < 3; ++ay) {
+        const int iy = 2 * cy + ay;
+        const T* row = uc + ((int64_t)iz * ny + iy) * nx + 2 * cx;
+        T v[3];
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax)
+          v[ax] = (interior || u_free_mask(fm[c], 2 * cx + ax, iy, iz, nx, ny, nz)) ? __ldg(row + ax) : T(0);
+#pragma unroll
+        for (int gx = 0; gx < 2; ++gx) {
+          const T t1 = fx[0][gx] * v[0] + fx[1][gx] * v[1] + fx[2][gx] * v[2];
+#pragma unroll
+          for (int gy = 0; gy < 2; ++gy) t2[az][gy][gx] += fy[ay][gy] * t1;
+        }
+      }
+    }
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+      const int gx = p & 1, gy = (p >> 1) & 1, gz = (p >> 2) & 1;
+      T a2 = 0;
+#pragma unroll
+      for (int az = 0; az < NA; ++az) a2 += fz[az][gz] * t2[az][gy][gx];
+      eu[p] += a2;
+    }
+  }
+}
 
 }  // namespace biot

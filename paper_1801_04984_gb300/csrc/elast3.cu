@@ -27,6 +27,8 @@
 // constrained rows are read as zero; constrained output rows return the input.  Every
 // output is computed by one thread: no atomics, bitwise reproducible.
 #include <algorithm>
+#include <cstring>
+#include <vector>
 
 #include "internal.h"
 
@@ -66,8 +68,15 @@ __host__ __device__ constexpr float tap_hi(int op) { return op == 0 ? 4.f : (op 
 
 // scaled taps of the y pass (per term) and of the x pass (per operator); dlo / dhi are the
 // boundary-row centre-tap differences (boundary minus interior)
+// One y-pass term in the order the warps run them: source z-pass array, destination pre-x
+// slot, whether the accumulator is stored (and restarted) after it, and its scaled taps.
+struct YEnt {
+  int src, slot, flush, pad;
+  float v[5], m[3], dlo, dhi;
+};
 struct ElastTaps {
-  float yv[21][5], ym[21][3], ydlo[21], ydhi[21];
+  YEnt ye[21];
+  int wbeg[13];  // warp w runs terms wbeg[w] .. wbeg[w+1]-1 (at most two)
   float xv[4][5], xm[4][3], xdlo[4], xdhi[4];
 };
 
@@ -110,80 +119,57 @@ __device__ __forceinline__ void zpass(const float (&w)[5], float (&o)[4], int bn
   }
 }
 
-// y pass of the terms of pre-x array Q with rank T0 <= rank < T1 among Q's terms (compile
-// time), for halo column hx: a y line of TY outputs written to pre-x slot S.  ylo / yhi >= 0:
-// tile output row that is the lower / upper domain boundary.
-template <int Q, int T0, int T1, int S>
-__device__ __forceinline__ void ypass(const ElastTaps& tp, const float* __restrict__ zp, float* __restrict__ px, int hx, int ylo,
-                                      int yhi) {
+// pre-x slots: array Q in slot Q; the 4-term arrays 4 and 8 are split into two partial slots
+// (4, 12) and (8, 13) so that no warp of the y pass carries more than two terms
+constexpr int NSLOT = 14;
+
+// y pass of one warp, lane = halo column hx: the warp's terms from the table (the same code for
+// every warp keeps the kernel small for the instruction cache; the table index is warp-uniform),
+// a y line of TY outputs per term, accumulated per destination slot.  ylo / yhi >= 0: tile
+// output row that is the lower / upper domain boundary.
+__device__ __forceinline__ void ypass_warp(int warp, const ElastTaps& tp, const float* __restrict__ zp, float* __restrict__ px, int hx,
+                                           int ylo, int yhi) {
+  const int e0 = tp.wbeg[warp], e1 = tp.wbeg[warp + 1];
   float acc[TY];
 #pragma unroll
   for (int o = 0; o < TY; ++o) acc[o] = 0.f;
-  int rank = 0;
-#pragma unroll
-  for (int t = 0; t < 21; ++t) {
-    if (term(t).i * 4 + term(t).xop != Q) continue;
-    const int rk = rank++;
-    if (rk < T0 || rk >= T1) continue;
-    const float* src = zp + (term(t).j * 4 + term(t).zop) * (HY * HX) + hx;
+  for (int e = e0; e < e1; ++e) {
+    const YEnt& t = tp.ye[e];
+    const float* src = zp + t.src * (HY * HX) + hx;
     float w[HY];
 #pragma unroll
     for (int y = 0; y < HY; ++y) w[y] = src[y * HX];
+    const float v0 = t.v[0], v1 = t.v[1], v2 = t.v[2], v3 = t.v[3], v4 = t.v[4];
+    const float m0 = t.m[0], m1 = t.m[1], m2 = t.m[2];
 #pragma unroll
     for (int o = 0; o < TY; ++o) {
       if ((o & 1) == 0) {
-        acc[o] = fmaf(tp.yv[t][0], w[o], acc[o]);
-        acc[o] = fmaf(tp.yv[t][1], w[o + 1], acc[o]);
-        acc[o] = fmaf(tp.yv[t][2], w[o + 2], acc[o]);
-        acc[o] = fmaf(tp.yv[t][3], w[o + 3], acc[o]);
-        acc[o] = fmaf(tp.yv[t][4], w[o + 4], acc[o]);
+        acc[o] = fmaf(v0, w[o], acc[o]);
+        acc[o] = fmaf(v1, w[o + 1], acc[o]);
+        acc[o] = fmaf(v2, w[o + 2], acc[o]);
+        acc[o] = fmaf(v3, w[o + 3], acc[o]);
+        acc[o] = fmaf(v4, w[o + 4], acc[o]);
       } else {
-        acc[o] = fmaf(tp.ym[t][0], w[o + 1], acc[o]);
-        acc[o] = fmaf(tp.ym[t][1], w[o + 2], acc[o]);
-        acc[o] = fmaf(tp.ym[t][2], w[o + 3], acc[o]);
+        acc[o] = fmaf(m0, w[o + 1], acc[o]);
+        acc[o] = fmaf(m1, w[o + 2], acc[o]);
+        acc[o] = fmaf(m2, w[o + 3], acc[o]);
       }
     }
     if (ylo >= 0 || yhi >= 0) {
 #pragma unroll
       for (int o = 0; o < TY; o += 2) {
-        if (o == ylo) acc[o] = fmaf(tp.ydlo[t], w[o + 2], acc[o]);
-        if (o == yhi) acc[o] = fmaf(tp.ydhi[t], w[o + 2], acc[o]);
+        if (o == ylo) acc[o] = fmaf(t.dlo, w[o + 2], acc[o]);
+        if (o == yhi) acc[o] = fmaf(t.dhi, w[o + 2], acc[o]);
       }
     }
-  }
-  float* dst = px + S * (TY * HX) + hx;
+    if (t.flush) {
+      float* dst = px + t.slot * (TY * HX) + hx;
 #pragma unroll
-  for (int o = 0; o < TY; ++o) dst[o * HX] = acc[o];
-}
-
-// pre-x slots: array Q in slot Q; the 4-term arrays 4 and 8 are split into two partial slots
-// (4, 12) and (8, 13) so that no warp of the y pass carries more than two terms
-constexpr int NSLOT = 14;
-
-// y pass of one warp: 11 warps carry the 21 terms (at most two each), warp 11 has none
-__device__ __forceinline__ void ypass_warp(int warp, const ElastTaps& tp, const float* zp, float* px, int hx, int ylo, int yhi) {
-  switch (warp) {
-    case 0: ypass<0, 0, 4, 0>(tp, zp, px, hx, ylo, yhi); break;
-    case 1: ypass<2, 0, 4, 2>(tp, zp, px, hx, ylo, yhi); break;
-    case 2: ypass<3, 0, 4, 3>(tp, zp, px, hx, ylo, yhi); break;
-    case 3: ypass<4, 0, 2, 4>(tp, zp, px, hx, ylo, yhi); break;
-    case 4: ypass<4, 2, 4, 12>(tp, zp, px, hx, ylo, yhi); break;
-    case 5: ypass<8, 0, 2, 8>(tp, zp, px, hx, ylo, yhi); break;
-    case 6: ypass<8, 2, 4, 13>(tp, zp, px, hx, ylo, yhi); break;
-    case 7:
-      ypass<1, 0, 4, 1>(tp, zp, px, hx, ylo, yhi);
-      ypass<5, 0, 4, 5>(tp, zp, px, hx, ylo, yhi);
-      break;
-    case 8:
-      ypass<6, 0, 4, 6>(tp, zp, px, hx, ylo, yhi);
-      ypass<7, 0, 4, 7>(tp, zp, px, hx, ylo, yhi);
-      break;
-    case 9:
-      ypass<9, 0, 4, 9>(tp, zp, px, hx, ylo, yhi);
-      ypass<10, 0, 4, 10>(tp, zp, px, hx, ylo, yhi);
-      break;
-    case 10: ypass<11, 0, 4, 11>(tp, zp, px, hx, ylo, yhi); break;
-    default: break;
+      for (int o = 0; o < TY; ++o) {
+        dst[o * HX] = acc[o];
+        acc[o] = 0.f;
+      }
+    }
   }
 }
 
@@ -263,46 +249,52 @@ __global__ void __launch_bounds__(NTH, 2) k_elast3_zm(const __grid_constant__ El
     if (xb >= 0 && xb < XSEG) { xhi_here = true; xhi_o = xb; }
   }
 
-  // ---- output-stage items of this thread (plane independent): in-plane offset and the
-  // x / y face flags of each, -1 for outputs outside the domain
-  int oin[OUT_PER_T], oso[OUT_PER_T], ocomp[OUT_PER_T];
-  unsigned oxyfree = 0;
+  // ---- output-stage items of this thread (plane independent): in-plane offset (-1 outside the
+  // domain) and a meta word: smem slot (bits 0-9), component (10-11), free on the x / y faces
+  // (12), constrained on the lower / upper z face (13, 14)
+  int oin[OUT_PER_T], ometa[OUT_PER_T];
 #pragma unroll
   for (int q = 0; q < OUT_PER_T; ++q) {
     const int it = tid - OUT_T0 + q * NOUT_T;
     oin[q] = -1;
-    oso[q] = 0;
-    ocomp[q] = 0;
+    ometa[q] = 0;
     if (tid >= OUT_T0 && it < NOUT) {
       const int i = it / (TY * TX), rem = it - i * (TY * TX);
       const int yy = rem / TX, xx = rem - yy * TX;
       const int ox = X0 + xx, oy = Y0 + yy;
       if (ox < nx && oy < ny) {
+        const int m = i == 0 ? a.fm[0] : (i == 1 ? a.fm[1] : a.fm[2]);
         oin[q] = oy * nx + ox;
-        oso[q] = it;
-        ocomp[q] = i;
-        if (face_free(a.fm[i] & 15, ox, oy, 1, nx, ny, 3)) oxyfree |= 1u << q;
+        ometa[q] = it | (i << 10) | (face_free(m & 15, ox, oy, 1, nx, ny, 3) ? 1 << 12 : 0) | (((m >> 4) & 1) << 13) |
+                   (((m >> 5) & 1) << 14);
       }
     }
   }
+  const int64_t coff[3] = {0, nn, 2 * nn};
+  auto item_cn = [&](int q, int64_t planeoff) {
+    const int i = (ometa[q] >> 10) & 3;
+    return (i == 0 ? coff[0] : (i == 1 ? coff[1] : coff[2])) + planeoff + oin[q];
+  };
   auto prefetch_stage = [&](int izo) {
     if (EPI::NPF == 0) return;
+    const int64_t planeoff = (int64_t)izo * pstride;
 #pragma unroll
     for (int q = 0; q < OUT_PER_T; ++q) {
       if (oin[q] < 0) continue;
-      ep.prefetch(eb, oso[q], ko, ocomp[q] * nn + izo * pstride + oin[q], u);
+      ep.prefetch(eb, ometa[q] & 1023, ko, item_cn(q, planeoff), u);
     }
     cp_async_commit();
   };
   auto output_stage = [&](int izo, const float* sob) {
     if (EPI::NPF > 0) cp_async_wait_all();
+    const int64_t planeoff = (int64_t)izo * pstride;
+    const bool zlo_plane = izo == 0, zhi_plane = izo == nz - 1;
 #pragma unroll
     for (int q = 0; q < OUT_PER_T; ++q) {
       if (oin[q] < 0) continue;
-      const int i = ocomp[q];
-      const bool fr = ((oxyfree >> q) & 1) && !(((a.fm[i] >> 4) & 1) && izo == 0) && !(((a.fm[i] >> 5) & 1) && izo == nz - 1);
-      const int64_t cn = i * nn + izo * pstride + oin[q];
-      ep.store(y, ko, cn, fr, sob[oso[q]], u, eb, oso[q]);
+      const int mt = ometa[q], it = mt & 1023;
+      const bool fr = ((mt >> 12) & 1) && !(((mt >> 13) & 1) && zlo_plane) && !(((mt >> 14) & 1) && zhi_plane);
+      ep.store(y, ko, item_cn(q, planeoff), fr, sob[it], u, eb, it);
     }
   };
 
@@ -451,15 +443,39 @@ constexpr size_t elast3_smem_bytes() {
 
 ElastTaps make_taps(const TabT<float>& tb, double lam, double mu) {
   ElastTaps t;
+  std::memset(&t, 0, sizeof(t));
   const double cf[3] = {2.0 * mu + lam, mu, lam};
-  for (int q = 0; q < 21; ++q) {
-    const Term3z tm = term(q);
-    const double s = cf[tm.coef] * (double)tb.opscale[2][tm.zop] * (double)tb.opscale[1][tm.yop];
-    for (int k = 0; k < 5; ++k) t.yv[q][k] = (float)(s * tap_v(tm.yop, k));
-    for (int k = 0; k < 3; ++k) t.ym[q][k] = (float)(s * tap_m(tm.yop, k));
-    t.ydlo[q] = (float)(s * (tap_lo(tm.yop) - tap_v(tm.yop, 2)));
-    t.ydhi[q] = (float)(s * (tap_hi(tm.yop) - tap_v(tm.yop, 2)));
+  // warps of the y pass: (pre-x array Q, first and last rank of its terms, slot) runs; every
+  // warp carries at most two terms (warp 11 none)
+  struct Run { int Q, r0, r1, slot; };
+  const std::vector<std::vector<Run>> plan = {
+      {{0, 0, 4, 0}}, {{2, 0, 4, 2}}, {{3, 0, 4, 3}}, {{4, 0, 2, 4}}, {{4, 2, 4, 12}}, {{8, 0, 2, 8}}, {{8, 2, 4, 13}},
+      {{1, 0, 4, 1}, {5, 0, 4, 5}}, {{6, 0, 4, 6}, {7, 0, 4, 7}}, {{9, 0, 4, 9}, {10, 0, 4, 10}}, {{11, 0, 4, 11}}, {}};
+  int ne = 0;
+  for (int w = 0; w < 12; ++w) {
+    t.wbeg[w] = ne;
+    for (const Run& run : plan[w]) {
+      int rank = 0;
+      const int first = ne;
+      for (int q = 0; q < 21; ++q) {
+        const Term3z tm = term(q);
+        if (tm.i * 4 + tm.xop != run.Q) continue;
+        const int rk = rank++;
+        if (rk < run.r0 || rk >= run.r1) continue;
+        YEnt& e = t.ye[ne++];
+        const double sc = cf[tm.coef] * (double)tb.opscale[2][tm.zop] * (double)tb.opscale[1][tm.yop];
+        e.src = tm.j * 4 + tm.zop;
+        e.slot = run.slot;
+        e.flush = 0;
+        for (int k = 0; k < 5; ++k) e.v[k] = (float)(sc * tap_v(tm.yop, k));
+        for (int k = 0; k < 3; ++k) e.m[k] = (float)(sc * tap_m(tm.yop, k));
+        e.dlo = (float)(sc * (tap_lo(tm.yop) - tap_v(tm.yop, 2)));
+        e.dhi = (float)(sc * (tap_hi(tm.yop) - tap_v(tm.yop, 2)));
+      }
+      if (ne > first) t.ye[ne - 1].flush = 1;  // the run's last term stores its slot
+    }
   }
+  t.wbeg[12] = ne;
   for (int op = 0; op < 4; ++op) {
     const double s = (double)tb.opscale[0][op];
     for (int k = 0; k < 5; ++k) t.xv[op][k] = (float)(s * tap_v(op, k));

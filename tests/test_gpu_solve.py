@@ -119,7 +119,7 @@ def test_autograd_goal_gradient_is_the_adjoint_gradient():
     J = B.goal_of_logk(ctx, g, 1e-2, 1.0, slabs, [f], [[1, 0, 0, 0]], U0, j, tol=1e-13)
     J.backward()
     dJ = torch.zeros(ctx.n_cells, dtype=torch.float64, device="cuda")
-    ctx.set_permeability(1e-2 * np.exp(g0))
+    ctx.set_log_permeability(g0, 1e-2)  # the parametrisation the autograd path uses
     J_ref = ctx.adjoint_grad(1.0, slabs, [f], [[1, 0, 0, 0]], U0, j, dJ, tol=1e-13)
     assert J.item() == J_ref and torch.equal(g.grad, dJ)
     U = torch.zeros_like(f)
