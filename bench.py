@@ -202,7 +202,7 @@ def run_batch(args):
     for it in range(args.warmup + args.steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        rc, status, stats = B.solve_batch(inst, workers=args.workers, tol=1e-8, mode=B.MIXED,
+        rc, status, stats = B.solve_batch(inst, workers=args.workers, tol=args.batch_tol, mode=B.MIXED,
                                           opts=dict(schur_mg=args.schur_mg) if args.schur_mg else None)
         torch.cuda.synchronize()
         if it >= args.warmup:
@@ -210,15 +210,25 @@ def run_batch(args):
         assert rc == 0, (rc, [s for s in status if s])
     t = float(np.mean(times))
     iters = [s["iterations"] for s in stats]
+    # relative error of the mixed end states against FP64 marches (relative residual 1e-12) on
+    # a seeded sample of 8 instances, one per 32 (every (n, r) mix is represented)
+    errs = []
+    for i in range(0, len(inst), max(1, len(inst) // 8)):
+        ref = dict(inst[i], U_end=np.zeros_like(inst[i]["U_end"]))
+        rc_ref, _, _ = B.solve_batch([ref], workers=1, tol=1e-12, mode=B.FP64, max_iters=20000)
+        assert rc_ref == 0, rc_ref
+        errs.append(float(np.linalg.norm(inst[i]["U_end"] - ref["U_end"]) / np.linalg.norm(ref["U_end"])))
     line = {"metric": METRIC + " (batching workload)", "value": dofs / t, "unit": "DoF/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": "%d independent 2-D Biot instances, n in {16,32,64,128}, dG(r) r in {0,1,2}, "
                                    "correlated log-normal K (std 1.0, 8-cell correlation), 4 slabs each, "
-                                   "FP32 inner + FP64 refinement to 1e-8; instances of equal (n, r) solved as one batched "
-                                   "context (all instances in every launch)" % args.instances,
+                                   "FP32 inner + FP64 refinement to relative residual %g; instances of equal (n, r) solved as one batched "
+                                   "context (all instances in every launch)" % (args.instances, args.batch_tol),
                        "instances_per_s": args.instances / t, "total_space_time_dofs": dofs,
-                       "mean_iterations_per_instance": float(np.mean(iters))}}
+                       "mean_iterations_per_instance": float(np.mean(iters))},
+            "error_vs_fp64": {"max": max(errs), "instances_checked": len(errs),
+                              "definition": "||U_end(mixed, residual tol) - U_end(FP64, residual 1e-12)|| / ||U_end(FP64)||"}}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -260,6 +270,76 @@ def run_apply(args):
         out[name] = {"ms": t * 1e3, "algorithmic_MB": algo / 1e6, "achieved_GBs": algo / t / 1e9,
                      "hbm_peak_GBs": hbm_peak_measured(ROOT), "frac_of_hbm": algo / t / 1e9 / hbm_peak_measured(ROOT),
                      "slab_dofs_per_s": ctx.n_slab / t}
+    ctx.destroy()
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def run_kernels(args):
+    """Per-kernel timings of the operator pieces on the layered 3-D problem at n^3, dG(r), without
+    a solve (no Krylov bases: a few GB on the device): the FP32 elasticity operator on one column,
+    one FP32 multigrid V-cycle, one FP32 flux-pressure Schur Chebyshev step, and FP32 / FP64 slab
+    applies; CUDA events, median of `steps`, L2 flushed before each.  One more V-cycle and Schur
+    step run inside the NVTX ranges 'vcycle' and 'schur_step' (for single-kernel profiler
+    captures)."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_1801_04984_gb300 import binding as B
+    from paper_1801_04984_gb300.inputs import layered_logk, K0
+    n, r = args.n, args.r
+    g = layered_logk((n, n, n), layer_cells=4, std=1.5, seed=1801)
+    ubc, fbc = consolidation_bcs(3)
+    ctx = B.Context(3, (n, n, n), dict(COEF, K=K0 * np.exp(g)), r, ubc, fbc)
+    tau = 1.0 / args.slabs
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    gen = torch.Generator(device="cuda").manual_seed(1801)
+    xs = torch.rand(ctx.n_space, device="cuda", generator=gen) - 0.5
+    ys = torch.empty_like(xs)
+    xl = torch.rand(ctx.n_slab, device="cuda", generator=gen) - 0.5
+    yl = torch.empty_like(xl)
+    xl64, yl64 = xl.double(), torch.empty(ctx.n_slab, dtype=torch.float64, device="cuda")
+
+    def timed(fn):
+        for _ in range(max(3, args.warmup)):
+            fn()
+        ts = []
+        for _ in range(max(1, args.steps)):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1) * 1e3)
+        return float(np.median(ts))
+    out = {"metric": "operator kernel timings (us, CUDA events, median)", "n_gpus": 1, "dtype": "f32/f64",
+           "data": "synthetic", "config": {"workload": "kernels of: " + WORKLOAD.format(n=n, r=r, slabs=args.slabs),
+                                           "l2": "256 MB buffer written before every timed call"}}
+    peak32, _ = B.fma_peak(B.FP32)
+    ctx.profile(True)
+    ctx.kernel_stats(B.KERNEL_ELASTICITY_FP32)
+    t1 = timed(lambda: ctx.apply_part(B.PART_ELASTICITY, tau, xs, ys))
+    k1 = ctx.kernel_stats(B.KERNEL_ELASTICITY_FP32)
+    ctx.profile(False)
+    nodes = (2 * n + 1) ** 3
+    out["elasticity_fp32_1col_us"] = t1
+    out["elasticity_fp32_1col_kernel_us"] = 1e3 * k1[1] / max(1, k1[0])
+    out["elasticity_fp32_1col_frac_of_fp32_peak"] = 360.0 * nodes / (k1[1] / max(1, k1[0]) / 1e3) / 1e12 / peak32
+    out["vcycle_fp32_us"] = timed(lambda: ctx.apply_part(B.PART_VCYCLE, tau, xs, ys))
+    out["schur_step_fp32_us"] = timed(lambda: ctx.apply_part(B.PART_SCHUR_STEP, tau, xs, ys))
+    out["slab_apply_fp32_us"] = timed(lambda: ctx.apply_slab(tau, xl, yl))
+    out["slab_apply_fp64_us"] = timed(lambda: ctx.apply_slab(tau, xl64, yl64))
+    out["fp32_fma_peak_tflops"] = peak32
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("vcycle")
+    ctx.apply_part(B.PART_VCYCLE, tau, xs, ys)
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.nvtx.range_push("schur_step")
+    ctx.apply_part(B.PART_SCHUR_STEP, tau, xs, ys)
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
     ctx.destroy()
     print(json.dumps(out), flush=True)
     return 0
@@ -350,11 +430,16 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison march")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer run")
-    ap.add_argument("--config", default="march", choices=["march", "batch", "apply", "dwr", "fixed_stress"],
+    ap.add_argument("--no-profile", action="store_true",
+                    help="skip the extra per-kernel-event step and the FMA peaks (for profiler launch lists)")
+    ap.add_argument("--config", default="march", choices=["march", "batch", "apply", "dwr", "fixed_stress", "kernels"],
                     help="march: the layered 3-D march (default 64^3 dG(2), 8 slabs); batch: 256 ragged 2-D instances; "
                          "apply: one slab-operator apply against the HBM roofline; "
-                         "dwr: goal-oriented time-error estimate; fixed_stress: iterative coupling vs monolithic")
+                         "dwr: goal-oriented time-error estimate; fixed_stress: iterative coupling vs monolithic; "
+                         "kernels: operator-kernel timings without a solve")
     ap.add_argument("--instances", type=int, default=256)
+    ap.add_argument("--batch-tol", type=float, default=1e-10,
+                    help="batch: relative residual of every slab solve (the end states are checked against FP64)")
     ap.add_argument("--workers", type=int, default=0, help="batch: max instances per batched context (0: library default)")
     ap.add_argument("--cheb-degree", type=int, default=0, help="elasticity smoother degree (0: library default)")
     ap.add_argument("--pair-coupling", type=int, default=0, help="0: block Gauss-Seidel on the complex pair, -1: dropped")
@@ -374,6 +459,8 @@ def main():
         return run_dwr(args)
     if args.config == "fixed_stress":
         return run_fixed_stress(args)
+    if args.config == "kernels":
+        return run_kernels(args)
 
     import torch
     ws, rank, local = dist_env()
@@ -432,19 +519,21 @@ def main():
     launches1, _, _ = ctx.counters()
     clocks = sampler.stop() if sampler else None
     # one more (untimed) step with CUDA events around every launch of the dominant kernels
-    ctx.profile(True)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    step(B.MIXED, U_mixed)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    t_prof = e0.elapsed_time(e1) / 1e3
-    el = ctx.kernel_stats(B.KERNEL_ELASTICITY_FP32)
-    sch = ctx.kernel_stats(B.KERNEL_SCHUR_FP32)
-    el64 = ctx.kernel_stats(B.KERNEL_ELASTICITY_FP64)
-    ctx.profile(False)
+    t_prof, el, sch, el64 = 0.0, (0, 0.0, 0.0), (0, 0.0, 0.0), (0, 0.0, 0.0)
+    if not args.no_profile:
+        ctx.profile(True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        step(B.MIXED, U_mixed)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_prof = e0.elapsed_time(e1) / 1e3
+        el = ctx.kernel_stats(B.KERNEL_ELASTICITY_FP32)
+        sch = ctx.kernel_stats(B.KERNEL_SCHUR_FP32)
+        el64 = ctx.kernel_stats(B.KERNEL_ELASTICITY_FP64)
+        ctx.profile(False)
     dofs_step = ctx.n_slab * slabs
     value, t_step = whole_job_rate(dofs_step, float(np.mean(times)), ws, dev)
 
@@ -487,8 +576,7 @@ def main():
     # throughput that biot_fma_peak measures on this GPU in this run.  The FP64 elasticity
     # launches of the same march (the true residuals of the refinement) are reported against
     # the measured FP64 FMA throughput.
-    peak32, _ = B.fma_peak(B.FP32)
-    peak64, _ = B.fma_peak(B.FP64)
+    peak32, peak64 = (B.fma_peak(B.FP32)[0], B.fma_peak(B.FP64)[0]) if not args.no_profile else (float("nan"),) * 2
     el_n, el_ms, el_units = el
     achieved = 360.0 * el_units / (el_ms / 1e3) / 1e12 if el_ms > 0 else None
     traffic, traffic_src = None, None
@@ -502,7 +590,8 @@ def main():
                                % os.path.relpath(prof_path, ROOT))
     except OSError:
         traffic = None
-    roofline = {"bound": "alu", "kernel": "k_apply_u3_col<float> (FP32 elasticity operator)",
+    roofline = {"bound": "alu",
+                "kernel": "FP32 elasticity operator (k_elast3_zm on grids of >= 1e5 nodes, k_apply_u3_col<float> below)",
                 "achieved": achieved, "peak": peak32, "unit": "TFLOP/s",
                 "frac": (achieved / peak32) if achieved else None,
                 "peak_source": "measured in this run: biot_fma_peak(FP32), independent FMA chains on every SM",

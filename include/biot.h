@@ -398,6 +398,24 @@ int biot_kernel_stats(biot_t ctx, int kind, int64_t* launches, double* ms, doubl
  * allocates nothing.  Errors: EINVAL for another prec, ECUDA. */
 int biot_fma_peak(int prec, double* tflops, double* ms, void* stream);
 
+/* Launch-shape tuning table.  The first FP32 solve of a context times every run length
+ * (planes per block) of the z-marching elasticity kernel on each multigrid level that uses
+ * it, for each column count the solver launches, with CUDA events on the solve's stream, and
+ * keeps the fastest; every candidate produces bitwise-identical results, so the choice
+ * changes only the time.  Results persist in a JSON object {"key": value} in the file
+ * $BIOT_TUNE_CACHE, else $XDG_CACHE_HOME/biot_gb300/tune.json, else
+ * $HOME/.cache/biot_gb300/tune.json (read once per process, rewritten atomically on every
+ * new entry; an unreadable or malformed file is ignored).  Environment BIOT_TUNE=0 turns the
+ * measurement off (a stored value is still used; without one the kernel's heuristic applies).
+ * Keys have the form "elast3_zrun|<device>_sm<SMs>|<nx>x<ny>x<nz>|cols<c>" (node counts).
+ * These three calls touch only the host table and the file (no GPU, no context):
+ * biot_tune_get returns the stored value of `key` or -1; biot_tune_put stores `value` under
+ * `key` (EINVAL for an empty key or one with '"' or '\\'); biot_tune_cache_path writes the
+ * file's path into buf (HOST, len bytes; EINVAL when it does not fit). */
+int biot_tune_get(const char* key);
+int biot_tune_put(const char* key, int value);
+int biot_tune_cache_path(char* buf, int len);
+
 const char* biot_last_error(biot_t ctx);
 void biot_destroy(biot_t ctx);
 

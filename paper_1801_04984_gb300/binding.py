@@ -110,6 +110,9 @@ def load(path: str = LIB_PATH):
         "biot_kernel_stats": (C.c_int, [vp, C.c_int, i64p, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
         "biot_counters": (C.c_int, [vp, i64p, i64p, C.POINTER(C.c_double)]),
         "biot_fma_peak": (C.c_int, [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), vp]),
+        "biot_tune_get": (C.c_int, [C.c_char_p]),
+        "biot_tune_put": (C.c_int, [C.c_char_p, C.c_int]),
+        "biot_tune_cache_path": (C.c_int, [C.c_char_p, C.c_int]),
         "biot_last_error": (C.c_char_p, [vp]),
         "biot_destroy": (None, [vp]),
     }
@@ -464,6 +467,27 @@ def fma_peak(prec=FP32):
     if rc != OK:
         raise BiotError(rc, "biot_fma_peak failed")
     return tf.value, ms.value
+
+
+def tune_get(key):
+    """Stored launch-shape choice for `key` (biot_tune_get), or -1."""
+    return int(load().biot_tune_get(key.encode()))
+
+
+def tune_put(key, value):
+    """Store a launch-shape choice (biot_tune_put); also written to the cache file."""
+    rc = load().biot_tune_put(key.encode(), int(value))
+    if rc != OK:
+        raise BiotError(rc, "biot_tune_put: invalid key %r" % key)
+
+
+def tune_cache_path():
+    """Path of the tuning cache file this process reads and writes (biot_tune_cache_path)."""
+    buf = C.create_string_buffer(4096)
+    rc = load().biot_tune_cache_path(buf, len(buf))
+    if rc != OK:
+        raise BiotError(rc, "biot_tune_cache_path failed")
+    return buf.value.decode()
 
 
 def time_tables(r):

@@ -322,6 +322,7 @@ struct biot_ctx {
   int nb = 1;                  // independent instances batched in this context (level-major vectors)
   int lumped_flux = 1;
   bool use_graphs = true;
+  bool tuned = false;          // launch shapes of this context's kernels looked up / measured
   std::map<GraphKey, GraphEntry> graphs;
   cudaStream_t ws = nullptr;   // the library's own work stream (graphs need a capturable stream)
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
@@ -1120,9 +1121,25 @@ template <> constexpr int prec_id<double>() { return 0; }
 template <> constexpr int prec_id<float>() { return 1; }
 
 // precompute what the preconditioner needs for this tau (host syncs, so never inside a capture)
+// launch shapes of the FP32 z-marching elasticity kernel on every level that uses it, for each
+// column count the solver launches (once per context; measured once per GPU and shape)
+template <typename T>
+void tune_levels(biot_ctx&, cudaStream_t) {}
+template <>
+void tune_levels<float>(biot_ctx& c, cudaStream_t st) {
+  if (c.tuned || c.g.dim != 3) return;
+  c.tuned = true;
+  for (Level& L : c.lv) {
+    if (L.g.nnode < ELAST3_MIN_NODES) continue;
+    for (int k = 1; k <= c.nt; ++k) elast3_tune(L.g, L.t32, c.lam, c.mu, k * c.nb, L.w32.x, L.w32.Ax, st);
+  }
+  CKL();
+}
+
 template <typename T>
 void prec_prepare(biot_ctx& c, double tau, cudaStream_t st) {
   ensure_prec<T>(c);
+  tune_levels<T>(c, st);
   PrecWork<T>& w = c.pw<T>();
   double lm = schur_lmax(c, tau, st);
   (void)lm;

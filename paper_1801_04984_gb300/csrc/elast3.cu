@@ -28,6 +28,9 @@
 // output is computed by one thread: no atomics, bitwise reproducible.
 #include <algorithm>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "internal.h"
@@ -407,7 +410,7 @@ struct EpiResid {
   }
   __device__ __forceinline__ void store(float* y, int64_t ko, int64_t cn, bool fr, float Ax, const float* u, const float* eb,
                                         int it) const {
-    y[ko + cn] = eb[it] - (fr ? Ax : u[cn]);
+    y[ko + cn] = __fsub_rn(eb[it], fr ? Ax : u[cn]);
   }
 };
 struct EpiCheb {
@@ -429,10 +432,12 @@ struct EpiCheb {
       d[ko + cn] = 0.f;
       return;
     }
-    float dn = c2 * di * (bi - Ax);
-    if (c1 != 0.f) dn += c1 * eb[3 * NOUT + it];
+    // explicit roundings: the stage is inlined twice (inside the plane loop and for a run's last
+    // plane), and both copies must compute the same sequence whatever the compiler contracts
+    float dn = __fmul_rn(__fmul_rn(c2, di), __fsub_rn(bi, Ax));
+    if (c1 != 0.f) dn = __fmaf_rn(c1, eb[3 * NOUT + it], dn);
     d[ko + cn] = dn;
-    xo[ko + cn] = eb[2 * NOUT + it] + dn;
+    xo[ko + cn] = __fadd_rn(eb[2 * NOUT + it], dn);
   }
 };
 
@@ -488,6 +493,29 @@ ElastTaps make_taps(const TabT<float>& tb, double lam, double mu) {
 
 }  // namespace
 
+// tuned planes per block by (device, nx, ny, nz, columns); filled from the tuning table on
+// first use of a shape (0: none, use the heuristic)
+std::mutex g_zrun_mu;
+std::map<std::tuple<int, int, int, int, int>, int> g_zrun;
+int g_zrun_force = 0;  // set only while elast3_tune times a candidate
+
+std::string zrun_key(int nx, int ny, int nz, int cols) {
+  return "elast3_zrun|" + tune_device_tag() + "|" + std::to_string(nx) + "x" + std::to_string(ny) + "x" + std::to_string(nz) +
+         "|cols" + std::to_string(cols);
+}
+
+int zrun_lookup(int nx, int ny, int nz, int cols) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const auto k = std::make_tuple(dev, nx, ny, nz, cols);
+  std::lock_guard<std::mutex> lk(g_zrun_mu);
+  auto it = g_zrun.find(k);
+  if (it != g_zrun.end()) return it->second;
+  const int v = std::max(0, tune_get(zrun_key(nx, ny, nz, cols)));
+  g_zrun[k] = v;
+  return v;
+}
+
 // host launcher (FP32, 3-D): `cols` columns of stride su / sy; column k takes au[k / udiv]
 void launch_elast3_f32(const Grid& g, const TabT<float>& tb, const SlabCoef& sc, int cols, const float* u, int64_t su, float* y,
                        int64_t sy, cudaStream_t st, const UEpi<float>* epi) {
@@ -509,13 +537,18 @@ void launch_elast3_f32(const Grid& g, const TabT<float>& tb, const SlabCoef& sc,
   }
   for (int k = 0; k < MAXR; ++k) a.au[k] = (float)sc.au[k];
   a.udiv = sc.udiv > 0 ? sc.udiv : 1;
-  // z runs per block: enough blocks for about four waves of two blocks per SM, runs of at
-  // least 6 planes (a run reloads 4 window planes; shorter runs trade that for parallelism)
+  // planes per block: the tuned value for this shape, else enough blocks for about four waves
+  // of two blocks per SM with runs of at least 6 planes (a run reloads 4 window planes)
   const int tiles = a.ntx * nty;
-  int nchunk = (4 * 2 * 152 + tiles * cols - 1) / (tiles * cols);
-  nchunk = std::max(1, std::min(nchunk, a.nz / 6));
-  a.zchunk = (a.nz + nchunk - 1) / nchunk;
-  nchunk = (a.nz + a.zchunk - 1) / a.zchunk;
+  const int tuned = g_zrun_force > 0 ? g_zrun_force : zrun_lookup(a.nx, a.ny, a.nz, cols);
+  if (tuned > 0) {
+    a.zchunk = std::min(tuned, a.nz);
+  } else {
+    int nc = (4 * 2 * 152 + tiles * cols - 1) / (tiles * cols);
+    nc = std::max(1, std::min(nc, a.nz / 6));
+    a.zchunk = (a.nz + nc - 1) / nc;
+  }
+  const int nchunk = (a.nz + a.zchunk - 1) / a.zchunk;
   const dim3 grid((unsigned)tiles, (unsigned)nchunk, (unsigned)cols);
   const int mode = epi ? epi->mode : EPI_NONE;
   prof_begin(st, 0, (double)g.nnode * cols);
@@ -529,6 +562,61 @@ void launch_elast3_f32(const Grid& g, const TabT<float>& tb, const SlabCoef& sc,
     (note_launch(), k_elast3_zm<EpiPlain><<<grid, NTH, elast3_smem_bytes<EpiPlain>(), st>>>(tp, a, u, su, y, sy, EpiPlain{}));
   }
   prof_end(st, 0);
+}
+
+// Time every candidate run length (planes per block) of the plain apply on this shape and keep
+// the fastest (median of 5 launches after 2 warm-ups, CUDA events on `st`).  All candidates give
+// bitwise-identical results.  Not to be called inside a stream capture.
+void elast3_tune(const Grid& g, const TabT<float>& tb, double lam, double mu, int cols, float* u, float* y, cudaStream_t st) {
+  if (g.dim != 3 || g.nnode < ELAST3_MIN_NODES || !tune_enabled()) return;
+  const int nx = g.nu[0], ny = g.nu[1], nz = g.nu[2];
+  if (zrun_lookup(nx, ny, nz, cols) > 0) return;
+  SlabCoef sc;
+  std::memset(&sc, 0, sizeof(sc));
+  sc.nt = 1;
+  sc.lam = lam;
+  sc.mu = mu;
+  sc.au[0] = 0.1;
+  sc.ucols = cols;
+  sc.udiv = cols;
+  if (cudaMemsetAsync(u, 0, sizeof(float) * cols * g.Nu, st) != cudaSuccess) return;
+  std::vector<int> cand;
+  for (int z : {4, 6, 8, 11, 16, 22, 32, 43, 65, 129, 257})
+    if (z <= nz && (cand.empty() || (nz + z - 1) / z != (nz + cand.back() - 1) / cand.back())) cand.push_back(z);
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return;
+  }
+  int best = 0;
+  float best_ms = 1e30f;
+  for (int z : cand) {
+    g_zrun_force = z;
+    for (int w = 0; w < 2; ++w) launch_elast3_f32(g, tb, sc, cols, u, g.Nu, y, g.Nu, st, nullptr);
+    float ts[5];
+    for (int rep = 0; rep < 5; ++rep) {
+      cudaEventRecord(e0, st);
+      launch_elast3_f32(g, tb, sc, cols, u, g.Nu, y, g.Nu, st, nullptr);
+      cudaEventRecord(e1, st);
+      cudaEventSynchronize(e1);
+      cudaEventElapsedTime(&ts[rep], e0, e1);
+    }
+    std::sort(ts, ts + 5);
+    if (ts[2] < best_ms) {
+      best_ms = ts[2];
+      best = z;
+    }
+  }
+  g_zrun_force = 0;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (cudaGetLastError() != cudaSuccess || best <= 0) return;
+  tune_put(zrun_key(nx, ny, nz, cols), best);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(g_zrun_mu);
+  g_zrun[std::make_tuple(dev, nx, ny, nz, cols)] = best;
 }
 
 // opt-in dynamic shared memory of the three instantiations (called once, before any capture)

@@ -1,6 +1,7 @@
 // Internal (not exported) declarations shared by the library's translation units.
 #pragma once
 #include <cstdint>
+#include <string>
 #include <cuda_runtime.h>
 #include "common.cuh"
 #include "tables.h"
@@ -48,6 +49,16 @@ void apply_init_attributes();
 // least ELAST3_MIN_NODES nodes per component (65^3 and finer)
 constexpr int64_t ELAST3_MIN_NODES = 100000;
 void elast3_init_attributes();
+// measure the launch shape of the z-marching kernel for this grid and column count once (per
+// GPU, cached in the tuning file); u and y: scratch of cols * g.Nu floats each
+void elast3_tune(const Grid& g, const TabT<float>& tb, double lam, double mu, int cols, float* u, float* y, cudaStream_t st);
+
+// ---- launch-shape autotuner (tune.cu): process table backed by a JSON cache file
+bool tune_enabled();
+int tune_get(const std::string& key);  // -1 when absent
+void tune_put(const std::string& key, int value);
+std::string tune_device_tag();
+std::string tune_cache_path();
 void launch_elast3_f32(const Grid& g, const TabT<float>& tb, const SlabCoef& sc, int cols, const float* u, int64_t su, float* y,
                        int64_t sy, cudaStream_t st, const UEpi<float>* epi);
 template <typename T>
