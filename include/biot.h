@@ -110,7 +110,8 @@ typedef struct {
 typedef struct {
   int gmres_restart;    /* m (default 30) */
   int cheb_degree;      /* Chebyshev degree of the elasticity smoother (default 3, at most 128) */
-  int schur_degree;     /* Chebyshev degree of the flux-pressure Schur solve (default 32, at most 128) */
+  int schur_degree;     /* Chebyshev degree of the flux-pressure Schur solve (at most 128; 0 (default):
+                           chosen per tau from the spectral bounds, see biot_schur_bounds) */
   int mg_min_cells;     /* stop coarsening at this many cells per direction (default 2) */
   double beta_fs;       /* fixed-stress parameter; <= 0 selects b^2 / K_dr */
   int flux_mass_exact;  /* flux-pressure block: 0 (default) replaces the Darcy mass by its diagonal;
@@ -397,6 +398,17 @@ int biot_kernel_stats(biot_t ctx, int kind, int64_t* launches, double* ms, doubl
  * the operator kernels' FP32 and FP64 arithmetic rates are reported.  No context needed;
  * allocates nothing.  Errors: EINVAL for another prec, ECUDA. */
 int biot_fma_peak(int prec, double* tflops, double* ms, void* stream);
+
+/* Spectral bounds of the Jacobi-scaled lumped Schur complement D^{-1} Shat of this tau, the
+ * operator whose inverse the flux-pressure block of the preconditioner approximates
+ * (paper §Preconditioning; Shat = cm Mp + tau B diag(Mq)^{-1} B^T, cm the storage
+ * coefficient of each temporal level).  They come from 30 FP64 Lanczos steps on every
+ * temporal level (cached per tau; the first call for a tau allocates the FP64
+ * preconditioner workspace).  bounds (HOST, 4 doubles): the smallest and largest Ritz values
+ * (over all temporal levels), then the interval [lo, hi] the Chebyshev-Jacobi solve is built
+ * on.  degree (HOST, may be NULL): the Chebyshev degree the solve uses for this tau, 0 when
+ * the cell-centred multigrid replaces it.  Errors: EINVAL (NULL bounds, tau <= 0), ECUDA. */
+int biot_schur_bounds(biot_t ctx, double tau, double* bounds, int* degree, void* stream);
 
 /* Launch-shape tuning table.  The first FP32 solve of a context times every run length
  * (planes per block) of the z-marching elasticity kernel on each multigrid level that uses

@@ -110,6 +110,7 @@ def load(path: str = LIB_PATH):
         "biot_kernel_stats": (C.c_int, [vp, C.c_int, i64p, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
         "biot_counters": (C.c_int, [vp, i64p, i64p, C.POINTER(C.c_double)]),
         "biot_fma_peak": (C.c_int, [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), vp]),
+        "biot_schur_bounds": (C.c_int, [vp, C.c_double, dp, ip, vp]),
         "biot_tune_get": (C.c_int, [C.c_char_p]),
         "biot_tune_put": (C.c_int, [C.c_char_p, C.c_int]),
         "biot_tune_cache_path": (C.c_int, [C.c_char_p, C.c_int]),
@@ -399,6 +400,14 @@ class Context:
         import torch
         return self._check(self.lib.biot_schur_apply_noalloc(self.h, float(tau), _ptr(x, torch.float64, self.n_space, "in"),
                                                              _ptr(y, torch.float64, self.n_space, "out"), _stream()))
+
+    def schur_bounds(self, tau):
+        """(smallest Ritz value, largest Ritz value, Chebyshev interval lo, hi, degree) of the
+        Jacobi-scaled lumped Schur complement for this tau (biot_schur_bounds)."""
+        b = (C.c_double * 4)()
+        deg = C.c_int()
+        self._check(self.lib.biot_schur_bounds(self.h, float(tau), b, C.byref(deg), _stream()))
+        return tuple(b) + (deg.value,)
 
     def profile(self, enable):
         return self._check(self.lib.biot_profile(self.h, int(bool(enable))))

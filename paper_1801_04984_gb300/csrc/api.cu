@@ -794,6 +794,9 @@ void schur_cm(const biot_ctx& c, double* cm) {
   for (int k = 0; k < c.nt; ++k) cm[k] = c.tb.lam[k] * (c.invM + c.beta);
 }
 
+// Chebyshev interval of the Schur solve: [max(0.7 lmin_ritz, lmax / SCHUR_KAPPA_MAX), 1.1 lmax]
+constexpr double SCHUR_KAPPA_MAX = 4000.0;
+
 // largest eigenvalue of Dinv Shat (CG-Lanczos in FP64 on every rhs, max over rhs), cached per tau
 double schur_lmax(biot_ctx& c, double tau, cudaStream_t st) {
   if (c.schur_lmax_tau == tau) return c.schur_lmax;
@@ -811,7 +814,7 @@ double schur_lmax(biot_ctx& c, double tau, cudaStream_t st) {
   c.schur_lmax = lm;
   c.schur_kappa = lmin > 0 ? lm / lmin : 1e300;
   // Ritz values converge from inside the spectrum: widen the lower end, keep it positive
-  c.schur_lmin = std::max(0.7 * lmin, lm / 200.0);
+  c.schur_lmin = std::max(0.7 * lmin, lm / SCHUR_KAPPA_MAX);
   c.schur_lmax_tau = tau;
   return lm;
 }
@@ -952,6 +955,19 @@ void schur_vcycle(biot_ctx& c, double tau, const double* cm, double lmax0, int k
   CKL();
 }
 
+// Chebyshev degree of the flux-pressure Schur solve: the caller's, else the degree at which
+// the Chebyshev error bound 2 rho^k, rho = (sqrt(kappa) - 1) / (sqrt(kappa) + 1), on the
+// solve's interval (kappa = its hi / lo) falls to about 0.025, i.e. k ~ 2.2 sqrt(kappa).
+// Measured on the layered 3-D problems: at 32^3 dG(1) (kappa 218, degree 33) degrees 20-40
+// give the same time to solution; at 64^3 dG(2) (kappa ~950, degree 68) 64-80 are fastest,
+// 32 is 16 % slower.  Called after schur_lmax for this tau.
+int schur_degree(const biot_ctx& c) {
+  if (c.opts.schur_degree > 0) return c.opts.schur_degree;
+  const double kappa = 1.1 * c.schur_lmax / c.schur_lmin;
+  const int k = (int)std::ceil(2.2 * std::sqrt(kappa));
+  return std::max(16, std::min(k, MAX_CHEB));
+}
+
 // p = Shat^{-1} g by Chebyshev-Jacobi (w.gp -> w.pp)
 template <typename T>
 void schur_solve(biot_ctx& c, double tau, cudaStream_t st, int k0, int nk) {
@@ -961,7 +977,7 @@ void schur_solve(biot_ctx& c, double tau, cudaStream_t st, int k0, int nk) {
   schur_cm(c, cm_all);
   const double* cm = cm_all + k0;
   double lmax = schur_lmax(c, tau, st);
-  ChebCoef cc = cheb_coefs(c.opts.schur_degree, c.schur_lmin, 1.1 * lmax);
+  ChebCoef cc = cheb_coefs(schur_degree(c), c.schur_lmin, 1.1 * lmax);
   if (c.lumped_flux) {
     if (w.schur_tau != tau) {  // stencil and diagonal of this tau (prec_prepare normally did this)
       schur_prepare<T>(c, tau, st);
@@ -2037,7 +2053,7 @@ int setup_impl(const biot_mesh* mesh, const biot_coeffs* co, int r, const biot_o
     biot_opts d;
     d.gmres_restart = 30;
     d.cheb_degree = 3;
-    d.schur_degree = 32;
+    d.schur_degree = 0;  // chosen per tau from the spectral bounds
     d.mg_min_cells = 2;
     d.beta_fs = -1;
     d.flux_mass_exact = 0;
@@ -2635,6 +2651,20 @@ extern "C" int biot_apply_part(biot_t c, int part, double tau, const void* in, v
   if (prec == BIOT_FP64) apply_part_T<double>(*c, part, tau, (const double*)in, (double*)out, st);
   else if (prec == BIOT_FP32) apply_part_T<float>(*c, part, tau, (const float*)in, (float*)out, st);
   else fail(BIOT_EINVAL, "prec must be BIOT_FP64 or BIOT_FP32");
+  return BIOT_OK;
+  API_END(c)
+}
+
+extern "C" int biot_schur_bounds(biot_t c, double tau, double* bounds, int* degree, void* stream) {
+  API_BEGIN(c)
+  if (!bounds || !(tau > 0)) fail(BIOT_EINVAL, "schur_bounds: NULL bounds or tau <= 0");
+  cudaStream_t st = (cudaStream_t)stream;
+  const double lm = schur_lmax(*c, tau, st);
+  bounds[0] = lm / c->schur_kappa;
+  bounds[1] = lm;
+  bounds[2] = c->schur_lmin;
+  bounds[3] = 1.1 * lm;
+  if (degree) *degree = use_schur_mg(*c) ? 0 : schur_degree(*c);
   return BIOT_OK;
   API_END(c)
 }

@@ -158,3 +158,38 @@ def test_schur_chebyshev_step_kernel(n, bcs, prec):
     got = yd.double().cpu().numpy()[m.off_p:]
     tol = 1e-12 if prec == "fp64" else 2e-6
     assert np.abs(got - ref).max() < tol * np.abs(ref).max(), np.abs(got - ref).max() / np.abs(ref).max()
+
+
+@pytest.mark.parametrize("n,bcs", CASES)
+@pytest.mark.parametrize("tau", [0.07, 1.0])
+def test_schur_spectral_bounds_and_chebyshev_degree(n, bcs, tau):
+    """biot_schur_bounds on a dG(0) context against the exact spectrum of the Jacobi-scaled
+    lumped Schur complement diag(Shat)^{-1} Shat (dense eigenvalues of the oracle's
+    assembled Shat): the Lanczos Ritz values lie inside the spectrum (Cauchy interlacing),
+    the largest one within 1 % of the largest eigenvalue, the smallest within a factor 2 of
+    the smallest; the Chebyshev interval's upper end covers the spectrum; the degree is the
+    one at which the Chebyshev error bound on that interval falls to ~0.025 (2.2 sqrt(kappa),
+    clamped to [16, 128])."""
+    import math
+    from paper_1801_04984_gb300 import binding as B
+    from oracle.timebasis import radau_matrices
+    rng = np.random.default_rng(37)
+    K = 1e-2 * np.exp(rng.normal(0, 1.5, size=int(np.prod(n))))
+    ubc, fbc = bcs
+    ctx = B.Context(len(n), n, dict(C2, K=K), 0, ubc, fbc)
+    m = Mesh(n)
+    blk = SpatialBlocks(m, dict(C2, K=K))
+    fq = constraint_mask(m, *bcs)[m.Nu:m.off_p] == 1.0
+    Mq = blk.Mq.tocsr()[fq][:, fq]
+    Bf = blk.B.tocsr()[:, fq]
+    Mt, D = radau_matrices(0)
+    lam = D[0, 0] / Mt[0, 0]  # the one eigenvalue of Mt^{-1} D for dG(0)
+    beta = C2["b"] ** 2 / C2["K_dr"]
+    S = (lam * (C2["invM"] + beta) * blk.Mp + tau * (Bf @ sp.diags(1.0 / Mq.diagonal()) @ Bf.T)).toarray()
+    d = np.diag(S)
+    ev = np.linalg.eigvalsh(S / np.sqrt(np.outer(d, d)))
+    ritz_lo, ritz_hi, lo, hi, deg = ctx.schur_bounds(tau)
+    assert ev[0] * (1 - 1e-10) <= ritz_lo <= ritz_hi <= ev[-1] * (1 + 1e-10), (ev[0], ev[-1], ritz_lo, ritz_hi)
+    assert ritz_hi > 0.99 * ev[-1] and ritz_lo < 2.0 * ev[0], (ev[0], ev[-1], ritz_lo, ritz_hi)
+    assert hi >= ev[-1] and 0 < lo <= ritz_lo
+    assert deg == max(16, min(128, math.ceil(2.2 * math.sqrt(hi / lo))))
