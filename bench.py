@@ -607,7 +607,7 @@ def main():
                      "peak_source": "measured in this run: biot_fma_peak(FP64)",
                      "launches_per_step": e64_n, "avg_launch_us": 1e3 * e64_ms / max(1, e64_n),
                      "share_of_step": (e64_ms / 1e3) / t_prof if t_prof > 0 else None}
-    schur = {"kernel": "k_schur_cheb_st<float> (one Chebyshev step, flux-pressure Schur)", "launches_per_step": sch[0],
+    schur = {"kernel": "k_schur_cheb_mf<float> (one matrix-free Chebyshev step of the flux-pressure Schur solve)", "launches_per_step": sch[0],
              "avg_launch_us": 1e3 * sch[1] / max(1, sch[0]), "share_of_step": (sch[1] / 1e3) / t_prof if t_prof > 0 else None}
     s_mean = stats[-1]
     cpu = None

@@ -957,14 +957,14 @@ void schur_vcycle(biot_ctx& c, double tau, const double* cm, double lmax0, int k
 
 // Chebyshev degree of the flux-pressure Schur solve: the caller's, else the degree at which
 // the Chebyshev error bound 2 rho^k, rho = (sqrt(kappa) - 1) / (sqrt(kappa) + 1), on the
-// solve's interval (kappa = its hi / lo) falls to about 0.025, i.e. k ~ 2.2 sqrt(kappa).
-// Measured on the layered 3-D problems: at 32^3 dG(1) (kappa 218, degree 33) degrees 20-40
-// give the same time to solution; at 64^3 dG(2) (kappa ~950, degree 68) 64-80 are fastest,
-// 32 is 16 % slower.  Called after schur_lmax for this tau.
+// solve's interval (kappa = its hi / lo) falls to about 0.07, i.e. k ~ 1.7 sqrt(kappa).
+// Measured on the layered 3-D problems: at 32^3 dG(1) (kappa 218, degree 26) degrees 20-40
+// give the same time to solution; at 64^3 dG(2) (kappa ~950, degree 53) 52 was fastest of
+// 32-96, 68 3 % and 84 6 % slower, 32 29 % slower.  Called after schur_lmax for this tau.
 int schur_degree(const biot_ctx& c) {
   if (c.opts.schur_degree > 0) return c.opts.schur_degree;
   const double kappa = 1.1 * c.schur_lmax / c.schur_lmin;
-  const int k = (int)std::ceil(2.2 * std::sqrt(kappa));
+  const int k = (int)std::ceil(1.7 * std::sqrt(kappa));
   return std::max(16, std::min(k, MAX_CHEB));
 }
 

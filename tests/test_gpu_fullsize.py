@@ -195,7 +195,9 @@ def test_fullsize_layered_march_matches_column_oracle(contexts, n, r, slabs, mod
     U0 = torch.zeros_like(f)
     U = torch.zeros_like(f)
     X_all = torch.empty(slabs * ctx.n_slab, dtype=torch.float64, device="cuda")
-    ctx.march(1.0, slabs, [f], [[1.0, 0, 0, 0]], U0, U, X_all=X_all, tol=1e-10,
+    # the bar is on the error (1e-8); the flux block's conditioning amplifies the residual by
+    # up to ~100 here, so the slab solves run to relative residual 1e-11
+    ctx.march(1.0, slabs, [f], [[1.0, 0, 0, 0]], U0, U, X_all=X_all, tol=1e-11,
               mode=B.MIXED if mode == "mixed" else B.FP64)
     m = Mesh((n, n, n))
     worst = 0.0

@@ -168,7 +168,7 @@ def test_schur_spectral_bounds_and_chebyshev_degree(n, bcs, tau):
     assembled Shat): the Lanczos Ritz values lie inside the spectrum (Cauchy interlacing),
     the largest one within 1 % of the largest eigenvalue, the smallest within a factor 2 of
     the smallest; the Chebyshev interval's upper end covers the spectrum; the degree is the
-    one at which the Chebyshev error bound on that interval falls to ~0.025 (2.2 sqrt(kappa),
+    one at which the Chebyshev error bound on that interval falls to ~0.07 (1.7 sqrt(kappa),
     clamped to [16, 128])."""
     import math
     from paper_1801_04984_gb300 import binding as B
@@ -192,4 +192,4 @@ def test_schur_spectral_bounds_and_chebyshev_degree(n, bcs, tau):
     assert ev[0] * (1 - 1e-10) <= ritz_lo <= ritz_hi <= ev[-1] * (1 + 1e-10), (ev[0], ev[-1], ritz_lo, ritz_hi)
     assert ritz_hi > 0.99 * ev[-1] and ritz_lo < 2.0 * ev[0], (ev[0], ev[-1], ritz_lo, ritz_hi)
     assert hi >= ev[-1] and 0 < lo <= ritz_lo
-    assert deg == max(16, min(128, math.ceil(2.2 * math.sqrt(hi / lo))))
+    assert deg == max(16, min(128, math.ceil(1.7 * math.sqrt(hi / lo))))
