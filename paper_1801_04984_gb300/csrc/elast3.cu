@@ -497,7 +497,7 @@ ElastTaps make_taps(const TabT<float>& tb, double lam, double mu) {
 // first use of a shape (0: none, use the heuristic)
 std::mutex g_zrun_mu;
 std::map<std::tuple<int, int, int, int, int>, int> g_zrun;
-int g_zrun_force = 0;  // set only while elast3_tune times a candidate
+thread_local int g_zrun_force = 0;  // set only while elast3_tune (on this thread) times a candidate
 
 std::string zrun_key(int nx, int ny, int nz, int cols) {
   return "elast3_zrun|" + tune_device_tag() + "|" + std::to_string(nx) + "x" + std::to_string(ny) + "x" + std::to_string(nz) +
