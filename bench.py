@@ -157,6 +157,52 @@ def oracle_sample(seconds_target=15.0, n=4, slabs=16):
             "host_cores": os.cpu_count()}
 
 
+def profile_figure(name, key):
+    """A figure recorded in a committed ncu summary under profiles/ (the line `key value`), or None."""
+    try:
+        for line in open(os.path.join(ROOT, "profiles", name)).read().splitlines():
+            if line.startswith(key):
+                return float(line.split(":")[1])
+    except (OSError, ValueError):
+        pass
+    return None
+
+
+def schur_roofline(sch, weight_bytes_per_launch, t_prof, hbm_peak, traffic_per_unit=None, traffic_file=None):
+    """HBM roofline of the flux-pressure Schur Chebyshev step k_schur_cheb_mf<float> from its
+    launches in one march, sch = (launches, ms, units), units = pressure point x right-hand side.
+    Algorithmic bytes of a step: per point and right-hand side x, b and the previous direction d
+    read and the new direction and iterate written (5 x 4 B); per launch the flux weights of the
+    instance (one float per flux DoF) read once.  About 45 flop per point and right-hand side
+    against those 20+ bytes: far below the FP32 ridge point, so the bound is HBM."""
+    n, ms, units = sch
+    if n <= 0 or ms <= 0:
+        return None
+    alg = 20.0 * units + weight_bytes_per_launch * n
+    ach = alg / (ms / 1e3) / 1e9
+    out = {"bound": "hbm", "kernel": "k_schur_cheb_mf<float> (one matrix-free Chebyshev step of the flux-pressure Schur solve)",
+           "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
+           "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy bandwidth)",
+           "traffic": None, "traffic_source": None,
+           "launches_per_step": n, "avg_launch_us": 1e3 * ms / n,
+           "share_of_step": (ms / 1e3) / t_prof if t_prof > 0 else None,
+           "algorithmic_bytes_per_launch": alg / n}
+    if traffic_per_unit:
+        out["traffic"] = traffic_per_unit * units / n
+        out["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of a one-column step (%s), per point x "
+                                 "right-hand side, times the average units of one launch of this march" % traffic_file)
+    return out
+
+
+def dominant_roofline(*rooflines):
+    """(the roofline object with the largest share of the profiled step, the next one)."""
+    ok = [r for r in rooflines if r and r.get("share_of_step")]
+    if not ok:
+        return (rooflines[0] if rooflines else None), None
+    ok.sort(key=lambda r: r["share_of_step"], reverse=True)
+    return ok[0], (ok[1] if len(ok) > 1 else None)
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -519,7 +565,7 @@ def main():
     launches1, _, _ = ctx.counters()
     clocks = sampler.stop() if sampler else None
     # one more (untimed) step with CUDA events around every launch of the dominant kernels
-    t_prof, el, sch, el64 = 0.0, (0, 0.0, 0.0), (0, 0.0, 0.0), (0, 0.0, 0.0)
+    t_prof, el, elc, sch, el64 = 0.0, (0, 0.0, 0.0), (0, 0.0, 0.0), (0, 0.0, 0.0), (0, 0.0, 0.0)
     if not args.no_profile:
         ctx.profile(True)
         e0 = torch.cuda.Event(enable_timing=True)
@@ -531,6 +577,7 @@ def main():
         torch.cuda.synchronize()
         t_prof = e0.elapsed_time(e1) / 1e3
         el = ctx.kernel_stats(B.KERNEL_ELASTICITY_FP32)
+        elc = ctx.kernel_stats(B.KERNEL_ELASTICITY_FP32_COARSE)
         sch = ctx.kernel_stats(B.KERNEL_SCHUR_FP32)
         el64 = ctx.kernel_stats(B.KERNEL_ELASTICITY_FP64)
         ctx.profile(False)
@@ -567,8 +614,10 @@ def main():
                 "ms_per_slab": t64 * 1e3 / slabs, "iterations": s64["iterations"],
                 "end_state_rel_diff_mixed_vs_fp64": rel}
 
-    # roofline of the dominant kernel: the FP32 elasticity (displacement-row) operator, all its
-    # launches in one march (every multigrid level and the slab applies).  Algorithmic work of the
+    # rooflines of the two dominant kernels; `roofline` is the one with the larger share of the
+    # profiled march.  (1) The FP32 elasticity (displacement-row) operator on the fine multigrid
+    # levels (the z-marching kernel, grids of >= 1e5 nodes; its launches in one march: smoothing
+    # steps, residuals and the slab applies).  Algorithmic work of the
     # sum-factorised Kronecker apply: 180 FMA = 360 flop per Q2 node and right-hand side (z pass
     # 12 outputs x 4 taps, y pass 21 terms x 4, x pass 12 x 4; 5-tap vertex / 3-tap mid rows);
     # algorithmic bytes: the displacement block read once and written once, 3 x 2 x 4 B per node.
@@ -590,8 +639,8 @@ def main():
                                % os.path.relpath(prof_path, ROOT))
     except OSError:
         traffic = None
-    roofline = {"bound": "alu",
-                "kernel": "FP32 elasticity operator (k_elast3_zm on grids of >= 1e5 nodes, k_apply_u3_col<float> below)",
+    el_roofline = {"bound": "alu",
+                "kernel": "k_elast3_zm (FP32 elasticity operator on the multigrid levels of >= 1e5 nodes)",
                 "achieved": achieved, "peak": peak32, "unit": "TFLOP/s",
                 "frac": (achieved / peak32) if achieved else None,
                 "peak_source": "measured in this run: biot_fma_peak(FP32), independent FMA chains on every SM",
@@ -607,8 +656,16 @@ def main():
                      "peak_source": "measured in this run: biot_fma_peak(FP64)",
                      "launches_per_step": e64_n, "avg_launch_us": 1e3 * e64_ms / max(1, e64_n),
                      "share_of_step": (e64_ms / 1e3) / t_prof if t_prof > 0 else None}
-    schur = {"kernel": "k_schur_cheb_mf<float> (one matrix-free Chebyshev step of the flux-pressure Schur solve)", "launches_per_step": sch[0],
-             "avg_launch_us": 1e3 * sch[1] / max(1, sch[0]), "share_of_step": (sch[1] / 1e3) / t_prof if t_prof > 0 else None}
+    coarse = {"kernel": "k_apply_u3_col<float> (FP32 elasticity operator on the levels below 1e5 nodes)",
+              "launches_per_step": elc[0], "avg_launch_us": 1e3 * elc[1] / max(1, elc[0]),
+              "share_of_step": (elc[1] / 1e3) / t_prof if t_prof > 0 else None,
+              "achieved_tflops": 360.0 * elc[2] / (elc[1] / 1e3) / 1e12 if elc[1] > 0 else None}
+    # (2) the flux-pressure Schur Chebyshev step, HBM-bound by its arithmetic intensity
+    nqt = ctx.n_space - 3 * (2 * n + 1) ** 3 - 8 * n ** 3  # flux DoFs of one temporal level
+    sch_roofline = schur_roofline(sch, 4.0 * nqt, t_prof, hbm_peak_measured(ROOT),
+                                  profile_figure("schur_step_fp32_%dcube.txt" % n, "dram_bytes_per_point_rhs:"),
+                                  "profiles/schur_step_fp32_%dcube.txt" % n)
+    roofline, second = dominant_roofline(el_roofline, sch_roofline)
     s_mean = stats[-1]
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -628,8 +685,9 @@ def main():
         "e2e": e2e,
         "gpu_launches": int((launches1 - launches0) / max(1, args.steps)),
         "roofline": roofline,
+        "second_kernel": second,
+        "coarse_elasticity": coarse,
         "fp64_roofline": fp64_roofline,
-        "second_kernel": schur,
         "clocks": clocks,
         "cpu_baseline": cpu,
     }

@@ -380,14 +380,21 @@ int biot_profile(biot_t ctx, int enable);
 int biot_counters(biot_t ctx, int64_t* launches, int64_t* op_launches, double* op_ms);
 
 /* Per-kernel tracing detail (after biot_profile(ctx, 1)): for kind
- * BIOT_KERNEL_ELASTICITY_FP32 / _FP64 (displacement-row operator) and
+ * BIOT_KERNEL_ELASTICITY_FP32 (displacement-row operator in FP32: the z-marching kernel on
+ * 3-D grids of 1e5 nodes or more, the 2-D kernel), BIOT_KERNEL_ELASTICITY_FP32_COARSE (the
+ * FP32 3-D operator on grids below 1e5 nodes), BIOT_KERNEL_ELASTICITY_FP64 and
  * BIOT_KERNEL_SCHUR_FP32 (one Chebyshev step of the flux-pressure Schur solve),
  * the number of launches recorded since the last query, their summed device time
  * in ms (CUDA events on the launching stream) and their summed work units (Q2 node
  * x right-hand side for the elasticity operator, Gauss pressure point x
  * right-hand side for the Schur step).  Synchronises on the events, then forgets
  * them.  With profiling on, CUDA graphs are not used. */
-enum { BIOT_KERNEL_ELASTICITY_FP32 = 0, BIOT_KERNEL_ELASTICITY_FP64 = 1, BIOT_KERNEL_SCHUR_FP32 = 2 };
+enum {
+  BIOT_KERNEL_ELASTICITY_FP32 = 0,
+  BIOT_KERNEL_ELASTICITY_FP64 = 1,
+  BIOT_KERNEL_SCHUR_FP32 = 2,
+  BIOT_KERNEL_ELASTICITY_FP32_COARSE = 3
+};
 int biot_kernel_stats(biot_t ctx, int kind, int64_t* launches, double* ms, double* units);
 
 /* Measured arithmetic peak of the CUDA cores on the current device: a kernel of

@@ -23,7 +23,7 @@ F_NATURAL, F_NOFLOW = 0, 1
 FP64, FP32, MIXED, FIXED_STRESS = 0, 1, 2, 3
 LOAD_TRACTION_TOP, LOAD_MMS2D_CONST, LOAD_MMS2D_LINEAR = 0, 1, 2
 PART_FLUX_MASS_INV, PART_SCHUR, PART_VCYCLE, PART_ELASTICITY, PART_SCHUR_STEP = 0, 1, 2, 3, 4
-KERNEL_ELASTICITY_FP32, KERNEL_ELASTICITY_FP64, KERNEL_SCHUR_FP32 = 0, 1, 2
+KERNEL_ELASTICITY_FP32, KERNEL_ELASTICITY_FP64, KERNEL_SCHUR_FP32, KERNEL_ELASTICITY_FP32_COARSE = 0, 1, 2, 3
 ERR_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOCONV", 5: "EBREAKDOWN", 6: "ETIMEOUT"}
 
 

@@ -704,7 +704,7 @@ void launch_apply_u(const Grid& g, const TabT<T>& tb, const SlabCoef& sc, const 
     constexpr bool ALLJ = sizeof(T) == 4;
     dim3 grid((g.nu[0] + T3 - 1) / T3, (g.nu[1] + T3 - 1) / T3, ((g.nu[2] + T3 - 1) / T3) * cols);
     size_t smem = sizeof(T) * (3 * H3 * H3 * H3 + (ALLJ ? 12 : 4) * H3 * H3 * T3 + 12 * H3 * T3 * T3);
-    const int kind = sizeof(T) == 4 ? 0 : 1;
+    const int kind = sizeof(T) == 4 ? 3 : 1;
     prof_begin(st, kind, (double)g.nnode * cols);
     (note_launch(), k_apply_u3_col<T, ALLJ><<<grid, U3_THREADS, smem, st>>>(g, tb, scu, u, su, y, sy, ep));
     prof_end(st, kind);

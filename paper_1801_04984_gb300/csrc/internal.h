@@ -9,9 +9,10 @@
 namespace biot {
 
 // ---- tracing (prof.cu) ------------------------------------------------------
-// 0 FP32 elasticity (displacement-row) operator, 1 FP64 elasticity operator, 2 FP32 Schur
-// Chebyshev step, 3 spare; units = the kernel's work units (node x right-hand side for the
-// elasticity operator, pressure point x right-hand side for the Schur step)
+// 0 FP32 elasticity (displacement-row) operator (z-marching kernel on 3-D grids of >= 1e5
+// nodes, the 2-D kernel), 1 FP64 elasticity operator, 2 FP32 Schur Chebyshev step, 3 FP32 3-D
+// elasticity on grids below 1e5 nodes; units = the kernel's work units (node x right-hand side
+// for the elasticity operator, pressure point x right-hand side for the Schur step)
 constexpr int PROF_KINDS = 4;
 void note_launch();
 void note_launches(long long k);  // graph replays: add the kernels of the graph

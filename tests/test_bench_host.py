@@ -37,3 +37,29 @@ def test_reference_arm_line(capsys, monkeypatch):
     assert line["metric"] == bench.METRIC and line["higher_is_better"] is True
     assert line["cpu_baseline"]["kind"] == "oracle" and line["e2e"]["h2d_bytes_per_step"] == 0
     assert "32^3 hexes" in line["config"]["workload"]
+
+
+def test_schur_roofline_and_dominant_kernel_choice():
+    # 10 launches, 0.3 ms in all, 3e7 point x column units, 8 MB of weights per launch, a 2 ms step
+    r = bench.schur_roofline((10, 0.3, 3e7), 8e6, 0.002, 6700.5, traffic_per_unit=20.5, traffic_file="f")
+    alg = 20.0 * 3e7 + 8e6 * 10
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s"
+    assert abs(r["achieved"] - alg / 0.3e-3 / 1e9) < 1e-9 * r["achieved"]
+    assert abs(r["frac"] - r["achieved"] / 6700.5) < 1e-15
+    assert abs(r["traffic"] - 20.5 * 3e6) < 1e-6 and r["traffic_source"]
+    assert abs(r["share_of_step"] - 0.15) < 1e-15 and abs(r["avg_launch_us"] - 30.0) < 1e-12
+    assert bench.schur_roofline((0, 0.0, 0.0), 8e6, 2.0, 6700.5) is None
+    el = {"kernel": "elasticity", "share_of_step": 0.2}
+    first, second = bench.dominant_roofline(el, r)
+    assert first is el and second is r
+    first, second = bench.dominant_roofline(dict(el, share_of_step=0.1), r)
+    assert first is r and second["kernel"] == "elasticity"
+    # profiling off: no shares, the first object is kept
+    none = {"kernel": "elasticity", "share_of_step": None}
+    assert bench.dominant_roofline(none, None) == (none, None)
+
+
+def test_profile_figures_are_read_from_the_committed_summaries():
+    assert bench.profile_figure("elasticity_fp32_64cube.txt", "dram_bytes_per_node_rhs:") > 24.0
+    assert bench.profile_figure("schur_step_fp32_64cube.txt", "dram_bytes_per_point_rhs:") > 4.0
+    assert bench.profile_figure("absent.txt", "x:") is None
