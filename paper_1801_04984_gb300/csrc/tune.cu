@@ -10,7 +10,9 @@
 // Cache file: $BIOT_TUNE_CACHE if set, else $XDG_CACHE_HOME/biot_gb300/tune.json, else
 // $HOME/.cache/biot_gb300/tune.json.  Format: one JSON object {"key": value, ...}.  BIOT_TUNE=0
 // disables measurement (the callers' heuristics then apply); an unreadable or malformed file
-// is ignored and rewritten.
+// is ignored and rewritten.  The file is read once per process and replaced as a whole: two
+// processes tuning new shapes at the same time can each drop the other's new entry, which is
+// then measured again by the next process that meets that shape.
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
