@@ -611,7 +611,8 @@ void elast3_tune(const Grid& g, const TabT<float>& tb, double lam, double mu, in
   g_zrun_force = 0;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  if (cudaGetLastError() != cudaSuccess || best <= 0) return;
+  // peek, not get: an error of a timed launch stays pending for the caller's launch check
+  if (cudaPeekAtLastError() != cudaSuccess || best <= 0) return;
   tune_put(zrun_key(nx, ny, nz, cols), best);
   int dev = 0;
   cudaGetDevice(&dev);
