@@ -1136,7 +1136,6 @@ template <typename T> constexpr int prec_id();
 template <> constexpr int prec_id<double>() { return 0; }
 template <> constexpr int prec_id<float>() { return 1; }
 
-// precompute what the preconditioner needs for this tau (host syncs, so never inside a capture)
 // launch shapes of the FP32 z-marching elasticity kernel on every level that uses it, for each
 // column count the solver launches (once per context; measured once per GPU and shape)
 template <typename T>
@@ -1152,6 +1151,7 @@ void tune_levels<float>(biot_ctx& c, cudaStream_t st) {
   CKL();
 }
 
+// precompute what the preconditioner needs for this tau (host syncs, so never inside a capture)
 template <typename T>
 void prec_prepare(biot_ctx& c, double tau, cudaStream_t st) {
   ensure_prec<T>(c);
