@@ -54,3 +54,17 @@ def test_library_time_tables_match_the_oracle():
         assert np.allclose(t["V"] @ Lam @ np.linalg.inv(t["V"]), T, atol=1e-11), r
         assert np.allclose(t["W"], np.linalg.inv(t["V"]) @ np.linalg.inv(Mt), atol=1e-10)
         assert (p >= 0) == (r >= 1)  # dG(1) and dG(2) have one complex pair
+
+
+def test_binding_constants_equal_the_header_enums():
+    """Every BIOT_<NAME> = value enumerator of include/biot.h has the same value as the
+    binding's <NAME> constant (the binding passes these integers through the C ABI)."""
+    txt = open(B.HEADER).read()
+    enums = {}
+    for block in re.finditer(r"\benum\s*\{([^}]*)\}", txt):
+        body = re.sub(r"/\*.*?\*/", "", block.group(1), flags=re.S)
+        enums.update({m.group(1): int(m.group(2)) for m in re.finditer(r"\bBIOT_([A-Z0-9_]+)\s*=\s*(-?\d+)", body)})
+    assert len(enums) >= 25
+    for name, value in enums.items():
+        assert hasattr(B, name), name
+        assert getattr(B, name) == value, (name, getattr(B, name), value)
